@@ -1,0 +1,12 @@
+"""Plain FP64 CPU oracle of the FR hot path (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import anything here; the product path (the CUDA library and
+its Python binding) never does, and shares no code with it.
+
+Modules: ``basis`` (Gauss-Legendre points, Lagrange, DG correction),
+``element`` (tensor reference element and dense operators), ``geometry``
+(element maps, metrics, face connectivity), ``physics`` (Navier-Stokes
+fluxes, Rusanov, boundary states), ``fr`` (residual), ``timestep`` (RK4,
+LSRK45), ``acoustics`` (probe, OASPL).
+"""

@@ -1,0 +1,422 @@
+"""Seeded synthetic quad/hex meshes shaped like the paper's workloads.
+
+Input generators only: vertex coordinates, corner connectivity, optional
+high-order geometry nodes and boundary tags.  Nothing here evaluates any part
+of the Flux Reconstruction method (no quadrature points, metrics, fluxes or
+face-point matching); both the FP64 oracle and the CUDA library derive all of
+that themselves from a ``Mesh``.
+
+Conventions shared by every consumer of a ``Mesh``:
+
+* corners of an element are listed in tensor order of the reference
+  coordinates, xi fastest: quad (-1,-1), (1,-1), (-1,1), (1,1); hex the same
+  square at zeta=-1 followed by the square at zeta=+1;
+* faces are numbered -xi, +xi, -eta, +eta (, -zeta, +zeta);
+* optional geometry nodes are the element map sampled at the equispaced
+  tensor lattice of degree ``geo_order`` (xi fastest), corners included;
+* face tags: 0 interior (matched through shared corner vertices), 1 periodic
+  (matched to a face whose corners coincide after adding or subtracting one
+  of ``periodic_shift``), 2 no-slip adiabatic wall, 3 characteristic far
+  field, 4 inflow (far field with a boundary-layer profile), 5 outflow
+  (characteristic, same construction as far field).
+
+Workload shapes follow the paper: cavity (Sec. 3.1.1: inlet 5D upstream,
+outlet 60D downstream with a 50D buffer, domain height 15D with a 5D buffer,
+stretching 1.05 / 1.075), NACA 4-digit O-meshes (Sec. 5), periodic boxes for
+the isentropic vortex and Taylor-Green cases.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+import numpy as np
+
+TAG_INTERIOR = 0
+TAG_PERIODIC = 1
+TAG_WALL = 2
+TAG_FARFIELD = 3
+TAG_INFLOW = 4
+TAG_OUTFLOW = 5
+
+
+@dataclass
+class Mesh:
+    dim: int
+    xyz: np.ndarray                 # (n_vert, dim) float64
+    elem_vert: np.ndarray           # (n_elem, 2**dim) int64
+    face_tag: np.ndarray            # (n_elem, 2*dim) int32
+    periodic_shift: np.ndarray      # (n_shift, dim) float64
+    geo_order: int = 1
+    geo_nodes: np.ndarray | None = None   # (n_elem, (q+1)**dim, dim) float64
+    info: dict = field(default_factory=dict)
+
+    @property
+    def n_elem(self) -> int:
+        return int(self.elem_vert.shape[0])
+
+    def node_coords(self) -> np.ndarray:
+        """Geometry nodes of every element, (n_elem, (q+1)**dim, dim)."""
+        if self.geo_nodes is not None:
+            return self.geo_nodes
+        return self.xyz[self.elem_vert]
+
+
+# ---------------------------------------------------------------------------
+# boundary classification helper (pure bookkeeping on corner vertex ids)
+# ---------------------------------------------------------------------------
+
+_QUAD_FACES = [(0, 2), (1, 3), (0, 1), (2, 3)]
+_HEX_FACES = [(0, 2, 4, 6), (1, 3, 5, 7), (0, 1, 4, 5), (2, 3, 6, 7),
+              (0, 1, 2, 3), (4, 5, 6, 7)]
+
+
+def face_corners(dim: int):
+    return _QUAD_FACES if dim == 2 else _HEX_FACES
+
+
+def _tag_unmatched(elem_vert, xyz, dim, classify):
+    """Tag every face without a vertex-sharing partner via ``classify``."""
+    faces = face_corners(dim)
+    n_elem = elem_vert.shape[0]
+    tags = np.zeros((n_elem, 2 * dim), dtype=np.int32)
+    keys = {}
+    for e in range(n_elem):
+        for f, loc in enumerate(faces):
+            k = tuple(sorted(int(elem_vert[e, c]) for c in loc))
+            keys.setdefault(k, []).append((e, f))
+    for k, lst in keys.items():
+        if len(lst) == 1:
+            e, f = lst[0]
+            centre = xyz[list(k)].mean(axis=0)
+            tags[e, f] = classify(centre, f)
+        elif len(lst) > 2:
+            raise ValueError("non-manifold face in generated mesh")
+    return tags
+
+
+# ---------------------------------------------------------------------------
+# G1 / G3: periodic Cartesian boxes
+# ---------------------------------------------------------------------------
+
+def periodic_box(dim: int, n, lo, hi, jitter: float = 0.0, seed: int = 2312) -> Mesh:
+    """Periodic box of n[0] x n[1] (x n[2]) straight-sided elements.
+
+    ``jitter`` moves every vertex that is not on the box boundary by a seeded
+    uniform offset of at most ``jitter`` times the local spacing, giving
+    non-affine elements for free-stream tests.
+    """
+    n = [int(v) for v in n]
+    lo = np.asarray(lo, float)
+    hi = np.asarray(hi, float)
+    axes = [np.linspace(lo[a], hi[a], n[a] + 1) for a in range(dim)]
+    grids = np.meshgrid(*axes, indexing="ij")
+    xyz = np.stack([g.ravel(order="F") for g in grids], axis=1)  # x fastest
+    nv = [v + 1 for v in n]
+
+    def vid(idx):
+        out = 0
+        stride = 1
+        for a in range(dim):
+            out += idx[a] * stride
+            stride *= nv[a]
+        return out
+
+    elems = []
+    if dim == 2:
+        for j in range(n[1]):
+            for i in range(n[0]):
+                elems.append([vid((i, j)), vid((i + 1, j)),
+                              vid((i, j + 1)), vid((i + 1, j + 1))])
+    else:
+        for k in range(n[2]):
+            for j in range(n[1]):
+                for i in range(n[0]):
+                    elems.append([vid((i + a, j + b, k + c))
+                                  for c in (0, 1) for b in (0, 1) for a in (0, 1)])
+    elem_vert = np.asarray(elems, dtype=np.int64)
+
+    if jitter > 0.0:
+        rng = np.random.default_rng(seed)
+        h = (hi - lo) / np.asarray(n, float)
+        inner = np.ones(xyz.shape[0], bool)
+        for a in range(dim):
+            inner &= (xyz[:, a] > lo[a] + 1e-12) & (xyz[:, a] < hi[a] - 1e-12)
+        off = rng.uniform(-1.0, 1.0, size=xyz.shape) * h * jitter
+        xyz = xyz + off * inner[:, None]
+
+    shift = np.diag(hi - lo)
+    tags = _tag_unmatched(elem_vert, xyz, dim, lambda c, f: TAG_PERIODIC)
+    return Mesh(dim=dim, xyz=xyz, elem_vert=elem_vert, face_tag=tags,
+                periodic_shift=shift, info={"kind": "periodic_box", "n": n})
+
+
+def vortex_mesh(n: int = 16, jitter: float = 0.0, seed: int = 2312) -> Mesh:
+    """Isentropic-vortex box [-5,5]^2 with n x n quads."""
+    return periodic_box(2, (n, n), (-5.0, -5.0), (5.0, 5.0), jitter, seed)
+
+
+def tgv_mesh(n: int = 16) -> Mesh:
+    """Taylor-Green box [0, 2 pi]^3 with n^3 hexes."""
+    two_pi = 2.0 * np.pi
+    return periodic_box(3, (n, n, n), (0.0, 0.0, 0.0), (two_pi, two_pi, two_pi))
+
+
+# ---------------------------------------------------------------------------
+# 1-D graded distributions
+# ---------------------------------------------------------------------------
+
+def graded_line(x0: float, x1: float, h0: float, ratio: float, at_start=True):
+    """Nodes from x0 to x1 whose spacing starts at about h0 at one end and
+    grows geometrically by ``ratio``; the last cell is absorbed so that the
+    end point is hit exactly."""
+    length = abs(x1 - x0)
+    sizes = []
+    h = h0
+    tot = 0.0
+    while tot + h < length - 1e-12:
+        sizes.append(h)
+        tot += h
+        h *= ratio
+    if not sizes:
+        sizes = [length]
+    else:
+        rem = length - tot
+        if rem < 0.5 * sizes[-1]:
+            sizes[-1] += rem
+        else:
+            sizes.append(rem)
+    sizes = np.asarray(sizes)
+    if not at_start:
+        sizes = sizes[::-1]
+    s = np.concatenate([[0.0], np.cumsum(sizes)])
+    s *= length / s[-1]
+    return x0 + np.sign(x1 - x0) * s
+
+
+def _two_zone(x0, x1, xb, h0, r1, r2):
+    """Spacing h0 at x0 grows by r1 up to xb, then by r2 to x1 (a buffer)."""
+    a = graded_line(x0, xb, h0, r1)
+    if abs(x1 - xb) < 1e-12:
+        return a
+    hb = abs(a[-1] - a[-2])
+    b = graded_line(xb, x1, hb * r2, r2)
+    return np.concatenate([a, b[1:]])
+
+
+# ---------------------------------------------------------------------------
+# G2: 2-D deep-cavity proxy
+# ---------------------------------------------------------------------------
+
+def _cavity_count(h0, LD):
+    xs = _cavity_x(h0, LD)
+    ys, yc = _cavity_y(h0)
+    return (len(xs) - 1) * (len(ys) - 1) + (len(_cavity_xc(xs, LD)) - 1) * (len(yc) - 1)
+
+
+def _cavity_x(h0, LD):
+    ncav = max(2, int(round(LD / h0)))
+    xc = np.linspace(0.0, LD, ncav + 1)
+    up = _two_zone(0.0, -5.0, -5.0, xc[1] - xc[0], 1.05, 1.05)[::-1]
+    down = _two_zone(LD, LD + 60.0, LD + 10.0, xc[1] - xc[0], 1.05, 1.075)
+    return np.concatenate([up[:-1], xc, down[1:]])
+
+
+def _cavity_xc(xs, LD):
+    return xs[(xs >= -1e-12) & (xs <= LD + 1e-12)]
+
+
+def _cavity_y(h0):
+    ys = _two_zone(0.0, 15.0, 10.0, h0, 1.05, 1.075)
+    nc = max(2, int(round(1.0 / h0)))
+    yc = np.linspace(-1.0, 0.0, nc + 1)
+    return ys, yc
+
+
+def cavity_mesh(target_elems: int = 32000, LD: float = 0.5, seed: int = 2312) -> Mesh:
+    """2-D channel over a flat plate with a rectangular cavity of depth D=1.
+
+    Cavity occupies 0<x<LD, -1<y<0.  Plate wall at y=0 elsewhere; inflow at
+    x=-5 (5D upstream), outflow at x=LD+60 with the last 50D stretched by 1.075
+    as a buffer; top boundary at y=15 with the last 5D stretched by 1.075.
+    The minimum spacing is found by bisection so that the element count is
+    close to ``target_elems``.  ``seed`` is accepted for interface symmetry;
+    the cavity proxy has no random component.
+    """
+    lo, hi = 1e-3, 0.5
+    for _ in range(60):
+        mid = np.sqrt(lo * hi)
+        if _cavity_count(mid, LD) > target_elems:
+            lo = mid
+        else:
+            hi = mid
+    h0 = hi
+    xs = _cavity_x(h0, LD)
+    ys, yc = _cavity_y(h0)
+    xc = _cavity_xc(xs, LD)
+    nx, ny = len(xs), len(ys)
+    # channel block vertices
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    pts = [np.stack([X.ravel(order="F"), Y.ravel(order="F")], 1)]
+
+    def vA(i, j):
+        return i + nx * j
+
+    # cavity block shares its top row (y=0) with the channel block
+    i0 = int(np.where(np.abs(xs) < 1e-12)[0][0])
+    ncx, ncy = len(xc), len(yc)
+    base = nx * ny
+    Xc, Yc = np.meshgrid(xc, yc[:-1], indexing="ij")
+    pts.append(np.stack([Xc.ravel(order="F"), Yc.ravel(order="F")], 1))
+
+    def vC(i, j):
+        if j == ncy - 1:
+            return vA(i0 + i, 0)
+        return base + i + ncx * j
+
+    elems = []
+    for j in range(ny - 1):
+        for i in range(nx - 1):
+            elems.append([vA(i, j), vA(i + 1, j), vA(i, j + 1), vA(i + 1, j + 1)])
+    for j in range(ncy - 1):
+        for i in range(ncx - 1):
+            elems.append([vC(i, j), vC(i + 1, j), vC(i, j + 1), vC(i + 1, j + 1)])
+    xyz = np.concatenate(pts, 0)
+    elem_vert = np.asarray(elems, np.int64)
+    x_in, x_out, y_top = xs[0], xs[-1], ys[-1]
+
+    def classify(c, f):
+        if abs(c[0] - x_in) < 1e-9:
+            return TAG_INFLOW
+        if abs(c[0] - x_out) < 1e-9:
+            return TAG_OUTFLOW
+        if abs(c[1] - y_top) < 1e-9:
+            return TAG_FARFIELD
+        return TAG_WALL
+
+    tags = _tag_unmatched(elem_vert, xyz, 2, classify)
+    probe = np.array([0.5 * LD, 7.16])
+    return Mesh(dim=2, xyz=xyz, elem_vert=elem_vert, face_tag=tags,
+                periodic_shift=np.zeros((0, 2)),
+                info={"kind": "cavity", "LD": LD, "h0": h0, "probe": probe,
+                      "wall_y": 0.0, "x_inflow": x_in})
+
+
+# ---------------------------------------------------------------------------
+# G4: NACA 4-digit O-meshes
+# ---------------------------------------------------------------------------
+
+def naca4(m: float, pc: float, t: float, xc: np.ndarray):
+    """Upper and lower surface points of a NACA 4-digit profile at chord
+    stations xc (closed trailing edge thickness form)."""
+    yt = 5.0 * t * (0.2969 * np.sqrt(xc) - 0.1260 * xc - 0.3516 * xc ** 2
+                    + 0.2843 * xc ** 3 - 0.1036 * xc ** 4)
+    if m > 0.0:
+        yc = np.where(xc < pc, m / pc ** 2 * (2 * pc * xc - xc ** 2),
+                      m / (1 - pc) ** 2 * ((1 - 2 * pc) + 2 * pc * xc - xc ** 2))
+        dy = np.where(xc < pc, 2 * m / pc ** 2 * (pc - xc),
+                      2 * m / (1 - pc) ** 2 * (pc - xc))
+    else:
+        yc = np.zeros_like(xc)
+        dy = np.zeros_like(xc)
+    th = np.arctan(dy)
+    xu, yu = xc - yt * np.sin(th), yc + yt * np.cos(th)
+    xl, yl = xc + yt * np.sin(th), yc - yt * np.cos(th)
+    return xu, yu, xl, yl
+
+
+def _naca_surface(m, pc, t, s):
+    """Surface point at O-mesh parameter s in [0,1): 0 = trailing edge, going
+    along the lower surface to the leading edge (s=0.5) and back over the
+    upper surface (counter-clockwise)."""
+    s = np.asarray(s, float) % 1.0
+    lower = s < 0.5
+    u = np.where(lower, 1.0 - 2.0 * s, 2.0 * s - 1.0)   # 1 at TE, 0 at LE
+    xc = 0.5 * (1.0 - np.cos(np.pi * u))
+    xu, yu, xl, yl = naca4(m, pc, t, xc)
+    x = np.where(lower, xl, xu)
+    y = np.where(lower, yl, yu)
+    return x, y
+
+
+def naca_omesh(m: float, pc: float, t: float, aoa_deg: float, n_elem: int,
+               p_geo: int = 3, radius: float = 20.0) -> Mesh:
+    """Curved O-mesh around a NACA 4-digit profile of unit chord.
+
+    N_theta x N_r quads, geometric stretching in the radial direction out to
+    ``radius`` chords, geometry nodes of degree ``p_geo`` sampled from the
+    continuous map, profile rotated about the quarter chord so that a free
+    stream along +x meets it at ``aoa_deg``.  Wall tag on the profile, far
+    field on the outer circle; the O-cut is an ordinary interior connection.
+    """
+    nr = max(4, int(round(np.sqrt(n_elem / 2.0))))
+    nth = max(8, 2 * int(round(n_elem / nr / 2.0)))
+    q = int(p_geo)
+    # radial map: geometric cell growth with first cell h1, total = 1 (fraction)
+    ratio = 1.0 + 8.0 / nr      # fixed growth; cells small near the wall
+    def rad(sr):
+        return (ratio ** (sr * nr) - 1.0) / (ratio ** nr - 1.0)
+    def xmap(sth, sr):
+        xs, ys = _naca_surface(m, pc, t, sth)
+        ang = 2.0 * np.pi * sth
+        # far-field circle centred at mid chord, matched in parameter
+        xf = 0.5 + radius * np.cos(ang)
+        yf = -radius * np.sin(ang)
+        w = rad(sr)
+        return xs + w * (xf - xs), ys + w * (yf - ys)
+    # fine lattice of geometry nodes, shared by neighbouring elements
+    fth = np.arange(nth * q) / (nth * q)
+    fr = np.arange(nr * q + 1) / (nr * q)
+    TH, R = np.meshgrid(fth, fr, indexing="ij")
+    FX, FY = xmap(TH, R)
+    # rotate by -aoa about quarter chord
+    a = np.deg2rad(aoa_deg)
+    ca, sa = np.cos(a), np.sin(a)
+    FX0, FY0 = FX - 0.25, FY
+    FX, FY = 0.25 + ca * FX0 + sa * FY0, -sa * FX0 + ca * FY0
+    # corner vertices
+    xyz = np.stack([FX[::q, ::q].ravel(order="F"), FY[::q, ::q].ravel(order="F")], 1)
+
+    def vid(i, j):
+        return (i % nth) + nth * j
+
+    elems, nodes = [], []
+    for j in range(nr):
+        for i in range(nth):
+            elems.append([vid(i, j), vid(i + 1, j), vid(i, j + 1), vid(i + 1, j + 1)])
+            ii = (np.arange(i * q, i * q + q + 1)) % (nth * q)
+            jj = np.arange(j * q, j * q + q + 1)
+            # tensor order: xi (theta) fastest
+            nx_ = FX[np.ix_(ii, jj)].T.ravel()
+            ny_ = FY[np.ix_(ii, jj)].T.ravel()
+            nodes.append(np.stack([nx_, ny_], 1))
+    elem_vert = np.asarray(elems, np.int64)
+    geo_nodes = np.asarray(nodes)
+    # the profile wall is eta=-1 of the first ring, the far field eta=+1 of the last
+    tags = np.zeros((elem_vert.shape[0], 4), np.int32)
+    tags[:nth, 2] = TAG_WALL
+    tags[(nr - 1) * nth:, 3] = TAG_FARFIELD
+    te = np.array([0.25 + ca * 0.75, -sa * 0.75])
+    return Mesh(dim=2, xyz=xyz, elem_vert=elem_vert, face_tag=tags,
+                periodic_shift=np.zeros((0, 2)), geo_order=q, geo_nodes=geo_nodes,
+                info={"kind": "naca", "m": m, "pc": pc, "t": t, "aoa": aoa_deg,
+                      "nth": nth, "nr": nr, "probe": te + np.array([0.0, -2.0])})
+
+
+def airfoil_batch(n_inst: int = 32, seed: int = 2312, e_lo: int = 8000,
+                  e_hi: int = 40000, p_geo: int = 3):
+    """One MADS poll's worth of NACA 4-digit candidates, drawn from ``seed``:
+    max camber U[0,0.06], camber position U[0.2,0.6], thickness U[0.08,0.16],
+    angle of attack U[0,6] deg, element count U[e_lo, e_hi]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_inst):
+        m = rng.uniform(0.0, 0.06)
+        pc = rng.uniform(0.2, 0.6)
+        t = rng.uniform(0.08, 0.16)
+        aoa = rng.uniform(0.0, 6.0)
+        ne = int(rng.uniform(e_lo, e_hi))
+        out.append(naca_omesh(m, pc, t, aoa, ne, p_geo))
+    return out
+
+
+def concat_info(meshes):
+    return [mm.info for mm in meshes]
