@@ -144,8 +144,13 @@ class FRDiscretisation:
         return F
 
     # -- residual -------------------------------------------------------------------
-    def residual(self, U, elems=None):
-        """du/dt at the solution points of ``elems`` (all when None)."""
+    def residual(self, U, elems=None, magnitude=False):
+        """du/dt at the solution points of ``elems`` (all when None).
+
+        With ``magnitude=True`` it also returns the sum of the absolute values
+        of the terms that step 7 adds up, divided by J: the scale of the
+        floating-point error bound of the residual (a sum of n terms computed
+        in precision eps has error at most about n eps times this)."""
         ref, phys = self.ref, self.phys
         E = self.mesh.n_elem
         if elems is None:
@@ -193,4 +198,8 @@ class FRDiscretisation:
             Fstar = Fstar - fv_common
         jump = Fstar - Fdisc                                         # step 6
         div = np.einsum("kst,etkv->esv", ref.D, Fhat) + np.einsum("sf,efv->esv", ref.Cdiv, jump)
+        if magnitude:
+            mag = (np.einsum("kst,etkv->esv", np.abs(ref.D), np.abs(Fhat))
+                   + np.einsum("sf,efv->esv", np.abs(ref.Cdiv), np.abs(Fstar) + np.abs(Fdisc)))
+            return -div / JA[..., None], mag / JA[..., None]
         return -div / JA[..., None]                                  # step 7

@@ -49,17 +49,24 @@ def _shape(q: int, dim: int, X):
 
 
 def map_points(mesh, elems, X):
-    """Physical coordinates (ne, npts, dim) of reference points X in elems."""
+    """Physical coordinates (ne, npts, dim) of reference points X in elems.
+
+    The map is translation invariant (the shape functions sum to one), so it
+    is evaluated on node offsets from the element's first node and the
+    offset added back: the same value with rounding relative to the element
+    size instead of the coordinates' magnitude."""
     nodes = mesh.node_coords()[elems]
+    base = nodes[:, :1, :]
     N, _ = _shape(mesh.geo_order, mesh.dim, X)
-    return np.einsum("pa,eaj->epj", N, nodes)
+    return base + np.einsum("pa,eaj->epj", N, nodes - base)
 
 
 def jacobian(mesh, elems, X):
-    """A[e, p, j, k] = dx_j / dxi_k at reference points X."""
+    """A[e, p, j, k] = dx_j / dxi_k at reference points X (from node offsets:
+    the derivative of a translation is zero)."""
     nodes = mesh.node_coords()[elems]
     _, dN = _shape(mesh.geo_order, mesh.dim, X)
-    return np.einsum("pak,eaj->epjk", dN, nodes)
+    return np.einsum("pak,eaj->epjk", dN, nodes - nodes[:, :1, :])
 
 
 def adjugate(A):
