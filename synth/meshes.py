@@ -306,9 +306,10 @@ def cavity_mesh(target_elems: int = 32000, LD: float = 0.5, seed: int = 2312) ->
 
 def naca4(m: float, pc: float, t: float, xc: np.ndarray):
     """Upper and lower surface points of a NACA 4-digit profile at chord
-    stations xc (closed trailing edge thickness form)."""
+    stations xc (standard open trailing edge: a blunt base of height about
+    0.021 t)."""
     yt = 5.0 * t * (0.2969 * np.sqrt(xc) - 0.1260 * xc - 0.3516 * xc ** 2
-                    + 0.2843 * xc ** 3 - 0.1036 * xc ** 4)
+                    + 0.2843 * xc ** 3 - 0.1015 * xc ** 4)
     if m > 0.0:
         yc = np.where(xc < pc, m / pc ** 2 * (2 * pc * xc - xc ** 2),
                       m / (1 - pc) ** 2 * ((1 - 2 * pc) + 2 * pc * xc - xc ** 2))
@@ -323,17 +324,37 @@ def naca4(m: float, pc: float, t: float, xc: np.ndarray):
     return xu, yu, xl, yl
 
 
-def _naca_surface(m, pc, t, s):
-    """Surface point at O-mesh parameter s in [0,1): 0 = trailing edge, going
-    along the lower surface to the leading edge (s=0.5) and back over the
-    upper surface (counter-clockwise)."""
+def _naca_surface(m, pc, t, s, s_base=0.0):
+    """Surface point at O-mesh parameter s in [0,1), clockwise: s in
+    [0, s_base/2) runs down the lower half of the blunt trailing-edge base
+    from its midpoint, [s_base/2, 0.5) along the lower surface from the
+    trailing edge to the leading edge, [0.5, 1 - s_base/2) back over the upper
+    surface and [1 - s_base/2, 1) down the upper half of the base."""
     s = np.asarray(s, float) % 1.0
+    hb = 0.5 * s_base
+    xu1, yu1, xl1, yl1 = naca4(m, pc, t, np.array([1.0]))
+    xm, ym = 0.5 * (xu1[0] + xl1[0]), 0.5 * (yu1[0] + yl1[0])
     lower = s < 0.5
-    u = np.where(lower, 1.0 - 2.0 * s, 2.0 * s - 1.0)   # 1 at TE, 0 at LE
-    xc = 0.5 * (1.0 - np.cos(np.pi * u))
+    if hb > 0:
+        u = np.where(lower, 1.0 - (s - hb) / (0.5 - hb), (s - 0.5) / (0.5 - hb))
+    else:
+        u = np.where(lower, 1.0 - 2.0 * s, 2.0 * s - 1.0)   # 1 at TE, 0 at LE
+    u = np.clip(u, 0.0, 1.0)
+    # clustered at the leading edge only; spacing at the trailing edge stays
+    # comparable to the wall-normal cells so that no cell there is a sliver
+    xc = 1.0 - np.cos(0.5 * np.pi * u)
     xu, yu, xl, yl = naca4(m, pc, t, xc)
     x = np.where(lower, xl, xu)
     y = np.where(lower, yl, yu)
+    if hb > 0:
+        b_lo = s < hb
+        b_up = s >= 1.0 - hb
+        f_lo = s / hb
+        f_up = (s - (1.0 - hb)) / hb
+        x = np.where(b_lo, xm + f_lo * (xl1[0] - xm), x)
+        y = np.where(b_lo, ym + f_lo * (yl1[0] - ym), y)
+        x = np.where(b_up, xu1[0] + f_up * (xm - xu1[0]), x)
+        y = np.where(b_up, yu1[0] + f_up * (ym - yu1[0]), y)
     return x, y
 
 
@@ -350,23 +371,68 @@ def naca_omesh(m: float, pc: float, t: float, aoa_deg: float, n_elem: int,
     nr = max(4, int(round(np.sqrt(n_elem / 2.0))))
     nth = max(8, 2 * int(round(n_elem / nr / 2.0)))
     q = int(p_geo)
-    # radial map: geometric cell growth with first cell h1, total = 1 (fraction)
-    ratio = 1.0 + 8.0 / nr      # fixed growth; cells small near the wall
-    def rad(sr):
-        return (ratio ** (sr * nr) - 1.0) / (ratio ** nr - 1.0)
-    def xmap(sth, sr):
-        xs, ys = _naca_surface(m, pc, t, sth)
-        ang = 2.0 * np.pi * sth
-        # far-field circle centred at mid chord, matched in parameter
-        xf = 0.5 + radius * np.cos(ang)
-        yf = -radius * np.sin(ang)
-        w = rad(sr)
-        return xs + w * (xf - xs), ys + w * (yf - ys)
-    # fine lattice of geometry nodes, shared by neighbouring elements
+    # radial distance: geometric cells from h_wall at the profile to ``radius``
+    h_wall = 1e-3
+    lo_r, hi_r = 1.0 + 1e-9, 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo_r + hi_r)
+        if h_wall * (mid ** nr - 1.0) / (mid - 1.0) > radius:
+            hi_r = mid
+        else:
+            lo_r = mid
+    ratio = 0.5 * (lo_r + hi_r)
+
+    def dist(sr):
+        return h_wall * (ratio ** (sr * nr) - 1.0) / (ratio - 1.0)
+
+    s_base = 2.0 / nth                    # one theta cell per half of the base
+
+    def surf(sth):
+        return _naca_surface(m, pc, t, sth, s_base)
+
+    def raw_normal(sth):
+        # outward normal of the clockwise surface curve: tangent rotated +90 deg
+        ds = 1e-7
+        xp, yp = surf(sth + ds)
+        xm_, ym_ = surf(sth - ds)
+        tx, ty = xp - xm_, yp - ym_
+        nrm = np.hypot(tx, ty)
+        return -ty / nrm, tx / nrm
+
+    sigma = 1.5 / nth
+
+    def normal(sth):
+        """Surface normal averaged with Gaussian weights over about three
+        cells along the wall, so the departure direction turns smoothly
+        around the corners of the trailing-edge base."""
+        sth = np.asarray(sth, float)
+        ax, ay = np.zeros_like(sth), np.zeros_like(sth)
+        for k in range(-64, 65):
+            w = np.exp(-0.5 * (k / 16.0) ** 2)
+            nx0, ny0 = raw_normal(sth + k * sigma / 16.0)
+            ax += w * nx0
+            ay += w * ny0
+        nrm = np.hypot(ax, ay)
+        return ax / nrm, ay / nrm
+
+    # Lines leave the wall along the smoothed normal (blend weight
+    # g = rho (1 - rho)^2 on a unit chord) and end on the far-field circle
+    # (weight h = rho^2), rho in [0, 1] from the radial distance.
+    # fine lattice of geometry nodes, shared by neighbouring elements; the map
+    # is separable, so evaluate the wall quantities once per theta station
     fth = np.arange(nth * q) / (nth * q)
     fr = np.arange(nr * q + 1) / (nr * q)
-    TH, R = np.meshgrid(fth, fr, indexing="ij")
-    FX, FY = xmap(TH, R)
+    xs, ys = surf(fth)
+    nx_, ny_ = normal(fth)
+    ang = 2.0 * np.pi * fth
+    xf = 0.5 + radius * np.cos(ang)
+    yf = -radius * np.sin(ang)
+    d = dist(fr)
+    rho = (-1.0 + np.sqrt(1.0 + 4.0 * radius * d)) / (2.0 * radius)
+    h = (rho * rho)[None, :]
+    g = (rho * (1.0 - rho) ** 2)[None, :]
+    FX = (1 - h) * xs[:, None] + h * xf[:, None] + g * nx_[:, None]
+    FY = (1 - h) * ys[:, None] + h * yf[:, None] + g * ny_[:, None]
     # rotate by -aoa about quarter chord
     a = np.deg2rad(aoa_deg)
     ca, sa = np.cos(a), np.sin(a)
@@ -378,27 +444,33 @@ def naca_omesh(m: float, pc: float, t: float, aoa_deg: float, n_elem: int,
     def vid(i, j):
         return (i % nth) + nth * j
 
-    elems, nodes = [], []
-    for j in range(nr):
-        for i in range(nth):
-            elems.append([vid(i, j), vid(i + 1, j), vid(i, j + 1), vid(i + 1, j + 1)])
-            ii = (np.arange(i * q, i * q + q + 1)) % (nth * q)
-            jj = np.arange(j * q, j * q + q + 1)
-            # tensor order: xi (theta) fastest
-            nx_ = FX[np.ix_(ii, jj)].T.ravel()
-            ny_ = FY[np.ix_(ii, jj)].T.ravel()
-            nodes.append(np.stack([nx_, ny_], 1))
+    jj_e, ii_e = np.meshgrid(np.arange(nr), np.arange(nth), indexing="ij")
+    ii_e, jj_e = ii_e.ravel(), jj_e.ravel()          # element (i, j), theta fastest
+    elems = np.stack([vid(ii_e, jj_e), vid(ii_e + 1, jj_e), vid(ii_e, jj_e + 1),
+                      vid(ii_e + 1, jj_e + 1)], 1)
+    a_loc = np.arange(q + 1)
+    # node (a, b) of element (i, j): lattice index (i q + a, j q + b), a fastest
+    la = ((ii_e[:, None, None] * q + a_loc[None, None, :]) % (nth * q))
+    lb = (jj_e[:, None, None] * q + a_loc[None, :, None])
+    la, lb = np.broadcast_arrays(la, lb)
+    nodes = np.stack([FX[la, lb].reshape(len(ii_e), -1), FY[la, lb].reshape(len(ii_e), -1)], -1)
     elem_vert = np.asarray(elems, np.int64)
-    geo_nodes = np.asarray(nodes)
+    geo_nodes = np.ascontiguousarray(nodes)
     # the profile wall is eta=-1 of the first ring, the far field eta=+1 of the last
     tags = np.zeros((elem_vert.shape[0], 4), np.int32)
     tags[:nth, 2] = TAG_WALL
     tags[(nr - 1) * nth:, 3] = TAG_FARFIELD
     te = np.array([0.25 + ca * 0.75, -sa * 0.75])
+    # dense sampling of the wall (for wall-distance based initial states)
+    ws = np.linspace(0.0, 1.0, 8 * nth * q, endpoint=False)
+    wx, wy = surf(ws)
+    wx0 = wx - 0.25
+    wall = np.stack([0.25 + ca * wx0 + sa * wy, -sa * wx0 + ca * wy], 1)
     return Mesh(dim=2, xyz=xyz, elem_vert=elem_vert, face_tag=tags,
                 periodic_shift=np.zeros((0, 2)), geo_order=q, geo_nodes=geo_nodes,
                 info={"kind": "naca", "m": m, "pc": pc, "t": t, "aoa": aoa_deg,
-                      "nth": nth, "nr": nr, "probe": te + np.array([0.0, -2.0])})
+                      "nth": nth, "nr": nr, "probe": te + np.array([0.0, -2.0]),
+                      "wall_points": wall})
 
 
 def airfoil_batch(n_inst: int = 32, seed: int = 2312, e_lo: int = 8000,

@@ -97,9 +97,10 @@ def smooth_perturbed(x, dim, mach, amp=0.05, seed=2312, n_modes=4, gamma=GAMMA):
     rng = np.random.default_rng(seed)
     x = np.asarray(x, float)
     shp = x.shape[:-1]
-    prim = [np.ones(shp)] + [np.zeros(shp) for _ in range(dim)] + [np.ones(shp)]
+    p_inf = 1.0 / (gamma * mach * mach)
+    prim = [np.ones(shp)] + [np.zeros(shp) for _ in range(dim)] + [np.full(shp, p_inf)]
     prim[1] = prim[1] + 1.0
-    scale = [1.0] + [1.0] * dim + [1.0 / (gamma * mach * mach)]
+    scale = [1.0] + [1.0] * dim + [p_inf]
     for comp in range(dim + 2):
         acc = np.zeros(shp)
         for _ in range(n_modes):
@@ -124,3 +125,20 @@ def random_state(n_elem, n_sp, dim, mach, amp=0.05, seed=2312, gamma=GAMMA):
     vel = vel + amp * rng.uniform(-1, 1, shp + (dim,))
     p = (1.0 / (gamma * mach * mach)) * (1.0 + amp * rng.uniform(-1, 1, shp))
     return primitive_to_conserved(rho, vel, p, gamma)
+
+
+def wall_damped(x, wall_pts, delta, base):
+    """Scale the velocity of the conserved state ``base`` by
+    1 - exp(-d/delta), d the distance of each point to the nearest of the
+    ``wall_pts`` (a dense sampling of the wall), keeping density and
+    pressure: a start that satisfies the no-slip wall instead of an
+    impulsive one."""
+    from scipy.spatial import cKDTree
+    x = np.asarray(x, float)
+    d, _ = cKDTree(np.asarray(wall_pts, float)).query(x.reshape(-1, x.shape[-1]))
+    f = (1.0 - np.exp(-d / delta)).reshape(x.shape[:-1])
+    dim = x.shape[-1]
+    rho = base[..., 0]
+    vel = base[..., 1:1 + dim] / rho[..., None]
+    p = (GAMMA - 1.0) * (base[..., -1] - 0.5 * rho * np.sum(vel * vel, -1))
+    return primitive_to_conserved(rho, vel * f[..., None], p)
