@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the FR hot path on one GB300 (or N, weak scaling).
+
+Workload: one MADS poll of NACA 4-digit candidates (Sec. 5 of
+arXiv:2312.14167; the batched-airfoil workload): 32 seeded 2-D O-meshes of
+8k-40k curved quads, p = 3, compressible Navier-Stokes (BR2) at Re_c = 23000,
+M = 0.2, LSRK45, mixed precision (FP32 state/fluxes, FP64 geometry setup and
+FP64 probe/force accumulators), one observer per candidate 2 chords below the
+trailing edge.  A step is one LSRK45 step of every candidate (5 stages x
+(gradient kernel + fused flux/update kernel)) plus the probe and wall-force
+sampling kernels, replayed from a CUDA graph.
+
+Metric: solution-point RK-stage updates per second (sum over candidates of
+elements x 16 solution points x 5 stages x steps / device time).
+
+Extra keys: the plain FP64 path on the same candidates run one after another
+(the comparison the metric names), sampled parity against the FP64 oracle at
+full size, the roofline of the dominant kernel, the oracle's own throughput on
+the host cores, clocks during the timed region, and an end-to-end figure
+through the C ABI with host buffers.
+
+``--impl reference`` times the FP64 oracle (the reference arm: a deliberately
+plain CPU program) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "sol-pt RK-stage updates/s, batched mixed-prec vs plain FP64 FR, same GB300"
+UNIT = "sol-pt RK-stage updates/s"
+GAMMA, PR = 1.4, 0.71
+RE, MACH, P = 23000.0, 0.2, 3
+N_INST = 32
+CANDIDATES = N_INST      # --candidates: a smaller poll for profiling captures
+STAGES = 5
+NSP = (P + 1) ** 2
+NFP = 4 * (P + 1)
+V = 4
+WORKLOAD = ("32 NACA 4-digit O-meshes (8k-40k curved quads, seed 2312), p=3, NS BR2, "
+            "Re_c=23000, M=0.2, LSRK45, one probe per candidate")
+
+# DRAM traffic of one launch of the dominant kernel from an ncu capture,
+# per element, valid only for the kernel source it was taken on.
+NCU_TRAFFIC = {
+    # "sha256 of fr_kernels.cuh": {"flux_bytes_per_elem": ..., "grad_bytes_per_elem": ...}
+}
+
+
+def kernel_source_hash():
+    with open(os.path.join(ROOT, "paper_2312_14167_gb300", "csrc", "fr_kernels.cuh"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def physics():
+    return dict(mu=1.0 / RE, p_inf=1.0 / (GAMMA * MACH ** 2), v_inf=(1.0, 0.0))
+
+
+def make_meshes(rank=0):
+    from synth import meshes as M
+    return M.airfoil_batch(N_INST, seed=2312 + rank, e_lo=8000, e_hi=40000, p_geo=P)[:CANDIDATES]
+
+
+def cfl_dt(meshes, cfl=0.4):
+    """Fixed step from a CFL estimate: smallest corner-edge length over
+    (|v| + c) (p+1)^2, the same dt for every candidate."""
+    c = np.sqrt(GAMMA * physics()["p_inf"])
+    hmin = np.inf
+    for m in meshes:
+        X = m.xyz[m.elem_vert]
+        for a, b in ((0, 1), (0, 2), (1, 3), (2, 3)):
+            hmin = min(hmin, np.linalg.norm(X[:, a] - X[:, b], axis=1).min())
+    return cfl * hmin / ((1.0 + c) * (P + 1) ** 2)
+
+
+def initial_state(x, inst, mesh):
+    """Seeded start: free stream with 1 % smooth perturbations, velocity
+    damped to zero within about 0.05 chord of the wall (no impulsive start)."""
+    from synth import states as S
+    u = S.smooth_perturbed(x, 2, MACH, amp=0.01, seed=7 + inst)
+    return S.wall_damped(x, mesh.info["wall_points"], 0.05, u)
+
+
+# --------------------------------------------------------------------------
+# oracle timing (CPU; reference arm and cpu_baseline)
+# --------------------------------------------------------------------------
+
+def oracle_sample_rate(mesh, n_sample, n_steps, dt):
+    """Time the FP64 oracle's LSRK45 stages restricted to a sample of
+    elements of one candidate: returns (updates/s, seconds, sample text)."""
+    from oracle.fr import FRDiscretisation
+    from oracle.physics import NavierStokes
+    ph = physics()
+    disc = FRDiscretisation(mesh, P, NavierStokes(2, gamma=GAMMA, mu=ph["mu"], prandtl=PR, viscous=True,
+                                                  rho_inf=1.0, v_inf=ph["v_inf"], p_inf=ph["p_inf"]))
+    U = initial_state(disc.sol_coords(), 0, mesh)
+    rng = np.random.default_rng(0)
+    elems = np.sort(rng.choice(mesh.n_elem, size=min(n_sample, mesh.n_elem), replace=False))
+    from oracle.timestep import LSRK45_A, LSRK45_B
+    A = [float(a) for a in LSRK45_A]
+    B = [float(b) for b in LSRK45_B]
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        du = np.zeros((elems.size, NSP, V))
+        for s in range(STAGES):
+            R = disc.residual(U, elems)
+            du = A[s] * du + dt * R
+            U[elems] = U[elems] + B[s] * du
+    sec = time.perf_counter() - t0
+    upd = elems.size * NSP * STAGES * n_steps
+    return upd / sec, sec, (f"{elems.size} of {mesh.n_elem} elements of candidate 0 "
+                            f"(their 2-ring neighbourhood evaluated), {n_steps} LSRK45 steps")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    meshes = make_meshes(0)
+    dt = cfl_dt(meshes)
+    # warm-up steps are untimed, then K timed steps of the bounded sample
+    oracle_sample_rate(meshes[0], 64, max(args.warmup, 1), dt)
+    rate, sec, sample = oracle_sample_rate(meshes[0], 64, args.steps, dt)
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------
+# GPU arm
+# --------------------------------------------------------------------------
+
+class Clocks:
+    """nvidia-smi sampling during the timed region (a child process we own)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [c.strip() for c in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def algorithmic_bytes(E, s, kind):
+    """Compulsory DRAM bytes of one launch (the kernel's design, per element):
+    flux: state read+write, RK register write (+read in 4 of 5 stages),
+    metrics, normals, partner indices, the partner's face state, own and
+    partner viscous normal flux, new face state; gradient: state, metrics,
+    normals, partner indices, partner face state, viscous normal flux."""
+    MS = 5
+    if kind == "flux":
+        per = (NSP * V * s * (3 + 0.8) + NSP * MS * s + NFP * 2 * s + NFP * 4 + NFP * V * s
+               + 2 * NFP * V * s + NFP * V * s)
+    else:
+        per = NSP * V * s + NSP * MS * s + NFP * 2 * s + NFP * 4 + NFP * V * s + NFP * V * s
+    return per * E
+
+
+def sampled_parity(fr, meshes, fms, sol, n_sample=48):
+    """Full-size parity on sampled elements of three candidates: FP32 library
+    residual vs the FP64 oracle on the FP32-rounded input (within the forward
+    error bound) and vs the exact input."""
+    from oracle.fr import FRDiscretisation
+    from oracle.physics import NavierStokes
+    ph = physics()
+    out = []
+    eps = 2.0 ** -24
+    for inst in sorted({0, len(fms) // 2, len(fms) - 1}):
+        disc = FRDiscretisation(meshes[inst], P, NavierStokes(2, gamma=GAMMA, mu=ph["mu"], prandtl=PR,
+                                                              viscous=True, rho_inf=1.0,
+                                                              v_inf=ph["v_inf"], p_inf=ph["p_inf"]))
+        u = initial_state(fms[inst].sol_coords(), inst, meshes[inst])
+        sol.set_state(inst, u)
+        Rg = sol.residual(inst)
+        rng = np.random.default_rng(inst)
+        el = np.sort(rng.choice(meshes[inst].n_elem, n_sample, replace=False))
+        el = np.union1d(el, np.arange(min(8, meshes[inst].n_elem)))    # wall/trailing-edge cells
+        u32 = u.astype(np.float32).astype(np.float64)
+        R32, mag = disc.residual(u32, el, magnitude=True)
+        R64 = disc.residual(u, el)
+        e_arith = float(np.linalg.norm(Rg[el] - R32) / np.linalg.norm(R32))
+        bound = float(16 * eps * np.linalg.norm(mag) / np.linalg.norm(R32))
+        e_total = float(np.linalg.norm(Rg[el] - R64) / np.linalg.norm(R64))
+        out.append({"inst": inst, "elements": int(el.size), "rel_l2_vs_oracle_fp32_input": e_arith,
+                    "bound": bound, "rel_l2_vs_oracle_exact_input": e_total,
+                    "pointwise_within_bound": bool(np.all(np.abs(Rg[el] - R32) <= 16 * eps * mag))})
+    return out
+
+
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    meshes = make_meshes(rank)
+    dt = cfl_dt(meshes)
+    cpu_base = None
+    if world == 1 and not args.no_cpu_baseline:
+        # the oracle runs before the first CUDA call of this process
+        rate, sec, sample = oracle_sample_rate(meshes[0], 64, 12, dt)
+        cpu_base = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+                    "seconds": sec}
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2312_14167_gb300 import fr
+    ph = physics()
+    cfg32 = fr.make_config(2, gamma=GAMMA, prandtl=PR, mu=ph["mu"], rho_inf=1.0, v_inf=ph["v_inf"],
+                           p_inf=ph["p_inf"], dt=dt, viscous=True, rk=fr.FR_LSRK45, precision=fr.FR_FP32)
+    cfg64 = fr.make_config(2, gamma=GAMMA, prandtl=PR, mu=ph["mu"], rho_inf=1.0, v_inf=ph["v_inf"],
+                           p_inf=ph["p_inf"], dt=dt, viscous=True, rk=fr.FR_LSRK45, precision=fr.FR_FP64)
+    fms = [fr.Mesh(m, P) for m in meshes]
+    E = sum(m.n_elem for m in fms)
+    sol = fr.Solver(fms, cfg32)
+    states = [initial_state(m.sol_coords(), i, meshes[i]) for i, m in enumerate(fms)]
+    parity = None
+    if rank == 0 and not args.no_parity:
+        parity = sampled_parity(fr, meshes, fms, sol)
+    for i, u in enumerate(states):
+        sol.set_state(i, u)
+    pids = [sol.probe_add(i, meshes[i].info["probe"]) for i in range(len(fms))]
+    st = sol.stream
+    # warm-up (captures the graph), then the timed steps
+    sol.rk_step(args.warmup)
+    sol.synchronize()
+    sol.probe_reset()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clk = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk.start()
+    e0.record(st)
+    sol.rk_step(args.steps)
+    e1.record(st)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    launches = sol.last_launch_count()
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        tot = torch.tensor([float(E)], device="cuda")
+        dist.all_reduce(tot)
+        E_all = tot.item()
+    else:
+        E_all = E
+    upd_all = E_all * NSP * STAGES * args.steps
+    value = upd_all / (ms / 1e3)
+    # observer results of the timed window
+    oaspl = [sol.oaspl([pid], p_ref=2e-5, p_scale=101325.0 / ph["p_inf"], mean_mode=0) for pid in pids[:4]]
+    forces = [list(sol.forces(i)) for i in range(2)]
+    tot, bad = sol.integral(0)
+    # per-kernel times (CUDA events around each launch, no graph)
+    kms, kcnt = sol.profile_steps(3)
+    kinds = ["flux", "grad", "probe", "force", "other"]
+    share = {kinds[k]: float(kms[k] * kcnt[k]) for k in range(5)}
+    dom = max(("flux", "grad"), key=lambda k: share[k])
+    kdx = kinds.index(dom)
+    alg = algorithmic_bytes(E, 4, dom)
+    achieved = alg / (kms[kdx] / 1e3) / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except OSError:
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    traffic = None
+    rec = NCU_TRAFFIC.get(kernel_source_hash())
+    if rec:
+        traffic = rec[f"{dom}_bytes_per_elem"] * E
+    roof = {"bound": "hbm", "kernel": f"k_{dom}<2,4,float>", "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes_per_launch": alg, "launch_ms": float(kms[kdx]),
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800",
+            "stage_ms": float(kms[0] + kms[1]),
+            "kernel_ms": {kinds[k]: float(kms[k]) for k in range(5)}}
+    del sol
+    torch.cuda.empty_cache()
+
+    # end to end through the C ABI: every step uploads the FP64 state of all
+    # candidates from pinned host memory, advances one step and reads the state back
+    sol = fr.Solver(fms, cfg32)
+    pinned = [torch.empty(u.shape, dtype=torch.float64, pin_memory=True).numpy() for u in states]
+    outs = [torch.empty(u.shape, dtype=torch.float64, pin_memory=True).numpy() for u in states]
+    for p_, u in zip(pinned, states):
+        p_[...] = u
+    n_e2e = max(3, min(args.steps, 10))
+    for i, u in enumerate(pinned):
+        sol.set_state(i, u)
+    sol.rk_step(1)
+    sol.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        for i, u in enumerate(pinned):
+            sol.set_state(i, u)
+        sol.rk_step(1)
+        for i in range(len(fms)):
+            outs[i][...] = sol.get_state(i)
+    sol.synchronize()
+    e2e_sec = time.perf_counter() - t0
+    e2e_val = E * NSP * STAGES * n_e2e / e2e_sec * (E_all / E)
+    state_bytes = sum(u.nbytes for u in states)
+    del sol
+    torch.cuda.empty_cache()
+
+    # the plain single-instance FP64 path, candidates one after another
+    n64 = 3
+    t64 = 0.0
+    for i, m in enumerate(fms):
+        s64 = fr.Solver([m], cfg64)
+        s64.set_state(0, states[i])
+        s64.rk_step(1)
+        s64.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(s64.stream)
+        s64.rk_step(n64)
+        b.record(s64.stream)
+        b.synchronize()
+        t64 += a.elapsed_time(b)
+        del s64
+    fp64_val = E * NSP * STAGES * n64 / (t64 / 1e3)
+
+    if dist:
+        dist.barrier()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD if CANDIDATES == N_INST else
+                           WORKLOAD.replace("32 NACA", f"{CANDIDATES} of the 32 NACA"),
+                           "candidates_per_gpu": len(fms), "elements_per_gpu": E,
+                           "sol_pts_per_gpu": E * NSP, "p": P, "dt": dt,
+                           "l2": "inputs larger than L2 (FP32 working set %.2f GB > 129 MB), no flush"
+                                 % (sol_bytes(E) / 1e9)},
+                "roofline": roof,
+                "cpu_baseline": cpu_base,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
+                        "d2h_bytes_per_step": state_bytes,
+                        "how": "per step: fr_set_state of every candidate from pinned FP64 host "
+                               "arrays, fr_rk_step(1), fr_get_state of every candidate"},
+                "gpu_launches": int(launches),
+                "clocks": clocks,
+                "fp64_single_instance": {"value": fp64_val, "unit": UNIT,
+                                         "ratio_mixed_batched_over_fp64": value / world / fp64_val,
+                                         "how": f"FP64 path, one candidate per solver, {n64} steps each, "
+                                                "candidates one after another, device time summed"},
+                "parity": parity,
+                "observers": {"oaspl_db_first4": oaspl, "mean_force_first2": forces,
+                              "state_finite": bool(bad == 0)}}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def sol_bytes(E):
+    s = 4
+    return E * (NSP * V * s * 4 + NFP * V * s * 3 + NSP * 5 * s + NFP * 2 * s + NFP * 4)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--candidates", type=int, default=N_INST)
+    args = ap.parse_args()
+    global CANDIDATES
+    CANDIDATES = max(1, min(N_INST, args.candidates))
+    if args.warmup < 3 and args.impl != "reference":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,193 @@
+/*
+ * fr.h - C ABI of the GB300 (sm_103a) Flux Reconstruction hot path.
+ *
+ * One design evaluation of the aeroacoustic shape-optimisation loop of
+ * Hamedi & Vermeire, "Gradient-Free Aeroacoustic Shape Optimization Using
+ * Large Eddy Simulation" (arXiv:2312.14167): the explicit high-order FR
+ * residual of the compressible Navier-Stokes equations (Sec. 2.1, Eqs. 1-7;
+ * FR discretisation Sec. 2.3) on unstructured quad / hex meshes, explicit
+ * Runge-Kutta time stepping, the observer pressure probe and the OASPL
+ * reduction (Sec. 3.1.2, Eqs. 9-12), with the candidate designs of one MADS
+ * poll (Sec. 2.2, Algorithm 1: all candidates of an iteration evaluated
+ * concurrently) advanced together as a batch on one GPU.
+ *
+ * Conventions shared by every entry point:
+ *  - every call returns an fr_status; nothing aborts or throws across the
+ *    ABI; fr_last_error() returns a message for the calling thread's last
+ *    failure;
+ *  - host arrays belong to the caller and are only read (inputs) or
+ *    written (outputs) during the call;
+ *  - device memory comes only from the caller's workspace (fr_solver_create);
+ *    the library itself never allocates device memory;
+ *  - work is issued on the caller's CUDA stream; calls that return host data
+ *    synchronise that stream before returning;
+ *  - state layout on the host is [element][solution point][variable] in
+ *    FP64, variables [rho, rho*v_x, rho*v_y(, rho*v_z), rho*E];
+ *  - solution points are the tensor product of the p+1 Gauss-Legendre
+ *    points, xi index fastest; element corners in tensor order (xi fastest);
+ *    faces numbered -xi, +xi, -eta, +eta(, -zeta, +zeta).
+ */
+#ifndef FR_H
+#define FR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int fr_status;
+#define FR_OK 0
+#define FR_ERR_INVALID_ARG 1   /* null pointer, out-of-range index or size */
+#define FR_ERR_MESH 2          /* unmatched face, non-positive Jacobian, ... */
+#define FR_ERR_UNSUPPORTED 3   /* p outside 1..4, mixed dims/orders in a batch */
+#define FR_ERR_CUDA 4          /* a CUDA runtime call failed */
+#define FR_ERR_NONFINITE 5     /* NaN/Inf found in the state */
+#define FR_ERR_TIMEOUT 6       /* a bounded device wait gave up */
+#define FR_ERR_WORKSPACE 7     /* workspace too small or misaligned */
+
+/* face tags (fr_mesh_create) */
+#define FR_TAG_INTERIOR 0   /* matched to the face with the same corner vertices */
+#define FR_TAG_PERIODIC 1   /* matched after a +/- periodic shift */
+#define FR_TAG_WALL 2       /* no-slip adiabatic wall (Sec. 3.1.1) */
+#define FR_TAG_FARFIELD 3   /* characteristic (Riemann-invariant) far field */
+#define FR_TAG_INFLOW 4     /* far field with a tanh boundary-layer profile */
+#define FR_TAG_OUTFLOW 5    /* characteristic outflow (same construction) */
+
+#define FR_RK4 0            /* classical 4-stage RK */
+#define FR_LSRK45 1         /* Carpenter-Kennedy 5-stage 4th-order 2N-storage */
+
+#define FR_FP64 0           /* plain FP64 state, geometry and arithmetic */
+#define FR_FP32 1           /* FP32 state/fluxes/contractions; geometry computed in
+                               FP64 then cast; FP64 probe/force/conservation sums */
+
+typedef struct fr_mesh fr_mesh;
+typedef struct fr_solver fr_solver;
+
+/* Physics, scheme and precision of one solver (all instances share it).
+ * Non-dimensional: the caller chooses the reference scales. */
+typedef struct fr_config {
+    double gamma;          /* ratio of specific heats (Sec. 2.1: 1.4) */
+    double prandtl;        /* Prandtl number (Sec. 2.1: 0.71) */
+    double mu;             /* constant dynamic viscosity */
+    double rho_inf;        /* reference (far-field) density */
+    double v_inf[3];       /* reference velocity */
+    double p_inf;          /* reference pressure */
+    double inflow_delta;   /* FR_TAG_INFLOW: v = v_inf tanh(3 (y - ywall)/delta); <= 0: uniform */
+    double inflow_ywall;
+    double br2_eta;        /* BR2 penalty; <= 0 selects the number of element faces */
+    double dt;             /* fixed time step of fr_rk_step */
+    int viscous;           /* 0: Euler, 1: Navier-Stokes (BR2) */
+    int rk;                /* FR_RK4 or FR_LSRK45 */
+    int precision;         /* FR_FP64 or FR_FP32 */
+    int reserved;
+} fr_config;
+
+/* Build one mesh (host, FP64).  The FR discretisation is Huynh's Flux
+ * Reconstruction (Sec. 2.3) with the DG-recovery correction; the mesh
+ * determines solution/flux points, metric terms (adjugate of the Jacobian of
+ * the element map), outward normals scaled by the surface Jacobian and the
+ * partner of every flux point.
+ *  dim            2 (quads) or 3 (hexes)
+ *  p              polynomial degree, 1..4
+ *  xyz            n_vert * dim vertex coordinates
+ *  elem_vert      n_elem * 2^dim corner vertex indices, tensor order
+ *  geo_order      degree q >= 1 of the element map
+ *  geo_nodes      NULL (straight-sided: corners) or n_elem * (q+1)^dim * dim
+ *                 coordinates of the equispaced tensor lattice (xi fastest)
+ *  face_tag       n_elem * 2*dim tags (FR_TAG_*)
+ *  n_shift, periodic_shift  n_shift * dim translation vectors for periodic
+ *                 faces (a periodic face matches the face whose corners equal
+ *                 its own plus or minus one shift)
+ * Errors: FR_ERR_INVALID_ARG, FR_ERR_UNSUPPORTED (p), FR_ERR_MESH (a face
+ * without partner, flux points that do not coincide, J <= 0). */
+fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_vert, const double *xyz,
+                         int64_t n_elem, const int64_t *elem_vert, int geo_order,
+                         const double *geo_nodes, const int32_t *face_tag, int n_shift,
+                         const double *periodic_shift);
+void fr_mesh_destroy(fr_mesh *mesh);
+/* Number of elements, solution points per element and flux points per element. */
+fr_status fr_mesh_info(const fr_mesh *mesh, int64_t *n_elem, int *nsp, int *nfp);
+/* Physical coordinates of all solution points, n_elem * nsp * dim FP64. */
+fr_status fr_mesh_sol_coords(const fr_mesh *mesh, double *xyz);
+
+/* Workspace (device bytes) a solver over these meshes needs; 0 on error. */
+size_t fr_workspace_bytes(fr_mesh *const *meshes, int n_inst, const fr_config *cfg);
+
+/* Create a batch solver: the n_inst meshes (same dim and p) are advanced
+ * together, one element tile table over all of them.  ``workspace`` is a
+ * device buffer of ``ws_bytes`` >= fr_workspace_bytes() aligned to 256 bytes,
+ * owned by the caller and kept alive until fr_solver_destroy; ``stream`` is a
+ * cudaStream_t (NULL: legacy default stream).  Meshes may be destroyed after
+ * this call.  The state starts at zero; call fr_set_state for every instance. */
+fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, int n_inst,
+                           const fr_config *cfg, void *workspace, size_t ws_bytes,
+                           void *stream);
+void fr_solver_destroy(fr_solver *solver);
+
+/* Copy one instance's state (host FP64 [elem][sp][var]) in / out. */
+fr_status fr_set_state(fr_solver *solver, int inst, const double *u);
+fr_status fr_get_state(fr_solver *solver, int inst, double *u);
+
+/* du/dt of the current state of instance ``inst`` at its solution points
+ * (host FP64 [elem][sp][var]): the FR residual of Sec. 2.3 applied to
+ * Eq. 1. */
+fr_status fr_residual(fr_solver *solver, int inst, double *r);
+
+/* Advance every instance by n_steps fixed steps of cfg->dt with cfg->rk,
+ * sampling every probe (and the wall force) after each completed step.  Work
+ * is replayed from a CUDA graph captured on first use.  Asynchronous. */
+fr_status fr_rk_step(fr_solver *solver, int n_steps);
+
+/* Add an observer at physical point x (dim values) of instance ``inst``; the
+ * containing element and reference coordinates are found by Newton's method
+ * on the element maps (FP64).  Returns its id in *probe_id.  The pressure is
+ * computed from the conserved variables interpolated to x (Sec. 3.1.2). */
+fr_status fr_probe_add(fr_solver *solver, int inst, const double *x, int *probe_id);
+/* Pressure at the probe after the last completed step (synchronises). */
+fr_status fr_probe_pressure(fr_solver *solver, int probe_id, double *p_latest);
+/* Start a new averaging window: zero all probe and force accumulators. */
+fr_status fr_probe_reset(fr_solver *solver);
+/* OASPL in dB (Sec. 3.1.2, Eqs. 9-12) over the samples since the last reset:
+ * p_RMS of each listed probe (mean_mode 0: p'_i = p_i - running mean up to
+ * sample i, the literal reading of Eqs. 11-12; mean_mode 1: p'_i = p_i -
+ * window mean), averaged over the probes, OASPL = 20 log10(p_scale p_RMS /
+ * p_ref).  Zero variance gives -inf with FR_OK.  Sums are FP64 and
+ * compensated. */
+fr_status fr_oaspl(fr_solver *solver, const int *probe_ids, int n, double p_ref,
+                   double p_scale, int mean_mode, double *oaspl_db);
+/* Number of samples in the current window and the sample moments of one
+ * probe: out[0] = count, out[1] = mean, out[2] = sum p'^2 (mode 0),
+ * out[3] = sum (p - mean)^2 (mode 1). */
+fr_status fr_probe_stats(fr_solver *solver, int probe_id, double *out4);
+
+/* Time-mean wall force of instance ``inst`` since the last reset (dim
+ * values): sum over wall flux points of w (p n - tau . n) (the force behind
+ * C_D, Sec. 3.1.2), averaged over the completed steps. */
+fr_status fr_forces(fr_solver *solver, int inst, double *mean_force);
+
+/* Conservation check: FP64 compensated sums over the instance of
+ * w_i J_i R_i per variable (zero to round-off on periodic meshes). */
+fr_status fr_conservation(fr_solver *solver, int inst, double *sums);
+/* Integral of the conserved variables over the instance (FP64), and the
+ * number of non-finite state values (all instances) in *n_nonfinite. */
+fr_status fr_integral(fr_solver *solver, int inst, double *sums, int64_t *n_nonfinite);
+
+/* Number of kernel launches issued by the last fr_rk_step call. */
+int64_t fr_last_launch_count(const fr_solver *solver);
+
+/* Profiling: run n_steps steps without graph replay, with CUDA events on the
+ * solver's stream around every launch.  ms[k] = mean duration (ms) of one
+ * launch of kind k and count[k] = launches, for k = 0 fused flux/update
+ * kernel, 1 BR2 gradient kernel, 2 probe kernel, 3 wall-force kernel,
+ * 4 other (5 entries each).  The steps advance the state like fr_rk_step.
+ * Synchronises. */
+fr_status fr_profile_steps(fr_solver *solver, int n_steps, double *ms, int64_t *count);
+
+const char *fr_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FR_H */

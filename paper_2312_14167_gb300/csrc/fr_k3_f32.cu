@@ -1,0 +1,37 @@
+// Kernel instantiations for 3-D elements in float (see fr_kernels.cuh).
+#include "fr_kernels.cuh"
+
+namespace frk {
+
+cudaError_t launch_3_f32(int N, int kind, bool visc, const KArgs<float> &a, int grid, cudaStream_t s) {
+    switch (N) {
+    case 2: return launch_n<3, 2, float>(kind, visc, a, grid, s);
+    case 3: return launch_n<3, 3, float>(kind, visc, a, grid, s);
+    case 4: return launch_n<3, 4, float>(kind, visc, a, grid, s);
+    case 5: return launch_n<3, 5, float>(kind, visc, a, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int N>
+static cudaError_t prepare_n(bool visc) {
+    cudaError_t e;
+    if (visc) e = prep_smem(k_flux<3, N, float, true>, smem_bytes<3, N, float>(K_FLUX, true));
+    else e = prep_smem(k_flux<3, N, float, false>, smem_bytes<3, N, float>(K_FLUX, false));
+    if (e != cudaSuccess) return e;
+    e = prep_smem(k_grad<3, N, float>, smem_bytes<3, N, float>(K_GRAD, true));
+    if (e != cudaSuccess) return e;
+    return prep_smem(k_interp<3, N, float>, smem_bytes<3, N, float>(K_INTERP, false));
+}
+
+cudaError_t prepare_3_f32(int N, bool visc) {
+    switch (N) {
+    case 2: return prepare_n<2>(visc);
+    case 3: return prepare_n<3>(visc);
+    case 4: return prepare_n<4>(visc);
+    case 5: return prepare_n<5>(visc);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace frk

@@ -1,0 +1,1104 @@
+// FR residual + explicit RK kernels for sm_103a (GB300).
+//
+// Method (arXiv:2312.14167): compressible Navier-Stokes (Sec. 2.1, Eqs. 1-7)
+// discretised with Huynh's Flux Reconstruction (Sec. 2.3), DG-recovery
+// correction on tensor Gauss-Legendre points, Rusanov inviscid interface flux,
+// BR2 viscous interface flux; explicit RK4 / LSRK45 in time.
+//
+// Design (one GPU, HBM-bound):
+//  * element-blocked layout: every per-element array is [elem][point][var],
+//    so a CTA's tile of NE consecutive elements is one contiguous chunk
+//    staged into shared memory with 128-bit loads;
+//  * sum-factorised 1-D operators along lines of n = p+1 points (the dense
+//    per-element operators are Kronecker products; applying them line by
+//    line costs n flops per point instead of n^d);
+//  * one fused kernel per RK stage does: own face values by interpolation,
+//    partner face values by a gather through the precomputed partner index,
+//    Rusanov + BR2 common fluxes, transformed flux at solution points
+//    (with the corrected gradient for viscous flows), divergence +
+//    correction, the RK register update, and the face values of the new
+//    state (written to the other half of a ping-pong buffer);
+//  * viscous flows add one kernel per stage that computes the BR2 face
+//    gradient and the own-side viscous normal flux at every flux point;
+//  * FP64 (plain) and FP32 (mixed) are the same templates; geometry arrives
+//    already cast from the FP64 host computation.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace frk {
+
+constexpr int kMaxN = 5;
+
+enum Kind : int {
+    K_FLUX = 0,      // fused common flux / divergence / RK update
+    K_GRAD = 1,      // BR2 face gradient + viscous normal flux (+ wall force)
+    K_INTERP = 2,    // face values of the current state (prologue)
+    K_PROBE = 3,     // observer sampling + FP64 accumulators
+    K_INTEGRAL = 4,  // per-block FP64 partial sums
+    K_REDUCE = 5,    // ordered compensated reduction of the partials
+    K_TO_REAL = 6,   // FP64 staging -> state
+    K_TO_F64 = 7,    // state/residual -> FP64 staging
+};
+
+enum Mode : int {
+    M_LSRK_FIRST = 0,  // dU = dt R; u += B dU
+    M_LSRK = 1,        // dU = A dU + dt R; u += B dU
+    M_RK4_1 = 2,       // R1 = u; R2 = R; u = u + c R
+    M_RK4_2 = 3,       // R2 += 2 R; u = R1 + c R
+    M_RK4_3 = 4,       // (same as M_RK4_2, c = dt)
+    M_RK4_4 = 5,       // u = R1 + c (R2 + R)
+    M_RESIDUAL = 6,    // RES = R
+    M_RESIDUAL_J = 7,  // RES = J R (= -divergence)
+};
+
+enum BcTag : int { BC_WALL = 2, BC_FARFIELD = 3, BC_INFLOW = 4, BC_OUTFLOW = 5 };
+
+struct ProbeDesc {
+    int64_t elem;      // global element index
+    int32_t inst, pad;
+    double w[125];     // tensor Lagrange weights of the solution points
+};
+
+struct ProbeAcc {      // FP64 accumulators of one observer
+    double count;
+    double sum, sum_c;         // running sum of p (Neumaier)
+    double sq0, sq0_c;         // sum of (p_i - running mean_i)^2 (Neumaier)
+    double mean, m2, m2_c;     // Welford window moments
+    double last;
+    double pad[7];
+};
+
+template <typename real>
+struct KArgs {
+    int64_t n_elem;            // elements (or list entries) in the launch
+    int64_t elem0;             // first element of the launch range
+    const int32_t *elist;      // optional element list (force sampling)
+    real *U, *R1, *R2, *RES;
+    const real *UFin;
+    real *UFout;
+    real *FV;
+    const real *MET;           // [E][NSP][D*D+1]: S[k][j] = J dxi_k/dx_j, then 1/J
+    const real *NRM;           // [E][NFP][D] outward normal * |dS|
+    const int32_t *PART;       // [E][NFP] partner flux point, or -1-b (boundary b)
+    const int32_t *BTAG;       // [nb] boundary tag
+    const real *BVREF;         // [nb][D] reference velocity at boundary points
+    const int32_t *EINST;      // [E] instance of each element
+    // physics
+    real gamma, prandtl, mu, eta, rho_inf, p_inf;
+    // stage
+    int mode, force;
+    real rk_a, rk_b, rk_c, dt;
+    // auxiliaries
+    const ProbeDesc *probes;
+    ProbeAcc *pacc;
+    int n_probe;
+    double *force_acc;         // [n_inst][3]
+    const double *stage64;     // FP64 staging in
+    double *stage64_out;       // FP64 staging out
+    double *partials;          // [blocks][2*V + 1]
+    double *reduce_out;        // [2*V + 1]
+    int64_t n_partials;
+    int integral_src;          // 0: integral of U, 1: sum of w * RES
+    // reference-element operators (1-D), FP64 master copies
+    double opD1[kMaxN * kMaxN];   // D1[i][m] = l_m'(xi_i)
+    double opL[2 * kMaxN];        // l_m(-1), l_m(+1)
+    double opGL[kMaxN], opGR[kMaxN];  // g_L'(xi_i), g_R'(xi_i)
+    double opW[kMaxN];            // Gauss weights
+};
+
+// --------------------------------------------------------------------------
+// index helpers
+// --------------------------------------------------------------------------
+// shared-memory regions are padded to multiples of 4 values (16 B in FP32,
+// 32 B in FP64) so that every region can take 128-bit accesses
+__host__ __device__ constexpr int pad4(int n) { return (n + 3) / 4 * 4; }
+
+template <int D, int N>
+struct Geo {
+    static constexpr int NSP = D == 2 ? N * N : N * N * N;
+    static constexpr int NFPF = D == 2 ? N : N * N;
+    static constexpr int NFP = 2 * D * NFPF;
+    static constexpr int V = D + 2;
+    static constexpr int MS = D * D + 1;
+    // elements per CTA: about 256 threads of one solution point each
+    static constexpr int NE = (256 / NSP) > 0 ? (256 / NSP) : 1;
+    static constexpr int THREADS = ((NE * NSP + 31) / 32) * 32;
+
+    __device__ __forceinline__ static int stride(int k) { return k == 0 ? 1 : (k == 1 ? N : N * N); }
+    __device__ __forceinline__ static int digit(int s, int k) { return (s / stride(k)) % N; }
+    // flux point at the end (side 0: -1, 1: +1) of the k-line through s
+    __device__ __forceinline__ static int fp_of(int s, int k, int side) {
+        int l;
+        if (D == 2) {
+            l = digit(s, 1 - k);
+        } else {
+            const int a = (k == 0) ? 1 : 0, b = (k == 2) ? 1 : 2;
+            l = digit(s, a) + N * digit(s, b);
+        }
+        return (2 * k + side) * NFPF + l;
+    }
+    // first solution point of the line of flux point f, direction and side
+    __device__ __forceinline__ static int line_base(int f, int &k, int &side) {
+        const int face = f / NFPF, l = f % NFPF;
+        k = face >> 1;
+        side = face & 1;
+        if (D == 2) return l * stride(1 - k);
+        const int a = (k == 0) ? 1 : 0, b = (k == 2) ? 1 : 2;
+        return (l % N) * stride(a) + (l / N) * stride(b);
+    }
+};
+
+// --------------------------------------------------------------------------
+// physics (Sec. 2.1)
+// --------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ real rsqrt_(real x) { return real(1) / sqrt(x); }
+
+template <int D, typename real>
+__device__ __forceinline__ void primitives(const real *u, real gm1, real &rho, real *vel, real &p) {
+    rho = u[0];
+    const real ir = real(1) / rho;
+    real ke = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        vel[i] = u[1 + i] * ir;
+        ke += vel[i] * u[1 + i];
+    }
+    p = gm1 * (u[D + 1] - real(0.5) * ke);
+}
+
+// normal inviscid flux F(u) . n (n not normalised)
+template <int D, typename real>
+__device__ __forceinline__ void flux_normal(const real *u, const real *n, real gm1, real *F,
+                                            real &vn, real &c2, real gamma) {
+    real rho, vel[D], p;
+    primitives<D>(u, gm1, rho, vel, p);
+    vn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) vn += vel[j] * n[j];
+    F[0] = u[0] * vn;
+#pragma unroll
+    for (int i = 0; i < D; ++i) F[1 + i] = u[1 + i] * vn + p * n[i];
+    F[D + 1] = (u[D + 1] + p) * vn;
+    c2 = gamma * p / rho;
+}
+
+template <int D, typename real>
+__device__ __forceinline__ void rusanov(const real *uL, const real *uR, const real *n,
+                                        real gamma, real *F) {
+    constexpr int V = D + 2;
+    const real gm1 = gamma - real(1);
+    real nn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn += n[j] * n[j];
+    const real nm = sqrt(nn);
+    real FL[V], FR[V], vnL, vnR, c2L, c2R;
+    flux_normal<D>(uL, n, gm1, FL, vnL, c2L, gamma);
+    flux_normal<D>(uR, n, gm1, FR, vnR, c2R, gamma);
+    const real lam = fmax(fabs(vnL) / nm + sqrt(c2L), fabs(vnR) / nm + sqrt(c2R));
+#pragma unroll
+    for (int v = 0; v < V; ++v) F[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * (lam * nm) * (uR[v] - uL[v]);
+}
+
+// inviscid flux F_j, j = 0..D-1
+template <int D, typename real>
+__device__ __forceinline__ void flux_inv(const real *u, real gm1, real (*F)[D + 2]) {
+    real rho, vel[D], p;
+    primitives<D>(u, gm1, rho, vel, p);
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        F[j][0] = u[1 + j];
+#pragma unroll
+        for (int i = 0; i < D; ++i) F[j][1 + i] = u[1 + i] * vel[j] + (i == j ? p : real(0));
+        F[j][D + 1] = vel[j] * (u[D + 1] + p);
+    }
+}
+
+// viscous flux F_vis,j = [0, tau_ij, v_i tau_ij - q_j]; grad[j][v] = d u_v / d x_j
+template <int D, typename real>
+__device__ __forceinline__ void flux_vis(const real *u, const real (*grad)[D + 2], real gamma,
+                                         real mu, real prandtl, real (*F)[D + 2]) {
+    const real rho = u[0], ir = real(1) / rho;
+    real vel[D];
+#pragma unroll
+    for (int i = 0; i < D; ++i) vel[i] = u[1 + i] * ir;
+    const real Es = u[D + 1] * ir;
+    real gv[D][D];   // gv[j][i] = d v_i / d x_j
+    real gE[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const real gr = grad[j][0];
+#pragma unroll
+        for (int i = 0; i < D; ++i) gv[j][i] = (grad[j][1 + i] - gr * vel[i]) * ir;
+        gE[j] = (grad[j][D + 1] - gr * Es) * ir;
+    }
+    real div = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) div += gv[i][i];
+    const real kq = mu / prandtl * gamma;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        F[j][0] = 0;
+        real work = 0;
+#pragma unroll
+        for (int i = 0; i < D; ++i) {
+            const real tau = mu * (gv[j][i] + gv[i][j] - (i == j ? real(2.0 / 3.0) * div : real(0)));
+            F[j][1 + i] = tau;
+            work += vel[i] * tau;
+        }
+        real vdv = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) vdv += vel[k] * gv[j][k];
+        // -q_j = (mu/Pr) d/dx_j (E + p/rho - v.v/2) = (mu/Pr) gamma (dE/dx_j - v_k dv_k/dx_j)
+        F[j][D + 1] = work + kq * (gE[j] - vdv);
+    }
+}
+
+// boundary states: ghost for the inviscid flux, state for gradients
+template <int D, typename real>
+__device__ __forceinline__ void bc_states(int tag, const real *uL, const real *n, const real *vref,
+                                          real gamma, real rho_inf, real p_inf, real *ug, real *ub) {
+    constexpr int V = D + 2;
+    const real gm1 = gamma - real(1);
+    real nn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn += n[j] * n[j];
+    const real inm = rsqrt_(nn);
+    real nh[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) nh[j] = n[j] * inm;
+    if (tag == BC_WALL) {
+        real mn = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) mn += uL[1 + j] * nh[j];
+        ug[0] = uL[0];
+#pragma unroll
+        for (int j = 0; j < D; ++j) ug[1 + j] = uL[1 + j] - real(2) * mn * nh[j];
+        ug[V - 1] = uL[V - 1];
+        real rho, vel[D], p;
+        primitives<D>(uL, gm1, rho, vel, p);
+        ub[0] = rho;
+#pragma unroll
+        for (int j = 0; j < D; ++j) ub[1 + j] = 0;
+        ub[V - 1] = p / gm1;
+        return;
+    }
+    real rL, vL[D], pL;
+    primitives<D>(uL, gm1, rL, vL, pL);
+    const real cL = sqrt(gamma * pL / rL);
+    const real cinf = sqrt(gamma * p_inf / rho_inf);
+    real vnL = 0, vnr = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        vnL += vL[j] * nh[j];
+        vnr += vref[j] * nh[j];
+    }
+    const real Rp = vnL + real(2) * cL / gm1;
+    const real Rm = vnr - real(2) * cinf / gm1;
+    const real vnb = real(0.5) * (Rp + Rm);
+    const real cb = real(0.25) * gm1 * (Rp - Rm);
+    const bool out = vnb > real(0);
+    const real s = out ? pL / pow(rL, gamma) : p_inf / pow(rho_inf, gamma);
+    real vb[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) vb[j] = (out ? vL[j] - vnL * nh[j] : vref[j] - vnr * nh[j]) + vnb * nh[j];
+    const real rb = pow(cb * cb / (gamma * s), real(1) / gm1);
+    const real pb = rb * cb * cb / gamma;
+    real ke = 0;
+    ub[0] = rb;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        ub[1 + j] = rb * vb[j];
+        ke += vb[j] * vb[j];
+    }
+    ub[V - 1] = pb / gm1 + real(0.5) * rb * ke;
+#pragma unroll
+    for (int v = 0; v < V; ++v) ug[v] = ub[v];
+}
+
+// --------------------------------------------------------------------------
+// shared-memory staging helpers
+// --------------------------------------------------------------------------
+template <typename real>
+__device__ __forceinline__ void load_ops(const KArgs<real> &a, real *sOp, int N) {
+    // layout: D1[N*N] | L[2N] | GL[N] | GR[N]
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) sOp[i] = (real)a.opD1[(i / N) * kMaxN + (i % N)];
+    for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) sOp[N * N + i] = (real)a.opL[(i / N) * kMaxN + (i % N)];
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        sOp[N * N + 2 * N + i] = (real)a.opGL[i];
+        sOp[N * N + 3 * N + i] = (real)a.opGR[i];
+    }
+}
+
+// copy a tile of ne elements, each `per` contiguous values, into shared memory
+template <typename real>
+__device__ __forceinline__ void load_tile(real *dst, const real *src, const int32_t *elist,
+                                          int64_t e0, int ne, int per) {
+    if (!elist) {
+        const real *g = src + e0 * per;
+        const int total = ne * per;
+        const bool a16 = ((reinterpret_cast<uintptr_t>(g) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0;
+        if (sizeof(real) == 4 && (per % 4) == 0 && a16) {
+            const float4 *g4 = reinterpret_cast<const float4 *>(g);
+            float4 *d4 = reinterpret_cast<float4 *>(dst);
+            for (int i = threadIdx.x; i < total / 4; i += blockDim.x) d4[i] = __ldg(g4 + i);
+        } else if (sizeof(real) == 8 && (per % 2) == 0 && a16) {
+            const double2 *g2 = reinterpret_cast<const double2 *>(g);
+            double2 *d2 = reinterpret_cast<double2 *>(dst);
+            for (int i = threadIdx.x; i < total / 2; i += blockDim.x) d2[i] = __ldg(g2 + i);
+        } else {
+            for (int i = threadIdx.x; i < total; i += blockDim.x) dst[i] = g[i];
+        }
+        return;
+    }
+    for (int i = threadIdx.x; i < ne * per; i += blockDim.x) {
+        const int j = i / per, r = i % per;
+        dst[i] = src[(int64_t)elist[e0 + j] * per + r];
+    }
+}
+
+template <typename real>
+__device__ __forceinline__ int64_t elem_of(const int32_t *elist, int64_t e0, int j) {
+    return elist ? (int64_t)elist[e0 + j] : e0 + j;
+}
+
+// --------------------------------------------------------------------------
+// K_GRAD: BR2 face gradient Q = interp((1/J) S^T D u) + eta r_f and the
+// viscous normal flux at every flux point (own side on connected points, the
+// common flux on boundary points).  With a.force != 0 it runs over the wall
+// element list and accumulates the wall force instead.
+// --------------------------------------------------------------------------
+template <int D, int N, typename real>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS)
+k_grad(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sOp = reinterpret_cast<real *>(smem_raw);
+    real *sU = sOp + pad4(N * N + 4 * N);
+    real *sM = sU + pad4(NE * NSP * V);
+    real *sD = sM + pad4(NE * NSP * MS);
+    real *sB = sD + pad4(NE * NFP * V);
+    real *sGD = sB + pad4(NE * NFP * V);
+    const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N;
+
+    const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
+    const int64_t e_end = a.elem0 + a.n_elem;
+    if (e0 >= e_end) return;
+    const int ne = (int)min((int64_t)NE, e_end - e0);
+    load_ops(a, sOp, N);
+    load_tile(sU, a.U, a.elist, e0, ne, NSP * V);
+    load_tile(sM, a.MET, a.elist, e0, ne, NSP * MS);
+    __syncthreads();
+
+    // face phase: jumps u_c - u_f and the state used in the viscous flux
+    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+        const int j = w / NFP, f = w % NFP;
+        const int64_t e = elem_of<real>(a.elist, e0, j);
+        int k, side;
+        const int base = G::line_base(f, k, side);
+        const int st = G::stride(k);
+        const real *L = side ? Lp : Lm;
+        real uL[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) uL[v] = 0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const real c = L[m];
+            const real *src = sU + (j * NSP + base + m * st) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) uL[v] += c * src[v];
+        }
+        const int32_t pt = a.PART[e * NFP + f];
+        real uc[V], ub[V];
+        if (pt >= 0) {
+            const real *src = a.UFin + (int64_t)pt * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                uc[v] = real(0.5) * (uL[v] + src[v]);
+                ub[v] = uL[v];
+            }
+        } else {
+            const int b = -1 - pt;
+            real n[D], vref[D], ug[V];
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                n[d] = a.NRM[(e * NFP + f) * D + d];
+                vref[d] = a.BVREF[(int64_t)b * D + d];
+            }
+            bc_states<D>(a.BTAG[b], uL, n, vref, a.gamma, a.rho_inf, a.p_inf, ug, ub);
+#pragma unroll
+            for (int v = 0; v < V; ++v) uc[v] = ub[v];
+        }
+        real *dD = sD + (j * NFP + f) * V;
+        real *dB = sB + (j * NFP + f) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            dD[v] = uc[v] - uL[v];
+            dB[v] = ub[v];
+        }
+    }
+    // solution-point phase: uncorrected physical gradient (1/J) S^T D u
+    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+        const int j = w / NSP, s = w % NSP;
+        const real *M = sM + (j * NSP + s) * MS;
+        const real iJ = M[D * D];
+        real Gk[D][V];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int ik = G::digit(s, k), st = G::stride(k);
+            const real *row = D1 + ik * N;
+            const real *src = sU + (j * NSP + s - ik * st) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) Gk[k][v] = 0;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                const real c = row[m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) Gk[k][v] += c * src[m * st * V + v];
+            }
+        }
+        real *dst = sGD + (j * NSP + s) * D * V;
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                real g = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) g += M[k * D + jd] * Gk[k][v];
+                dst[jd * V + v] = g * iJ;
+            }
+    }
+    __syncthreads();
+    // face phase: Q and the viscous normal flux
+    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+        const int j = w / NFP, f = w % NFP;
+        const int64_t e = elem_of<real>(a.elist, e0, j);
+        int k, side;
+        const int base = G::line_base(f, k, side);
+        const int st = G::stride(k);
+        const real *L = side ? Lp : Lm;
+        const real *Gs = side ? GR : GL;
+        real Q[D][V], lf[D];
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd) {
+            lf[jd] = 0;
+#pragma unroll
+            for (int v = 0; v < V; ++v) Q[jd][v] = 0;
+        }
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const int sp = base + m * st;
+            const real c = L[m];
+            const real *gd = sGD + (j * NSP + sp) * D * V;
+            const real *M = sM + (j * NSP + sp) * MS;
+            const real cg = c * Gs[m] * M[D * D];
+#pragma unroll
+            for (int jd = 0; jd < D; ++jd) {
+                lf[jd] += cg * M[k * D + jd];
+#pragma unroll
+                for (int v = 0; v < V; ++v) Q[jd][v] += c * gd[jd * V + v];
+            }
+        }
+        const real *dD = sD + (j * NFP + f) * V;
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd)
+#pragma unroll
+            for (int v = 0; v < V; ++v) Q[jd][v] += a.eta * lf[jd] * dD[v];
+        const real *ub = sB + (j * NFP + f) * V;
+        real Fv[D][V];
+        flux_vis<D>(ub, Q, a.gamma, a.mu, a.prandtl, Fv);
+        real n[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) n[d] = a.NRM[(e * NFP + f) * D + d];
+        real fvn[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            real t = 0;
+#pragma unroll
+            for (int d = 0; d < D; ++d) t += Fv[d][v] * n[d];
+            fvn[v] = t;
+        }
+        const int32_t pt = a.PART[e * NFP + f];
+        const bool wall = pt < 0 && a.BTAG[-1 - pt] == BC_WALL;
+        if (wall) fvn[V - 1] = 0;
+        if (!a.force) {
+            real *dst = a.FV + (e * NFP + f) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) dst[v] = fvn[v];
+        } else if (wall) {
+            // face quadrature weight: product of the free directions' weights
+            const int l = f % G::NFPF;
+            const double wf = (D == 2) ? a.opW[l] : a.opW[l % N] * a.opW[l / N];
+            real rho, vel[D], p;
+            primitives<D>(ub, a.gamma - real(1), rho, vel, p);
+            const int inst = a.EINST[e];
+#pragma unroll
+            for (int d = 0; d < D; ++d)
+                atomicAdd(&a.force_acc[inst * 3 + d], wf * ((double)p * (double)n[d] - (double)fvn[1 + d]));
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// K_FLUX: fused common flux + transformed flux + divergence/correction + RK
+// --------------------------------------------------------------------------
+template <int D, int N, typename real, bool VISC>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS)
+k_flux(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sOp = reinterpret_cast<real *>(smem_raw);
+    real *sU = sOp + pad4(N * N + 4 * N);
+    real *sM = sU + pad4(NE * NSP * V);
+    real *sC = sM + pad4(NE * NSP * MS);
+    real *sD = sC + pad4(NE * NFP * V);
+    real *sF = sD + (VISC ? pad4(NE * NFP * V) : 0);
+    const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N;
+
+    const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
+    const int64_t e_end = a.elem0 + a.n_elem;
+    if (e0 >= e_end) return;
+    const int ne = (int)min((int64_t)NE, e_end - e0);
+    load_ops(a, sOp, N);
+    load_tile(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP * V);
+    load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
+    __syncthreads();
+
+    // 1) common normal flux at every own flux point
+    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+        const int j = w / NFP, f = w % NFP;
+        const int64_t e = e0 + j;
+        int k, side;
+        const int base = G::line_base(f, k, side);
+        const int st = G::stride(k);
+        const real *L = side ? Lp : Lm;
+        real uL[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) uL[v] = 0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const real c = L[m];
+            const real *src = sU + (j * NSP + base + m * st) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) uL[v] += c * src[v];
+        }
+        real n[D];
+#pragma unroll
+        for (int d = 0; d < D; ++d) n[d] = a.NRM[(e * NFP + f) * D + d];
+        const int32_t pt = a.PART[e * NFP + f];
+        real uR[V], ub[V];
+        if (pt >= 0) {
+            const real *src = a.UFin + (int64_t)pt * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) uR[v] = src[v];
+        } else {
+            const int b = -1 - pt;
+            real vref[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d];
+            bc_states<D>(a.BTAG[b], uL, n, vref, a.gamma, a.rho_inf, a.p_inf, uR, ub);
+        }
+        real Fs[V];
+        rusanov<D>(uL, uR, n, a.gamma, Fs);
+        if (VISC) {
+            const real *fo = a.FV + (e * NFP + f) * V;
+            real *dD = sD + (j * NFP + f) * V;
+            if (pt >= 0) {
+                const real *fp = a.FV + (int64_t)pt * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    Fs[v] -= real(0.5) * (fo[v] - fp[v]);
+                    dD[v] = real(0.5) * (uL[v] + uR[v]) - uL[v];
+                }
+            } else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    Fs[v] -= fo[v];
+                    dD[v] = ub[v] - uL[v];
+                }
+            }
+        }
+        real *dC = sC + (j * NFP + f) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) dC[v] = Fs[v];
+    }
+    if (VISC) __syncthreads();
+
+    // 2) transformed flux at the solution points
+    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+        const int j = w / NSP, s = w % NSP;
+        const real *M = sM + (j * NSP + s) * MS;
+        const real *u = sU + (j * NSP + s) * V;
+        real uu[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) uu[v] = u[v];
+        real F[D][V];
+        flux_inv<D>(uu, a.gamma - real(1), F);
+        if (VISC) {
+            const real iJ = M[D * D];
+            real Gk[D][V];
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                const int ik = G::digit(s, k), st = G::stride(k);
+                const real *row = D1 + ik * N;
+                const real *src = sU + (j * NSP + s - ik * st) * V;
+                const real *dm = sD + (j * NFP + G::fp_of(s, k, 0)) * V;
+                const real *dp = sD + (j * NFP + G::fp_of(s, k, 1)) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) Gk[k][v] = GL[ik] * dm[v] + GR[ik] * dp[v];
+#pragma unroll
+                for (int m = 0; m < N; ++m) {
+                    const real c = row[m];
+#pragma unroll
+                    for (int v = 0; v < V; ++v) Gk[k][v] += c * src[m * st * V + v];
+                }
+            }
+            real gr[D][V];
+#pragma unroll
+            for (int jd = 0; jd < D; ++jd)
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    real g = 0;
+#pragma unroll
+                    for (int k = 0; k < D; ++k) g += M[k * D + jd] * Gk[k][v];
+                    gr[jd][v] = g * iJ;
+                }
+            real Fv[D][V];
+            flux_vis<D>(uu, gr, a.gamma, a.mu, a.prandtl, Fv);
+#pragma unroll
+            for (int jd = 0; jd < D; ++jd)
+#pragma unroll
+                for (int v = 0; v < V; ++v) F[jd][v] -= Fv[jd][v];
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            real *dst = sF + ((j * D + k) * NSP + s) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                real t = 0;
+#pragma unroll
+                for (int jd = 0; jd < D; ++jd) t += M[k * D + jd] * F[jd][v];
+                dst[v] = t;
+            }
+        }
+    }
+    __syncthreads();
+
+    // 3) jump = common - discontinuous normal flux (flux polynomial at the face)
+    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+        const int j = w / NFP, f = w % NFP;
+        int k, side;
+        const int base = G::line_base(f, k, side);
+        const int st = G::stride(k);
+        const real *L = side ? Lp : Lm;
+        real fd[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) fd[v] = 0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const real c = L[m];
+            const real *src = sF + ((j * D + k) * NSP + base + m * st) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) fd[v] += c * src[v];
+        }
+        real *dC = sC + (j * NFP + f) * V;
+        if (side) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) dC[v] -= fd[v];
+        } else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) dC[v] += fd[v];
+        }
+    }
+    __syncthreads();
+
+    // 4) divergence + correction, residual, RK update
+    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+        const int j = w / NSP, s = w % NSP;
+        const int64_t e = e0 + j;
+        real div[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) div[v] = 0;
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int ik = G::digit(s, k), st = G::stride(k);
+            const real *row = D1 + ik * N;
+            const real *src = sF + ((j * D + k) * NSP + s - ik * st) * V;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                const real c = row[m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) div[v] += c * src[m * st * V + v];
+            }
+            const real *jm = sC + (j * NFP + G::fp_of(s, k, 0)) * V;
+            const real *jp = sC + (j * NFP + G::fp_of(s, k, 1)) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) div[v] += GR[ik] * jp[v] - GL[ik] * jm[v];
+        }
+        const real iJ = sM[(j * NSP + s) * MS + D * D];
+        const int64_t g = (e * NSP + s) * V;
+        real *su = sU + (j * NSP + s) * V;
+        switch (a.mode) {
+        case M_LSRK_FIRST:
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const real R = -div[v] * iJ;
+                const real dU = a.dt * R;
+                a.R1[g + v] = dU;
+                const real un = su[v] + a.rk_b * dU;
+                a.U[g + v] = un;
+                su[v] = un;
+            }
+            break;
+        case M_LSRK:
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const real R = -div[v] * iJ;
+                const real dU = a.rk_a * a.R1[g + v] + a.dt * R;
+                a.R1[g + v] = dU;
+                const real un = su[v] + a.rk_b * dU;
+                a.U[g + v] = un;
+                su[v] = un;
+            }
+            break;
+        case M_RK4_1:
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const real R = -div[v] * iJ;
+                a.R1[g + v] = su[v];
+                a.R2[g + v] = R;
+                const real un = su[v] + a.rk_c * R;
+                a.U[g + v] = un;
+                su[v] = un;
+            }
+            break;
+        case M_RK4_2:
+        case M_RK4_3:
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const real R = -div[v] * iJ;
+                a.R2[g + v] = a.R2[g + v] + real(2) * R;
+                const real un = a.R1[g + v] + a.rk_c * R;
+                a.U[g + v] = un;
+                su[v] = un;
+            }
+            break;
+        case M_RK4_4:
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                const real R = -div[v] * iJ;
+                const real un = a.R1[g + v] + a.rk_c * (a.R2[g + v] + R);
+                a.U[g + v] = un;
+                su[v] = un;
+            }
+            break;
+        case M_RESIDUAL:
+#pragma unroll
+            for (int v = 0; v < V; ++v) a.RES[g + v] = -div[v] * iJ;
+            break;
+        default:  // M_RESIDUAL_J
+#pragma unroll
+            for (int v = 0; v < V; ++v) a.RES[g + v] = -div[v];
+            break;
+        }
+    }
+    if (a.mode == M_RESIDUAL || a.mode == M_RESIDUAL_J) return;
+    __syncthreads();
+
+    // 5) face values of the new state for the next stage
+    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+        const int j = w / NFP, f = w % NFP;
+        int k, side;
+        const int base = G::line_base(f, k, side);
+        const int st = G::stride(k);
+        const real *L = side ? Lp : Lm;
+        real uf[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) uf[v] = 0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const real c = L[m];
+            const real *src = sU + (j * NSP + base + m * st) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) uf[v] += c * src[v];
+        }
+        real *dst = a.UFout + ((e0 + j) * NFP + f) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) dst[v] = uf[v];
+    }
+}
+
+// --------------------------------------------------------------------------
+// K_INTERP: face values of the current state (after fr_set_state)
+// --------------------------------------------------------------------------
+template <int D, int N, typename real>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS)
+k_interp(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, NE = G::NE;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sOp = reinterpret_cast<real *>(smem_raw);
+    real *sU = sOp + pad4(N * N + 4 * N);
+    const real *Lm = sOp + N * N, *Lp = Lm + N;
+    const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
+    const int64_t e_end = a.elem0 + a.n_elem;
+    if (e0 >= e_end) return;
+    const int ne = (int)min((int64_t)NE, e_end - e0);
+    load_ops(a, sOp, N);
+    load_tile(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP * V);
+    __syncthreads();
+    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+        const int j = w / NFP, f = w % NFP;
+        int k, side;
+        const int base = G::line_base(f, k, side);
+        const int st = G::stride(k);
+        const real *L = side ? Lp : Lm;
+        real uf[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) uf[v] = 0;
+#pragma unroll
+        for (int m = 0; m < N; ++m) {
+            const real c = L[m];
+            const real *src = sU + (j * NSP + base + m * st) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) uf[v] += c * src[v];
+        }
+        real *dst = a.UFout + ((e0 + j) * NFP + f) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) dst[v] = uf[v];
+    }
+}
+
+// --------------------------------------------------------------------------
+// K_PROBE: one warp per observer; FP64 interpolation of the conserved
+// variables, pressure, compensated running moments (Sec. 3.1.2).
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void neumaier_add(double &s, double &c, double x) {
+    const double t = s + x;
+    if (fabs(s) >= fabs(x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+}
+
+template <int D, int N, typename real>
+__global__ void k_probe(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, V = G::V;
+    const int lane = threadIdx.x & 31;
+    const int pr = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (pr >= a.n_probe) return;
+    const ProbeDesc &P = a.probes[pr];
+    double u[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) u[v] = 0.0;
+    for (int s = lane; s < NSP; s += 32) {
+        const double w = P.w[s];
+        const real *src = a.U + (P.elem * NSP + s) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] += w * (double)src[v];
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u[v] += __shfl_xor_sync(0xffffffffu, u[v], o);
+    if (lane != 0) return;
+    double ke = 0.0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) ke += u[1 + i] * u[1 + i];
+    const double p = ((double)a.gamma - 1.0) * (u[V - 1] - 0.5 * ke / u[0]);
+    ProbeAcc &A = a.pacc[pr];
+    const double n = A.count + 1.0;
+    A.count = n;
+    neumaier_add(A.sum, A.sum_c, p);
+    const double pbar = (A.sum + A.sum_c) / n;
+    const double d = p - pbar;
+    neumaier_add(A.sq0, A.sq0_c, d * d);
+    const double delta = p - A.mean;
+    A.mean += delta / n;
+    neumaier_add(A.m2, A.m2_c, delta * (p - A.mean));
+    A.last = p;
+}
+
+// --------------------------------------------------------------------------
+// K_INTEGRAL / K_REDUCE: FP64 sums over an element range, per block, then an
+// ordered compensated reduction (deterministic).  Slot layout per block:
+// [0, V): sum, [V, 2V): compensation, [2V]: count of non-finite values.
+// --------------------------------------------------------------------------
+template <int D, int N, typename real>
+__global__ void k_integral(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, V = G::V, MS = G::MS;
+    __shared__ double red[32][V + 1];
+    double acc[V];
+    double bad = 0.0;
+#pragma unroll
+    for (int v = 0; v < V; ++v) acc[v] = 0.0;
+    const int64_t total = a.n_elem * NSP;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = a.elem0 + i / NSP;
+        const int s = (int)(i % NSP);
+        double w = 1.0;
+        int t = s;
+#pragma unroll
+        for (int d = 0; d < D; ++d) { w *= a.opW[t % N]; t /= N; }
+        const real *src;
+        if (a.integral_src == 0) {
+            w /= (double)a.MET[(e * NSP + s) * MS + D * D];
+            src = a.U + (e * NSP + s) * V;
+        } else {
+            src = a.RES + (e * NSP + s) * V;
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            const double x = (double)src[v];
+            if (!isfinite(x)) bad += 1.0;
+            acc[v] += w * x;
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[v] += __shfl_xor_sync(0xffffffffu, acc[v], o);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_xor_sync(0xffffffffu, bad, o);
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+#pragma unroll
+        for (int v = 0; v < V; ++v) red[wid][v] = acc[v];
+        red[wid][V] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s[V + 1], c[V + 1];
+        for (int v = 0; v <= V; ++v) { s[v] = 0.0; c[v] = 0.0; }
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2)
+            for (int v = 0; v <= V; ++v) neumaier_add(s[v], c[v], red[w2][v]);
+        double *out = a.partials + (int64_t)blockIdx.x * (2 * V + 1);
+        for (int v = 0; v < V; ++v) { out[v] = s[v]; out[V + v] = c[v]; }
+        out[2 * V] = s[V] + c[V];
+    }
+}
+
+template <int D, int N, typename real>
+__global__ void k_reduce(const KArgs<real> a) {
+    constexpr int V = D + 2;
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double s[V], c[V], bad = 0.0;
+    for (int v = 0; v < V; ++v) { s[v] = 0.0; c[v] = 0.0; }
+    for (int64_t b = 0; b < a.n_partials; ++b) {
+        const double *in = a.partials + b * (2 * V + 1);
+        for (int v = 0; v < V; ++v) {
+            neumaier_add(s[v], c[v], in[v]);
+            neumaier_add(s[v], c[v], in[V + v]);
+        }
+        bad += in[2 * V];
+    }
+    for (int v = 0; v < V; ++v) a.reduce_out[v] = s[v] + c[v];
+    a.reduce_out[V] = bad;
+}
+
+// --------------------------------------------------------------------------
+// K_TO_REAL / K_TO_F64: FP64 host-layout staging <-> state of one instance
+// --------------------------------------------------------------------------
+template <int D, int N, typename real>
+__global__ void k_to_real(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    const int64_t total = a.n_elem * G::NSP * G::V;
+    const int64_t off = a.elem0 * G::NSP * G::V;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a.U[off + i] = (real)a.stage64[i];
+}
+
+template <int D, int N, typename real>
+__global__ void k_to_f64(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    const int64_t total = a.n_elem * G::NSP * G::V;
+    const int64_t off = a.elem0 * G::NSP * G::V;
+    const real *src = a.integral_src ? a.RES : a.U;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a.stage64_out[i] = (double)src[off + i];
+}
+
+// --------------------------------------------------------------------------
+// launch glue (instantiated per dimension and precision)
+// --------------------------------------------------------------------------
+template <int D, int N, typename real>
+size_t smem_bytes(int kind, bool visc) {
+    using G = Geo<D, N>;
+    constexpr int NE = G::NE, NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS;
+    size_t n = pad4(N * N + 4 * N);
+    if (kind == K_FLUX) {
+        n += pad4(NE * NSP * V) + pad4(NE * NSP * MS) + pad4(NE * NFP * V) * (visc ? 2 : 1) +
+             pad4(NE * D * NSP * V);
+    } else if (kind == K_GRAD) {
+        n += pad4(NE * NSP * V) + pad4(NE * NSP * MS) + 2 * pad4(NE * NFP * V) + pad4(NE * NSP * D * V);
+    } else if (kind == K_INTERP) {
+        n += pad4(NE * NSP * V);
+    }
+    return n * sizeof(real);
+}
+
+template <typename K>
+cudaError_t prep_smem(K kernel, size_t bytes) {
+    if (bytes > 48 * 1024)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaSuccess;
+}
+
+template <int D, int N, typename real>
+cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, cudaStream_t st) {
+    using G = Geo<D, N>;
+    const int64_t tiles = (a.n_elem + G::NE - 1) / G::NE;
+    if (kind == K_FLUX) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        const size_t sm = smem_bytes<D, N, real>(K_FLUX, visc);
+        if (visc) {
+            auto k = k_flux<D, N, real, true>;
+            cudaError_t err = prep_smem(k, sm);
+            if (err != cudaSuccess) return err;
+            k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+        } else {
+            auto k = k_flux<D, N, real, false>;
+            cudaError_t err = prep_smem(k, sm);
+            if (err != cudaSuccess) return err;
+            k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+        }
+    } else if (kind == K_GRAD) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        const size_t sm = smem_bytes<D, N, real>(K_GRAD, true);
+        auto k = k_grad<D, N, real>;
+        cudaError_t err = prep_smem(k, sm);
+        if (err != cudaSuccess) return err;
+        k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+    } else if (kind == K_INTERP) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        const size_t sm = smem_bytes<D, N, real>(K_INTERP, false);
+        auto k = k_interp<D, N, real>;
+        cudaError_t err = prep_smem(k, sm);
+        if (err != cudaSuccess) return err;
+        k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+    } else if (kind == K_PROBE) {
+        if (a.n_probe <= 0) return cudaSuccess;
+        k_probe<D, N, real><<<(a.n_probe + 3) / 4, 128, 0, st>>>(a);
+    } else if (kind == K_INTEGRAL) {
+        k_integral<D, N, real><<<grid_hint, 256, 0, st>>>(a);
+    } else if (kind == K_REDUCE) {
+        k_reduce<D, N, real><<<1, 32, 0, st>>>(a);
+    } else if (kind == K_TO_REAL) {
+        k_to_real<D, N, real><<<grid_hint, 256, 0, st>>>(a);
+    } else if (kind == K_TO_F64) {
+        k_to_f64<D, N, real><<<grid_hint, 256, 0, st>>>(a);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace frk

@@ -1,0 +1,506 @@
+// Host (FP64) mesh processing of the FR library: reference element, element
+// maps, metric terms, normals and flux-point connectivity.
+//
+// Method: Flux Reconstruction (Sec. 2.3 of arXiv:2312.14167, Huynh's scheme)
+// on tensor-product Gauss-Legendre points with the DG-recovery correction
+// functions g_L = (-1)^(p+1)/2 (P_{p+1} - P_p), g_R = 1/2 (P_{p+1} + P_p).
+// Geometry: the element map is the tensor Lagrange interpolant of equispaced
+// geometry nodes; metric terms S[k][j] = J dxi_k/dx_j are the adjugate of the
+// map Jacobian, evaluated analytically; the outward normal at a flux point is
+// +-S[k][:] there.  All of this runs once per mesh in FP64; the FP32 solver
+// casts the results.
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <unordered_map>
+
+#include "fr_internal.h"
+
+namespace fr {
+
+namespace {
+
+// Legendre polynomial and derivative in long double (Bonnet recurrence).
+void legendre_ld(int k, long double x, long double *P, long double *dP) {
+    long double p0 = 1.0L, p1 = x, d0 = 0.0L, d1 = 1.0L;
+    if (k == 0) { *P = 1.0L; *dP = 0.0L; return; }
+    for (int n = 1; n < k; ++n) {
+        long double p2 = ((2 * n + 1) * x * p1 - n * p0) / (n + 1);
+        long double d2 = d0 + (2 * n + 1) * p1;
+        p0 = p1; p1 = p2; d0 = d1; d1 = d2;
+    }
+    *P = p1; *dP = d1;
+}
+
+double lagrange_1d(const double *nodes, int n, int j, double x) {
+    double v = 1.0;
+    for (int m = 0; m < n; ++m)
+        if (m != j) v *= (x - nodes[m]) / (nodes[j] - nodes[m]);
+    return v;
+}
+
+double lagrange_1d_deriv(const double *nodes, int n, int j, double x) {
+    double denom = 1.0;
+    for (int m = 0; m < n; ++m)
+        if (m != j) denom *= nodes[j] - nodes[m];
+    double s = 0.0;
+    for (int r = 0; r < n; ++r) {
+        if (r == j) continue;
+        double t = 1.0;
+        for (int m = 0; m < n; ++m)
+            if (m != j && m != r) t *= x - nodes[m];
+        s += t;
+    }
+    return s / denom;
+}
+
+}  // namespace
+
+void build_ref(RefElem &r, int dim, int p) {
+    const int n = p + 1;
+    r.dim = dim; r.p = p; r.n = n;
+    r.nsp = (dim == 2) ? n * n : n * n * n;
+    r.nfpf = (dim == 2) ? n : n * n;
+    r.nfp = 2 * dim * r.nfpf;
+    // Gauss-Legendre nodes: Newton in long double from Chebyshev-like guesses
+    for (int i = 0; i < n; ++i) {
+        long double x = -cosl(3.14159265358979323846264338327950288L * (i + 0.75L) / (n + 0.5L));
+        for (int it = 0; it < 200; ++it) {
+            long double P, dP;
+            legendre_ld(n, x, &P, &dP);
+            long double dx = P / dP;
+            x -= dx;
+            if (fabsl(dx) < 1e-19L) break;
+        }
+        long double P, dP;
+        legendre_ld(n, x, &P, &dP);
+        r.xi[i] = (double)x;
+        r.w[i] = (double)(2.0L / ((1.0L - x * x) * dP * dP));
+    }
+    for (int m = 0; m < n; ++m) {
+        r.lend[0][m] = lagrange_1d(r.xi, n, m, -1.0);
+        r.lend[1][m] = lagrange_1d(r.xi, n, m, 1.0);
+        for (int i = 0; i < n; ++i) r.D1[i][m] = lagrange_1d_deriv(r.xi, n, m, r.xi[i]);
+    }
+    const long double sgn = (p % 2 == 0) ? -0.5L : 0.5L;   // (-1)^(p+1) / 2
+    for (int i = 0; i < n; ++i) {
+        long double P1, dP1, P0, dP0;
+        legendre_ld(p + 1, r.xi[i], &P1, &dP1);
+        legendre_ld(p, r.xi[i], &P0, &dP0);
+        r.dgL[i] = (double)(sgn * (dP1 - dP0));
+        r.dgR[i] = (double)(0.5L * (dP1 + dP0));
+    }
+    r.sp_xi.assign((size_t)r.nsp * dim, 0.0);
+    r.sp_w.assign(r.nsp, 1.0);
+    for (int s = 0; s < r.nsp; ++s) {
+        int t = s;
+        for (int a = 0; a < dim; ++a) {
+            int ia = t % n; t /= n;
+            r.sp_xi[(size_t)s * dim + a] = r.xi[ia];
+            r.sp_w[s] *= r.w[ia];
+        }
+    }
+    r.fp_xi.assign((size_t)r.nfp * dim, 0.0);
+    r.fp_w.assign(r.nfp, 1.0);
+    r.fp_dir.assign(r.nfp, 0);
+    r.fp_side.assign(r.nfp, 0);
+    for (int f = 0; f < r.nfp; ++f) {
+        const int face = f / r.nfpf, l = f % r.nfpf, k = face / 2, side = face % 2;
+        r.fp_dir[f] = k; r.fp_side[f] = side;
+        int t = l;
+        for (int a = 0; a < dim; ++a) {
+            if (a == k) { r.fp_xi[(size_t)f * dim + a] = side ? 1.0 : -1.0; continue; }
+            int ia = t % n; t /= n;
+            r.fp_xi[(size_t)f * dim + a] = r.xi[ia];
+            r.fp_w[f] *= r.w[ia];
+        }
+    }
+}
+
+int ref_line_sp(const RefElem &r, int f, int m) {
+    const int n = r.n, face = f / r.nfpf, k = face / 2;
+    int l = f % r.nfpf, idx[3] = {0, 0, 0};
+    for (int a = 0; a < r.dim; ++a) {
+        if (a == k) { idx[a] = m; continue; }
+        idx[a] = l % n; l /= n;
+    }
+    return idx[0] + n * idx[1] + n * n * idx[2];
+}
+
+void ref_interp(const RefElem &r, const double *xi, double *out) {
+    const int n = r.n;
+    double L[3][kMaxN];
+    for (int a = 0; a < r.dim; ++a)
+        for (int m = 0; m < n; ++m) L[a][m] = lagrange_1d(r.xi, n, m, xi[a]);
+    for (int s = 0; s < r.nsp; ++s) {
+        int t = s;
+        double v = 1.0;
+        for (int a = 0; a < r.dim; ++a) { v *= L[a][t % n]; t /= n; }
+        out[s] = v;
+    }
+}
+
+// --------------------------------------------------------------------------
+// element map
+// --------------------------------------------------------------------------
+namespace {
+
+struct MapEval {
+    int dim, q, nn;
+    std::vector<double> eq;
+    explicit MapEval(int dim_, int q_) : dim(dim_), q(q_) {
+        nn = 1;
+        for (int a = 0; a < dim; ++a) nn *= (q + 1);
+        eq.resize(q + 1);
+        for (int i = 0; i <= q; ++i) eq[i] = -1.0 + 2.0 * i / q;
+    }
+    // x (dim) and A[j][k] = dx_j/dxi_k at xi, from the element's nodes.  The
+    // sums run over offsets from node 0 (the shape functions sum to one and
+    // their derivatives to zero), so rounding scales with the element size.
+    void eval(const double *nodes, const double *xi, double *x, double A[3][3]) const {
+        double L[3][8], dL[3][8];
+        for (int a = 0; a < dim; ++a)
+            for (int m = 0; m <= q; ++m) {
+                L[a][m] = lagrange_1d(eq.data(), q + 1, m, xi[a]);
+                dL[a][m] = lagrange_1d_deriv(eq.data(), q + 1, m, xi[a]);
+            }
+        for (int j = 0; j < dim; ++j) {
+            x[j] = 0.0;
+            for (int k = 0; k < dim; ++k) A[j][k] = 0.0;
+        }
+        for (int a = 0; a < nn; ++a) {
+            int idx[3] = {0, 0, 0}, t = a;
+            for (int d = 0; d < dim; ++d) { idx[d] = t % (q + 1); t /= (q + 1); }
+            double N = 1.0, dN[3];
+            for (int d = 0; d < dim; ++d) N *= L[d][idx[d]];
+            for (int k = 0; k < dim; ++k) {
+                dN[k] = 1.0;
+                for (int d = 0; d < dim; ++d) dN[k] *= (d == k) ? dL[d][idx[d]] : L[d][idx[d]];
+            }
+            for (int j = 0; j < dim; ++j) {
+                const double X = nodes[(size_t)a * dim + j] - nodes[j];
+                x[j] += N * X;
+                for (int k = 0; k < dim; ++k) A[j][k] += dN[k] * X;
+            }
+        }
+        for (int j = 0; j < dim; ++j) x[j] += nodes[j];
+    }
+};
+
+// S[k][j] = J dxi_k / dx_j (adjugate of A), returns J
+double adjugate(int dim, const double A[3][3], double S[3][3]) {
+    if (dim == 2) {
+        S[0][0] = A[1][1];  S[0][1] = -A[0][1];
+        S[1][0] = -A[1][0]; S[1][1] = A[0][0];
+        return A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    }
+    for (int k = 0; k < 3; ++k) {
+        const int k1 = (k + 1) % 3, k2 = (k + 2) % 3;
+        // row k = (dx/dxi_k1) x (dx/dxi_k2)
+        S[k][0] = A[1][k1] * A[2][k2] - A[2][k1] * A[1][k2];
+        S[k][1] = A[2][k1] * A[0][k2] - A[0][k1] * A[2][k2];
+        S[k][2] = A[0][k1] * A[1][k2] - A[1][k1] * A[0][k2];
+    }
+    return A[0][0] * S[0][0] + A[1][0] * S[0][1] + A[2][0] * S[0][2];
+}
+
+const int kQuadFaces[4][2] = {{0, 2}, {1, 3}, {0, 1}, {2, 3}};
+const int kHexFaces[6][4] = {{0, 2, 4, 6}, {1, 3, 5, 7}, {0, 1, 4, 5},
+                             {2, 3, 6, 7}, {0, 1, 2, 3}, {4, 5, 6, 7}};
+
+struct Key4 {
+    std::array<int64_t, 4> v;
+    bool operator==(const Key4 &o) const { return v == o.v; }
+};
+struct Key4Hash {
+    size_t operator()(const Key4 &k) const {
+        uint64_t h = 1469598103934665603ull;
+        for (int64_t x : k.v) { h ^= (uint64_t)x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2); }
+        return (size_t)h;
+    }
+};
+
+}  // namespace
+
+bool mesh_locate(const fr_mesh &m, const double *x, int64_t *elem, double *xi) {
+    MapEval me(m.dim, m.q);
+    const int d = m.dim;
+    for (int64_t e = 0; e < m.n_elem; ++e) {
+        const double *nd = &m.nodes[(size_t)e * me.nn * d];
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int a = 0; a < me.nn; ++a)
+            for (int j = 0; j < d; ++j) {
+                lo[j] = std::min(lo[j], nd[a * d + j]);
+                hi[j] = std::max(hi[j], nd[a * d + j]);
+            }
+        double span = 0;
+        for (int j = 0; j < d; ++j) span = std::max(span, hi[j] - lo[j]);
+        bool inside = true;
+        for (int j = 0; j < d; ++j)
+            if (x[j] < lo[j] - 1e-9 * span || x[j] > hi[j] + 1e-9 * span) inside = false;
+        if (!inside) continue;
+        double z[3] = {0, 0, 0};
+        bool ok = true;
+        for (int it = 0; it < 60; ++it) {
+            double xx[3], A[3][3], S[3][3];
+            me.eval(nd, z, xx, A);
+            const double J = adjugate(d, A, S);
+            if (J == 0.0) { ok = false; break; }
+            double r[3] = {x[0] - xx[0], x[1] - xx[1], d == 3 ? x[2] - xx[2] : 0.0};
+            double dz[3] = {0, 0, 0}, mx = 0;
+            // A^{-1} = S / J (S is the adjugate)
+            for (int k = 0; k < d; ++k) {
+                for (int j = 0; j < d; ++j) dz[k] += S[k][j] * r[j] / J;
+                z[k] += dz[k];
+                mx = std::max(mx, std::fabs(dz[k]));
+            }
+            if (std::fabs(z[0]) > 3 || std::fabs(z[1]) > 3 || (d == 3 && std::fabs(z[2]) > 3)) { ok = false; break; }
+            if (mx < 1e-14) break;
+        }
+        if (!ok) continue;
+        bool in = true;
+        for (int k = 0; k < d; ++k) in = in && std::fabs(z[k]) <= 1.0 + 1e-10;
+        if (!in) continue;
+        *elem = e;
+        for (int k = 0; k < d; ++k) xi[k] = std::max(-1.0, std::min(1.0, z[k]));
+        return true;
+    }
+    return false;
+}
+
+}  // namespace fr
+
+using fr::RefElem;
+
+extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_vert,
+                                    const double *xyz, int64_t n_elem, const int64_t *elem_vert,
+                                    int geo_order, const double *geo_nodes,
+                                    const int32_t *face_tag, int n_shift,
+                                    const double *periodic_shift) {
+    if (!out || !xyz || !elem_vert || !face_tag || n_elem <= 0 || n_vert <= 0 ||
+        (dim != 2 && dim != 3) || geo_order < 1 || geo_order > 7 ||
+        (n_shift > 0 && !periodic_shift) || n_shift < 0) {
+        fr::set_error("fr_mesh_create: invalid argument");
+        return FR_ERR_INVALID_ARG;
+    }
+    if (p < 1 || p > 4) {
+        fr::set_error("fr_mesh_create: polynomial degree must be 1..4");
+        return FR_ERR_UNSUPPORTED;
+    }
+    *out = nullptr;
+    fr_mesh *m = new fr_mesh();
+    m->dim = dim; m->p = p; m->n_elem = n_elem;
+    RefElem &r = m->ref;
+    fr::build_ref(r, dim, p);
+    const int nc = 1 << dim;
+    for (int64_t i = 0; i < n_elem * nc; ++i)
+        if (elem_vert[i] < 0 || elem_vert[i] >= n_vert) {
+            delete m;
+            fr::set_error("fr_mesh_create: vertex index out of range");
+            return FR_ERR_INVALID_ARG;
+        }
+    // geometry nodes
+    int q = geo_nodes ? geo_order : 1;
+    m->q = q;
+    fr::MapEval me(dim, q);
+    m->nodes.resize((size_t)n_elem * me.nn * dim);
+    if (geo_nodes) {
+        std::memcpy(m->nodes.data(), geo_nodes, m->nodes.size() * sizeof(double));
+    } else {
+        for (int64_t e = 0; e < n_elem; ++e)
+            for (int c = 0; c < nc; ++c)
+                for (int j = 0; j < dim; ++j)
+                    m->nodes[((size_t)e * nc + c) * dim + j] = xyz[elem_vert[e * nc + c] * dim + j];
+    }
+    const int nsp = r.nsp, nfp = r.nfp, nfpf = r.nfpf;
+    m->x_sp.resize((size_t)n_elem * nsp * dim);
+    m->S.resize((size_t)n_elem * nsp * dim * dim);
+    m->J.resize((size_t)n_elem * nsp);
+    m->nrm.resize((size_t)n_elem * nfp * dim);
+    m->x_fp.resize((size_t)n_elem * nfp * dim);
+    m->partner.assign((size_t)n_elem * nfp, -1);
+    m->bctag.assign((size_t)n_elem * nfp, 0);
+    for (int64_t e = 0; e < n_elem; ++e) {
+        const double *nd = &m->nodes[(size_t)e * me.nn * dim];
+        for (int s = 0; s < nsp; ++s) {
+            double x[3], A[3][3], S[3][3];
+            me.eval(nd, &r.sp_xi[(size_t)s * dim], x, A);
+            const double J = fr::adjugate(dim, A, S);
+            if (!(J > 0.0)) {
+                delete m;
+                fr::set_error("fr_mesh_create: non-positive Jacobian in element " + std::to_string(e));
+                return FR_ERR_MESH;
+            }
+            m->J[(size_t)e * nsp + s] = J;
+            for (int j = 0; j < dim; ++j) m->x_sp[((size_t)e * nsp + s) * dim + j] = x[j];
+            for (int k = 0; k < dim; ++k)
+                for (int j = 0; j < dim; ++j)
+                    m->S[(((size_t)e * nsp + s) * dim + k) * dim + j] = S[k][j];
+        }
+        for (int f = 0; f < nfp; ++f) {
+            double x[3], A[3][3], S[3][3];
+            me.eval(nd, &r.fp_xi[(size_t)f * dim], x, A);
+            fr::adjugate(dim, A, S);
+            const int k = r.fp_dir[f];
+            const double sg = r.fp_side[f] ? 1.0 : -1.0;
+            for (int j = 0; j < dim; ++j) {
+                m->nrm[((size_t)e * nfp + f) * dim + j] = sg * S[k][j];
+                m->x_fp[((size_t)e * nfp + f) * dim + j] = x[j];
+            }
+        }
+    }
+
+    // ---- face connectivity -------------------------------------------------
+    auto corners = [&](int64_t e, int fc, int c) -> int64_t {
+        return dim == 2 ? elem_vert[e * nc + fr::kQuadFaces[fc][c]]
+                        : elem_vert[e * nc + fr::kHexFaces[fc][c]];
+    };
+    const int ncf = dim == 2 ? 2 : 4;
+    struct Pair { int64_t e; int fc; int64_t e2; int fc2; double sh[3]; };
+    std::vector<Pair> pairs;
+    std::unordered_map<fr::Key4, std::vector<std::pair<int64_t, int>>, fr::Key4Hash> by_ids;
+    by_ids.reserve((size_t)n_elem * dim * 2);
+    for (int64_t e = 0; e < n_elem; ++e)
+        for (int fc = 0; fc < 2 * dim; ++fc) {
+            const int32_t tg = face_tag[e * 2 * dim + fc];
+            if (tg < 0 || tg > 5) {
+                delete m;
+                fr::set_error("fr_mesh_create: unknown face tag");
+                return FR_ERR_INVALID_ARG;
+            }
+            if (tg != FR_TAG_INTERIOR) continue;
+            fr::Key4 k{{-1, -1, -1, -1}};
+            for (int c = 0; c < ncf; ++c) k.v[c] = corners(e, fc, c);
+            std::sort(k.v.begin(), k.v.begin() + ncf);
+            by_ids[k].push_back({e, fc});
+        }
+    for (auto &kv : by_ids) {
+        if (kv.second.size() != 2) {
+            delete m;
+            fr::set_error("fr_mesh_create: interior face without exactly one partner");
+            return FR_ERR_MESH;
+        }
+        auto a = kv.second[0], b = kv.second[1];
+        pairs.push_back({a.first, a.second, b.first, b.second, {0, 0, 0}});
+        pairs.push_back({b.first, b.second, a.first, a.second, {0, 0, 0}});
+    }
+    // periodic faces: corner coordinates rounded on a fine lattice
+    {
+        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+        for (int64_t v = 0; v < n_vert; ++v)
+            for (int j = 0; j < dim; ++j) {
+                lo[j] = std::min(lo[j], xyz[v * dim + j]);
+                hi[j] = std::max(hi[j], xyz[v * dim + j]);
+            }
+        double span = 0;
+        for (int j = 0; j < dim; ++j) span = std::max(span, hi[j] - lo[j]);
+        const double scale = 1e6 / std::max(span, 1e-300);
+        using CKey = std::vector<int64_t>;
+        std::map<CKey, std::pair<int64_t, int>> table;
+        auto ckey = [&](int64_t e, int fc, const double *sh) {
+            std::vector<std::array<int64_t, 3>> pts(ncf);
+            for (int c = 0; c < ncf; ++c) {
+                const int64_t v = corners(e, fc, c);
+                for (int j = 0; j < 3; ++j)
+                    pts[c][j] = j < dim ? (int64_t)std::llround((xyz[v * dim + j] + (sh ? sh[j] : 0.0)) * scale) : 0;
+            }
+            std::sort(pts.begin(), pts.end());
+            CKey k;
+            for (auto &pt : pts) k.insert(k.end(), pt.begin(), pt.end());
+            return k;
+        };
+        std::vector<std::pair<int64_t, int>> per;
+        for (int64_t e = 0; e < n_elem; ++e)
+            for (int fc = 0; fc < 2 * dim; ++fc)
+                if (face_tag[e * 2 * dim + fc] == FR_TAG_PERIODIC) {
+                    per.push_back({e, fc});
+                    table[ckey(e, fc, nullptr)] = {e, fc};
+                }
+        for (auto &pf : per) {
+            bool found = false;
+            for (int s = 0; s < n_shift && !found; ++s)
+                for (int sg = 1; sg >= -1 && !found; sg -= 2) {
+                    double sh[3] = {0, 0, 0};
+                    for (int j = 0; j < dim; ++j) sh[j] = sg * periodic_shift[s * dim + j];
+                    auto it = table.find(ckey(pf.first, pf.second, sh));
+                    if (it != table.end() && it->second != pf) {
+                        pairs.push_back({pf.first, pf.second, it->second.first, it->second.second,
+                                         {sh[0], sh[1], sh[2]}});
+                        found = true;
+                    }
+                }
+            if (!found) {
+                delete m;
+                fr::set_error("fr_mesh_create: periodic face without partner");
+                return FR_ERR_MESH;
+            }
+        }
+    }
+    // pair flux points by physical position
+    for (const Pair &pr : pairs) {
+        const double *xa = &m->x_fp[((size_t)pr.e * nfp + pr.fc * nfpf) * dim];
+        const double *xb = &m->x_fp[((size_t)pr.e2 * nfp + pr.fc2 * nfpf) * dim];
+        double hmin = 1e300;
+        for (int i = 0; i < ncf; ++i)
+            for (int j = i + 1; j < ncf; ++j) {
+                double d2 = 0;
+                for (int c = 0; c < dim; ++c) {
+                    double dd = xyz[corners(pr.e, pr.fc, i) * dim + c] - xyz[corners(pr.e, pr.fc, j) * dim + c];
+                    d2 += dd * dd;
+                }
+                hmin = std::min(hmin, std::sqrt(d2));
+            }
+        for (int a = 0; a < nfpf; ++a) {
+            int best = -1;
+            double bd = 1e300;
+            for (int b = 0; b < nfpf; ++b) {
+                double d2 = 0;
+                for (int c = 0; c < dim; ++c) {
+                    double dd = xa[a * dim + c] + pr.sh[c] - xb[b * dim + c];
+                    d2 += dd * dd;
+                }
+                if (d2 < bd) { bd = d2; best = b; }
+            }
+            if (std::sqrt(bd) > 1e-6 * hmin) {
+                delete m;
+                fr::set_error("fr_mesh_create: flux points of a connected face do not coincide");
+                return FR_ERR_MESH;
+            }
+            m->partner[(size_t)pr.e * nfp + pr.fc * nfpf + a] = pr.e2 * nfp + pr.fc2 * nfpf + best;
+        }
+    }
+    for (int64_t e = 0; e < n_elem; ++e)
+        for (int fc = 0; fc < 2 * dim; ++fc) {
+            const int32_t tg = face_tag[e * 2 * dim + fc];
+            for (int a = 0; a < nfpf; ++a) {
+                const size_t i = (size_t)e * nfp + fc * nfpf + a;
+                if (tg >= FR_TAG_WALL) {
+                    m->bctag[i] = tg;
+                } else if (m->partner[i] < 0) {
+                    delete m;
+                    fr::set_error("fr_mesh_create: face left unconnected");
+                    return FR_ERR_MESH;
+                }
+            }
+        }
+    *out = m;
+    return FR_OK;
+}
+
+extern "C" void fr_mesh_destroy(fr_mesh *mesh) { delete mesh; }
+
+extern "C" fr_status fr_mesh_info(const fr_mesh *m, int64_t *n_elem, int *nsp, int *nfp) {
+    if (!m) { fr::set_error("fr_mesh_info: null mesh"); return FR_ERR_INVALID_ARG; }
+    if (n_elem) *n_elem = m->n_elem;
+    if (nsp) *nsp = m->ref.nsp;
+    if (nfp) *nfp = m->ref.nfp;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_mesh_sol_coords(const fr_mesh *m, double *xyz) {
+    if (!m || !xyz) { fr::set_error("fr_mesh_sol_coords: null argument"); return FR_ERR_INVALID_ARG; }
+    std::memcpy(xyz, m->x_sp.data(), m->x_sp.size() * sizeof(double));
+    return FR_OK;
+}

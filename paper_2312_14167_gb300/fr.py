@@ -1,0 +1,283 @@
+"""Thin Python binding of libfr.so (include/fr.h): argument marshalling only.
+
+Every step of the hot path runs in the library's CUDA kernels; PyTorch
+supplies the device workspace (a uint8 tensor) and the CUDA stream.  There is
+no CPU fallback: importing this module fails loudly when libfr.so is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "libfr.so")
+
+FR_OK = 0
+FR_TAG_INTERIOR, FR_TAG_PERIODIC, FR_TAG_WALL = 0, 1, 2
+FR_TAG_FARFIELD, FR_TAG_INFLOW, FR_TAG_OUTFLOW = 3, 4, 5
+FR_RK4, FR_LSRK45 = 0, 1
+FR_FP64, FR_FP32 = 0, 1
+
+STATUS = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_MESH", 3: "FR_ERR_UNSUPPORTED",
+          4: "FR_ERR_CUDA", 5: "FR_ERR_NONFINITE", 6: "FR_ERR_TIMEOUT", 7: "FR_ERR_WORKSPACE"}
+
+EXPORTED = ["fr_mesh_create", "fr_mesh_destroy", "fr_mesh_info", "fr_mesh_sol_coords",
+            "fr_workspace_bytes", "fr_solver_create", "fr_solver_destroy", "fr_set_state",
+            "fr_get_state", "fr_residual", "fr_rk_step", "fr_probe_add", "fr_probe_pressure",
+            "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
+            "fr_integral", "fr_last_launch_count", "fr_profile_steps", "fr_last_error"]
+
+
+class FRError(RuntimeError):
+    def __init__(self, status, where, msg):
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Config(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("prandtl", C.c_double), ("mu", C.c_double),
+                ("rho_inf", C.c_double), ("v_inf", C.c_double * 3), ("p_inf", C.c_double),
+                ("inflow_delta", C.c_double), ("inflow_ywall", C.c_double),
+                ("br2_eta", C.c_double), ("dt", C.c_double), ("viscous", C.c_int),
+                ("rk", C.c_int), ("precision", C.c_int), ("reserved", C.c_int)]
+
+
+def make_config(dim, gamma=1.4, prandtl=0.71, mu=0.0, rho_inf=1.0, v_inf=None, p_inf=1.0,
+                inflow_delta=0.0, inflow_ywall=0.0, br2_eta=0.0, dt=1e-3, viscous=False,
+                rk=FR_LSRK45, precision=FR_FP64) -> Config:
+    c = Config()
+    c.gamma, c.prandtl, c.mu = gamma, prandtl, mu
+    c.rho_inf, c.p_inf = rho_inf, p_inf
+    v = [0.0, 0.0, 0.0] if v_inf is None else list(v_inf) + [0.0] * (3 - len(v_inf))
+    for i in range(3):
+        c.v_inf[i] = v[i]
+    c.inflow_delta, c.inflow_ywall = inflow_delta, inflow_ywall
+    c.br2_eta, c.dt = br2_eta, dt
+    c.viscous, c.rk, c.precision = int(bool(viscous)), rk, precision
+    return c
+
+
+_lib = None
+
+
+def lib():
+    """Load libfr.so once; raise if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise ImportError(f"libfr.so not built ({_LIB_PATH}); run __graft_entry__.build()")
+    L = C.CDLL(_LIB_PATH)
+    P, I, I64, D = C.c_void_p, C.c_int, C.c_int64, C.c_double
+    dp = C.POINTER(C.c_double)
+    L.fr_mesh_create.argtypes = [C.POINTER(P), I, I, I64, dp, I64, C.POINTER(C.c_int64), I, dp,
+                                 C.POINTER(C.c_int32), I, dp]
+    L.fr_mesh_destroy.argtypes = [P]
+    L.fr_mesh_destroy.restype = None
+    L.fr_mesh_info.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(I), C.POINTER(I)]
+    L.fr_mesh_sol_coords.argtypes = [P, dp]
+    L.fr_workspace_bytes.argtypes = [C.POINTER(P), I, C.POINTER(Config)]
+    L.fr_workspace_bytes.restype = C.c_size_t
+    L.fr_solver_create.argtypes = [C.POINTER(P), C.POINTER(P), I, C.POINTER(Config), P, C.c_size_t, P]
+    L.fr_solver_destroy.argtypes = [P]
+    L.fr_solver_destroy.restype = None
+    L.fr_set_state.argtypes = [P, I, dp]
+    L.fr_get_state.argtypes = [P, I, dp]
+    L.fr_residual.argtypes = [P, I, dp]
+    L.fr_rk_step.argtypes = [P, I]
+    L.fr_probe_add.argtypes = [P, I, dp, C.POINTER(I)]
+    L.fr_probe_pressure.argtypes = [P, I, dp]
+    L.fr_probe_reset.argtypes = [P]
+    L.fr_oaspl.argtypes = [P, C.POINTER(I), I, D, D, I, dp]
+    L.fr_probe_stats.argtypes = [P, I, dp]
+    L.fr_forces.argtypes = [P, I, dp]
+    L.fr_conservation.argtypes = [P, I, dp]
+    L.fr_integral.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
+    L.fr_last_launch_count.argtypes = [P]
+    L.fr_last_launch_count.restype = C.c_int64
+    L.fr_profile_steps.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
+    L.fr_last_error.argtypes = []
+    L.fr_last_error.restype = C.c_char_p
+    for name in EXPORTED:
+        if name not in ("fr_mesh_destroy", "fr_solver_destroy", "fr_workspace_bytes",
+                        "fr_last_launch_count", "fr_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(st, where):
+    if st != FR_OK:
+        raise FRError(st, where, lib().fr_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Mesh:
+    """fr_mesh_create over a ``synth.meshes.Mesh``-like object (fields dim,
+    xyz, elem_vert, face_tag, periodic_shift, geo_order, geo_nodes)."""
+
+    def __init__(self, mesh, p: int):
+        L = lib()
+        self.dim = int(mesh.dim)
+        self.p = int(p)
+        xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
+        ev = np.ascontiguousarray(mesh.elem_vert, dtype=np.int64)
+        tags = np.ascontiguousarray(mesh.face_tag, dtype=np.int32)
+        sh = np.ascontiguousarray(mesh.periodic_shift, dtype=np.float64).reshape(-1, self.dim)
+        gn = None if getattr(mesh, "geo_nodes", None) is None else np.ascontiguousarray(mesh.geo_nodes, dtype=np.float64)
+        h = C.c_void_p()
+        st = L.fr_mesh_create(C.byref(h), self.dim, self.p, xyz.shape[0], _dptr(xyz), ev.shape[0],
+                              ev.ctypes.data_as(C.POINTER(C.c_int64)),
+                              int(getattr(mesh, "geo_order", 1)), None if gn is None else _dptr(gn),
+                              tags.ctypes.data_as(C.POINTER(C.c_int32)), sh.shape[0],
+                              _dptr(sh) if sh.size else None)
+        _check(st, "fr_mesh_create")
+        self.handle = h
+        ne, nsp, nfp = C.c_int64(), C.c_int(), C.c_int()
+        _check(L.fr_mesh_info(h, C.byref(ne), C.byref(nsp), C.byref(nfp)), "fr_mesh_info")
+        self.n_elem, self.nsp, self.nfp = ne.value, nsp.value, nfp.value
+
+    def sol_coords(self):
+        out = np.empty((self.n_elem, self.nsp, self.dim))
+        _check(lib().fr_mesh_sol_coords(self.handle, _dptr(out)), "fr_mesh_sol_coords")
+        return out
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fr_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Solver:
+    """fr_solver_create over a batch of Mesh objects; device workspace and
+    stream come from PyTorch."""
+
+    def __init__(self, meshes, cfg: Config, device="cuda", stream=None):
+        import torch
+        L = lib()
+        self.meshes = list(meshes)
+        self.cfg = cfg
+        self.dim = self.meshes[0].dim
+        self.V = self.dim + 2
+        arr = (C.c_void_p * len(self.meshes))(*[m.handle for m in self.meshes])
+        self._arr = arr
+        nbytes = L.fr_workspace_bytes(arr, len(self.meshes), C.byref(cfg))
+        if nbytes == 0:
+            raise FRError(1, "fr_workspace_bytes", L.fr_last_error().decode())
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=device)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        h = C.c_void_p()
+        torch.cuda.synchronize(device)
+        st = L.fr_solver_create(C.byref(h), arr, len(self.meshes), C.byref(cfg), C.c_void_p(aligned),
+                                nbytes, C.c_void_p(self.stream.cuda_stream))
+        _check(st, "fr_solver_create")
+        self.handle = h
+        self.ws_bytes = nbytes
+
+    def n_elem(self, inst):
+        return self.meshes[inst].n_elem
+
+    def set_state(self, inst, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        m = self.meshes[inst]
+        if u.shape != (m.n_elem, m.nsp, self.V):
+            raise ValueError("state shape")
+        _check(lib().fr_set_state(self.handle, inst, _dptr(u)), "fr_set_state")
+
+    def get_state(self, inst):
+        m = self.meshes[inst]
+        out = np.empty((m.n_elem, m.nsp, self.V))
+        _check(lib().fr_get_state(self.handle, inst, _dptr(out)), "fr_get_state")
+        return out
+
+    def residual(self, inst):
+        m = self.meshes[inst]
+        out = np.empty((m.n_elem, m.nsp, self.V))
+        _check(lib().fr_residual(self.handle, inst, _dptr(out)), "fr_residual")
+        return out
+
+    def rk_step(self, n):
+        _check(lib().fr_rk_step(self.handle, int(n)), "fr_rk_step")
+
+    def last_launch_count(self):
+        return int(lib().fr_last_launch_count(self.handle))
+
+    def probe_add(self, inst, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        pid = C.c_int()
+        _check(lib().fr_probe_add(self.handle, inst, _dptr(x), C.byref(pid)), "fr_probe_add")
+        return pid.value
+
+    def probe_pressure(self, pid):
+        v = C.c_double()
+        _check(lib().fr_probe_pressure(self.handle, pid, C.byref(v)), "fr_probe_pressure")
+        return v.value
+
+    def probe_stats(self, pid):
+        out = np.empty(4)
+        _check(lib().fr_probe_stats(self.handle, pid, _dptr(out)), "fr_probe_stats")
+        return out
+
+    def probe_reset(self):
+        _check(lib().fr_probe_reset(self.handle), "fr_probe_reset")
+
+    def oaspl(self, pids, p_ref=2e-5, p_scale=1.0, mean_mode=0):
+        ids = (C.c_int * len(pids))(*pids)
+        v = C.c_double()
+        _check(lib().fr_oaspl(self.handle, ids, len(pids), p_ref, p_scale, mean_mode, C.byref(v)),
+               "fr_oaspl")
+        return v.value
+
+    def forces(self, inst):
+        out = np.zeros(3)
+        _check(lib().fr_forces(self.handle, inst, _dptr(out)), "fr_forces")
+        return out[:self.dim]
+
+    def conservation(self, inst):
+        out = np.zeros(self.V)
+        _check(lib().fr_conservation(self.handle, inst, _dptr(out)), "fr_conservation")
+        return out
+
+    def integral(self, inst):
+        out = np.zeros(self.V)
+        bad = C.c_int64()
+        st = lib().fr_integral(self.handle, inst, _dptr(out), C.byref(bad))
+        if st not in (0, 5):
+            _check(st, "fr_integral")
+        return out, bad.value
+
+    def profile_steps(self, n):
+        """Mean ms per launch and launch counts per kernel kind:
+        (flux, gradient, probe, force, other)."""
+        ms = np.zeros(5)
+        cnt = np.zeros(5, dtype=np.int64)
+        _check(lib().fr_profile_steps(self.handle, int(n), _dptr(ms),
+                                      cnt.ctypes.data_as(C.POINTER(C.c_int64))), "fr_profile_steps")
+        return ms, cnt
+
+    def synchronize(self):
+        self.stream.synchronize()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().fr_solver_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
