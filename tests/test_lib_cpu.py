@@ -1,0 +1,95 @@
+"""CPU checks of the C-ABI library (no kernel launches): it loads, exports
+every function include/fr.h declares, and its host-side mesh processing
+(FP64) agrees with the oracle's and reports bad meshes with error codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from synth import meshes as M
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fr():
+    from paper_2312_14167_gb300 import build, fr as _fr
+    if not os.path.exists(os.path.join(ROOT, "paper_2312_14167_gb300", "libfr.so")):
+        build.build()
+    _fr.lib()
+    return _fr
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(fr_[a-z0-9_]+)\s*\(", txt))
+    return names
+
+
+def test_library_exports_every_declared_function(fr):
+    import ctypes
+    names = _declared()
+    assert len(names) >= 20
+    L = ctypes.CDLL(os.path.join(ROOT, "paper_2312_14167_gb300", "libfr.so"))
+    missing = [n for n in sorted(names) if not hasattr(L, n)]
+    assert not missing, missing
+    assert set(fr.EXPORTED) == names
+
+
+@pytest.mark.parametrize("maker,p", [
+    (lambda: M.vortex_mesh(5, jitter=0.2), 3),
+    (lambda: M.tgv_mesh(3), 2),
+    (lambda: M.cavity_mesh(800), 3),
+    (lambda: M.naca_omesh(0.04, 0.3, 0.1, 2.0, 500), 3),
+])
+def test_host_geometry_matches_oracle(fr, maker, p):
+    from oracle.fr import FRDiscretisation
+    from oracle.physics import NavierStokes
+    mesh = maker()
+    lm = fr.Mesh(mesh, p)
+    d = FRDiscretisation(mesh, p, NavierStokes(mesh.dim))
+    assert lm.n_elem == mesh.n_elem and lm.nsp == d.ref.nsp and lm.nfp == d.ref.nfp
+    span = np.ptp(mesh.xyz, axis=0).max()
+    assert np.abs(lm.sol_coords() - d.sol_coords()).max() < 1e-13 * span
+
+
+def test_mesh_errors_are_reported(fr):
+    good = M.vortex_mesh(3)
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(good, 5)
+    assert e.value.status == 3                       # FR_ERR_UNSUPPORTED
+    bad = M.vortex_mesh(3)
+    bad.face_tag = bad.face_tag.copy()
+    bad.face_tag[0, 0] = 0                           # periodic face marked interior
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(bad, 2)
+    assert e.value.status == 2                       # FR_ERR_MESH
+    inv = M.vortex_mesh(3)
+    inv.elem_vert = inv.elem_vert.copy()
+    inv.elem_vert[4] = inv.elem_vert[4][[1, 0, 3, 2]]   # mirrored element: J < 0
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(inv, 2)
+    assert e.value.status == 2
+    tag = M.vortex_mesh(3)
+    tag.face_tag = tag.face_tag.copy()
+    tag.face_tag[1, 1] = 9
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(tag, 2)
+    assert e.value.status == 1                       # FR_ERR_INVALID_ARG
+
+
+def test_solver_needs_a_device_workspace(fr):
+    """fr_solver_create refuses a null workspace before touching the GPU."""
+    import ctypes as C
+    m = fr.Mesh(M.vortex_mesh(3), 2)
+    cfg = fr.make_config(2, p_inf=1.0)
+    arr = (C.c_void_p * 1)(m.handle)
+    assert fr.lib().fr_workspace_bytes(arr, 1, C.byref(cfg)) > 0
+    h = C.c_void_p()
+    st = fr.lib().fr_solver_create(C.byref(h), arr, 1, C.byref(cfg), None, 0, None)
+    assert st == 7                                   # FR_ERR_WORKSPACE
