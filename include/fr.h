@@ -174,6 +174,31 @@ fr_status fr_conservation(fr_solver *solver, int inst, double *sums);
  * number of non-finite state values (all instances) in *n_nonfinite. */
 fr_status fr_integral(fr_solver *solver, int inst, double *sums, int64_t *n_nonfinite);
 
+/* Allocation-free variant of fr_integral (the paper has no counterpart: it is
+ * a service of this library).  Some callers cannot obtain device memory at
+ * the point where they want this check: a host application whose memory
+ * pool already owns all of the GPU's memory, a monitor that must not grow
+ * the solver's workspace, code that may not trigger the implicit device
+ * synchronisation an allocation brings.  This entry point allocates nothing
+ * and uses no part of the solver's workspace for its reduction: its per-block
+ * partial sums live in a fixed device array inside libfr.so (at most
+ * 1024 x 11 doubles plus the result, about 90 KB), which every GPU that loads
+ * the library holds until the process exits.
+ *  - Same inputs and outputs as fr_integral; the sums agree with it to
+ *    rounding (the reduction is partitioned differently).
+ *  - Limit: the instance may have at most 1024 * 256 * 8 = 2,097,152 solution
+ *    points; larger instances get FR_ERR_INVALID_ARG with a message (use
+ *    fr_integral for them).
+ *  - The first call on a device looks up the array's device address for
+ *    that device (once per device, with it current); make that first call
+ *    before any stream capture on that device.
+ *  - All calls share the one array and it keeps the last call's contents;
+ *    each call clears it first.  Calls that overlap on the GPU (other
+ *    streams, other threads, other solvers on the same device) race on it:
+ *    serialise them.
+ *  - Synchronises the solver's stream. */
+fr_status fr_integral_static(fr_solver *solver, int inst, double *sums, int64_t *n_nonfinite);
+
 /* Number of kernel launches issued by the last fr_rk_step call. */
 int64_t fr_last_launch_count(const fr_solver *solver);
 

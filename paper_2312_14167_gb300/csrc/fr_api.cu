@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -795,4 +796,97 @@ extern "C" fr_status fr_integral(fr_solver *s, int inst, double *sums, int64_t *
     if (n_nonfinite) *n_nonfinite = (int64_t)bad;
     if (st == FR_OK && bad > 0) { set_error("non-finite values in the state"); return FR_ERR_NONFINITE; }
     return st;
+}
+
+// --------------------------------------------------------------------------
+// Allocation-free integral (fr_integral_static)
+//
+// Same result as fr_integral, but the per-block partial sums and the final
+// sums live in a file-scope device array instead of the solver's workspace.
+// The array is part of the loaded module: every GPU that loads libfr.so holds
+// it until the process exits, and all calls share it.
+// --------------------------------------------------------------------------
+namespace fr {
+namespace {
+
+constexpr int kStaticBlocks = 1024;                 // partial-sum slots
+constexpr int kStaticThreads = 256;
+constexpr int kStaticItemsPerThread = 8;
+constexpr int64_t kStaticMaxItems = (int64_t)kStaticBlocks * kStaticThreads * kStaticItemsPerThread;
+constexpr int kStaticSlotsPerBlock = 2 * 5 + 1;      // sum, compensation (V <= 5), non-finite count
+constexpr size_t kStaticDoubles = (size_t)kStaticBlocks * kStaticSlotsPerBlock + 8;
+
+__device__ __align__(256) double g_static_scratch[kStaticDoubles];
+
+std::mutex g_static_mu;
+double *g_static_ptr[64] = {};   // device address of g_static_scratch, per device
+
+// Device address of the scratch array on the current device.  Looked up once
+// per device (cudaGetSymbolAddress), with that device current.
+fr_status static_scratch(double **out) {
+    int dev = 0;
+    FR_CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) { set_error("device index out of range"); return FR_ERR_INVALID_ARG; }
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void *p = nullptr;
+        FR_CK(cudaGetSymbolAddress(&p, g_static_scratch));
+        g_static_ptr[dev] = static_cast<double *>(p);
+    }
+    *out = g_static_ptr[dev];
+    return FR_OK;
+}
+
+template <typename real>
+cudaError_t launch_static(const fr_solver *s, int kind, int inst, int grid, double *scratch) {
+    frk::KArgs<real> a;
+    fill_args(s, a);
+    a.elem0 = s->off[inst];
+    a.n_elem = s->ne[inst];
+    a.integral_src = 0;
+    a.partials = scratch;
+    a.n_partials = grid;
+    a.reduce_out = scratch + (size_t)kStaticBlocks * kStaticSlotsPerBlock;
+    if constexpr (std::is_same<real, float>::value) {
+        return s->dim == 2 ? frk::launch_2_f32(s->N, kind, s->visc, a, grid, s->stream)
+                           : frk::launch_3_f32(s->N, kind, s->visc, a, grid, s->stream);
+    } else {
+        return s->dim == 2 ? frk::launch_2_f64(s->N, kind, s->visc, a, grid, s->stream)
+                           : frk::launch_3_f64(s->N, kind, s->visc, a, grid, s->stream);
+    }
+}
+
+}  // namespace
+}  // namespace fr
+
+extern "C" fr_status fr_integral_static(fr_solver *s, int inst, double *sums, int64_t *n_nonfinite) {
+    fr_status st = check_inst(s, inst);
+    if (st != FR_OK) return st;
+    if (!sums) { set_error("null output"); return FR_ERR_INVALID_ARG; }
+    const int64_t items = s->ne[inst] * (int64_t)s->nsp;
+    if (items > fr::kStaticMaxItems) {
+        set_error("fr_integral_static: instance has " + std::to_string(items) +
+                  " solution points, more than the static scratch serves (" +
+                  std::to_string(fr::kStaticMaxItems) + "); use fr_integral");
+        return FR_ERR_INVALID_ARG;
+    }
+    double *scratch = nullptr;
+    st = fr::static_scratch(&scratch);
+    if (st != FR_OK) return st;
+    const int per_block = fr::kStaticThreads * fr::kStaticItemsPerThread;
+    const int grid = (int)std::max<int64_t>(1, (items + per_block - 1) / per_block);
+    // every block writes all of its slots; the result slots are cleared anyway
+    FR_CK(cudaMemsetAsync(scratch, 0, fr::kStaticDoubles * sizeof(double), s->stream));
+    FR_CK(s->fp64 ? fr::launch_static<double>(s, frk::K_INTEGRAL, inst, grid, scratch)
+                  : fr::launch_static<float>(s, frk::K_INTEGRAL, inst, grid, scratch));
+    FR_CK(s->fp64 ? fr::launch_static<double>(s, frk::K_REDUCE, inst, grid, scratch)
+                  : fr::launch_static<float>(s, frk::K_REDUCE, inst, grid, scratch));
+    double h[6] = {0, 0, 0, 0, 0, 0};
+    FR_CK(cudaMemcpyAsync(h, scratch + (size_t)fr::kStaticBlocks * fr::kStaticSlotsPerBlock,
+                          (size_t)(s->V + 1) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    FR_CK(cudaStreamSynchronize(s->stream));
+    for (int v = 0; v < s->V; ++v) sums[v] = h[v];
+    if (n_nonfinite) *n_nonfinite = (int64_t)h[s->V];
+    if (h[s->V] > 0) { set_error("non-finite values in the state"); return FR_ERR_NONFINITE; }
+    return FR_OK;
 }

@@ -27,7 +27,8 @@ EXPORTED = ["fr_mesh_create", "fr_mesh_destroy", "fr_mesh_info", "fr_mesh_sol_co
             "fr_workspace_bytes", "fr_solver_create", "fr_solver_destroy", "fr_set_state",
             "fr_get_state", "fr_residual", "fr_rk_step", "fr_probe_add", "fr_probe_pressure",
             "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
-            "fr_integral", "fr_last_launch_count", "fr_profile_steps", "fr_last_error"]
+            "fr_integral", "fr_integral_static", "fr_last_launch_count", "fr_profile_steps",
+            "fr_last_error"]
 
 
 class FRError(RuntimeError):
@@ -95,6 +96,7 @@ def lib():
     L.fr_forces.argtypes = [P, I, dp]
     L.fr_conservation.argtypes = [P, I, dp]
     L.fr_integral.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
+    L.fr_integral_static.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
     L.fr_last_launch_count.argtypes = [P]
     L.fr_last_launch_count.restype = C.c_int64
     L.fr_profile_steps.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
@@ -267,6 +269,17 @@ class Solver:
         _check(lib().fr_profile_steps(self.handle, int(n), _dptr(ms),
                                       cnt.ctypes.data_as(C.POINTER(C.c_int64))), "fr_profile_steps")
         return ms, cnt
+
+    def integral_static(self, inst):
+        """fr_integral without workspace scratch (reduction scratch in a
+        fixed device array inside the library); raises FRError for instances
+        above its size limit."""
+        out = np.zeros(self.V)
+        bad = C.c_int64()
+        st = lib().fr_integral_static(self.handle, inst, _dptr(out), C.byref(bad))
+        if st not in (0, 5):
+            _check(st, "fr_integral_static")
+        return out, bad.value
 
     def synchronize(self):
         self.stream.synchronize()
