@@ -26,6 +26,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <climits>
 
 namespace frk {
 
@@ -365,16 +366,110 @@ __device__ __forceinline__ int64_t elem_of(const int32_t *elist, int64_t e0, int
 }
 
 // --------------------------------------------------------------------------
+// V-vector accesses: 128-bit for 4-variable states (2-D), scalar otherwise
+// --------------------------------------------------------------------------
+template <int V, typename real>
+__device__ __forceinline__ void ldg_v(const real *__restrict__ p, real *o) {
+    if constexpr (V == 4 && sizeof(real) == 4) {
+        const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (V == 4 && sizeof(real) == 8) {
+        const double2 t0 = __ldg(reinterpret_cast<const double2 *>(p));
+        const double2 t1 = __ldg(reinterpret_cast<const double2 *>(p) + 1);
+        o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = __ldg(p + v);
+    }
+}
+
+// plain (coherent) vector load: for arrays this kernel also writes
+template <int V, typename real>
+__device__ __forceinline__ void ld_v(const real *p, real *o) {
+    if constexpr (V == 4 && sizeof(real) == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(p);
+        o[0] = t.x; o[1] = t.y; o[2] = t.z; o[3] = t.w;
+    } else if constexpr (V == 4 && sizeof(real) == 8) {
+        const double2 t0 = reinterpret_cast<const double2 *>(p)[0];
+        const double2 t1 = reinterpret_cast<const double2 *>(p)[1];
+        o[0] = t0.x; o[1] = t0.y; o[2] = t1.x; o[3] = t1.y;
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) o[v] = p[v];
+    }
+}
+
+template <int V, typename real>
+__device__ __forceinline__ void st_v(real *p, const real *o) {
+    if constexpr (V == 4 && sizeof(real) == 4) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else if constexpr (V == 4 && sizeof(real) == 8) {
+        reinterpret_cast<double2 *>(p)[0] = make_double2(o[0], o[1]);
+        reinterpret_cast<double2 *>(p)[1] = make_double2(o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) p[v] = o[v];
+    }
+}
+
+// 2-vector (normals in 2-D) or scalar loads
+template <int D, typename real>
+__device__ __forceinline__ void ldg_n(const real *__restrict__ p, real *o) {
+    if constexpr (D == 2 && sizeof(real) == 4) {
+        const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else if constexpr (D == 2 && sizeof(real) == 8) {
+        const double2 t = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = t.x; o[1] = t.y;
+    } else {
+#pragma unroll
+        for (int d = 0; d < D; ++d) o[d] = __ldg(p + d);
+    }
+}
+
+// value at flux point f of the degree-p interpolant along its line
+template <int D, int N, int V, typename real>
+__device__ __forceinline__ void interp_line(const real *sX, int j, int f, const real *Lm, const real *Lp,
+                                            real *out) {
+    using G = Geo<D, N>;
+    int k, side;
+    const int base = G::line_base(f, k, side);
+    const int st = G::stride(k);
+    const real *L = side ? Lp : Lm;
+#pragma unroll
+    for (int v = 0; v < V; ++v) out[v] = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        real x[V];
+        ld_v<V>(sX + (j * G::NSP + base + m * st) * V, x);
+        const real c = L[m];
+#pragma unroll
+        for (int v = 0; v < V; ++v) out[v] += c * x[v];
+    }
+}
+
+// minimum CTAs per SM requested from the register allocator
+template <int D, typename real>
+struct MinBlocks {
+    static constexpr int value = sizeof(real) == 8 ? 1 : (D == 2 ? 5 : 2);
+};
+
+// --------------------------------------------------------------------------
 // K_GRAD: BR2 face gradient Q = interp((1/J) S^T D u) + eta r_f and the
 // viscous normal flux at every flux point (own side on connected points, the
 // common flux on boundary points).  With a.force != 0 it runs over the wall
 // element list and accumulates the wall force instead.
+//
+// Global gathers of the face data (partner index, normal, partner face
+// state) are issued before the tile barrier so that their latency overlaps
+// the tile load.
 // --------------------------------------------------------------------------
 template <int D, int N, typename real>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS)
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, MinBlocks<D, real>::value)
 k_grad(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
+    constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
     real *sU = sOp + pad4(N * N + 4 * N);
@@ -388,60 +483,62 @@ k_grad(const KArgs<real> a) {
     const int64_t e_end = a.elem0 + a.n_elem;
     if (e0 >= e_end) return;
     const int ne = (int)min((int64_t)NE, e_end - e0);
+    const int tid = threadIdx.x;
+
+    // face data of this thread's flux points, issued first
+    int32_t pt[IT];
+    real nr[IT][D], uR[IT][V];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        pt[it] = -1;
+        if (w < ne * NFP) {
+            const int64_t e = elem_of<real>(a.elist, e0, w / NFP);
+            const int64_t gf = e * NFP + w % NFP;
+            pt[it] = __ldg(a.PART + gf);
+            ldg_n<D>(a.NRM + gf * D, nr[it]);
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it)
+        if (pt[it] >= 0) ldg_v<V>(a.UFin + (int64_t)pt[it] * V, uR[it]);
     load_ops(a, sOp, N);
     load_tile(sU, a.U, a.elist, e0, ne, NSP * V);
     load_tile(sM, a.MET, a.elist, e0, ne, NSP * MS);
     __syncthreads();
 
     // face phase: jumps u_c - u_f and the state used in the viscous flux
-    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
-        const int64_t e = elem_of<real>(a.elist, e0, j);
-        int k, side;
-        const int base = G::line_base(f, k, side);
-        const int st = G::stride(k);
-        const real *L = side ? Lp : Lm;
         real uL[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) uL[v] = 0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const real c = L[m];
-            const real *src = sU + (j * NSP + base + m * st) * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) uL[v] += c * src[v];
-        }
-        const int32_t pt = a.PART[e * NFP + f];
+        interp_line<D, N, V>(sU, j, f, Lm, Lp, uL);
         real uc[V], ub[V];
-        if (pt >= 0) {
-            const real *src = a.UFin + (int64_t)pt * V;
+        if (pt[it] >= 0) {
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                uc[v] = real(0.5) * (uL[v] + src[v]);
+                uc[v] = real(0.5) * (uL[v] + uR[it][v]);
                 ub[v] = uL[v];
             }
         } else {
-            const int b = -1 - pt;
-            real n[D], vref[D], ug[V];
+            const int b = -1 - pt[it];
+            real vref[D], ug[V];
 #pragma unroll
-            for (int d = 0; d < D; ++d) {
-                n[d] = a.NRM[(e * NFP + f) * D + d];
-                vref[d] = a.BVREF[(int64_t)b * D + d];
-            }
-            bc_states<D>(a.BTAG[b], uL, n, vref, a.gamma, a.rho_inf, a.p_inf, ug, ub);
+            for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d];
+            bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, ug, ub);
 #pragma unroll
             for (int v = 0; v < V; ++v) uc[v] = ub[v];
         }
-        real *dD = sD + (j * NFP + f) * V;
-        real *dB = sB + (j * NFP + f) * V;
+        real dd[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            dD[v] = uc[v] - uL[v];
-            dB[v] = ub[v];
-        }
+        for (int v = 0; v < V; ++v) dd[v] = uc[v] - uL[v];
+        st_v<V>(sD + (j * NFP + f) * V, dd);
+        st_v<V>(sB + (j * NFP + f) * V, ub);
     }
     // solution-point phase: uncorrected physical gradient (1/J) S^T D u
-    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+    for (int w = tid; w < ne * NSP; w += blockDim.x) {
         const int j = w / NSP, s = w % NSP;
         const real *M = sM + (j * NSP + s) * MS;
         const real iJ = M[D * D];
@@ -455,25 +552,33 @@ k_grad(const KArgs<real> a) {
             for (int v = 0; v < V; ++v) Gk[k][v] = 0;
 #pragma unroll
             for (int m = 0; m < N; ++m) {
+                real x[V];
+                ld_v<V>(src + m * st * V, x);
                 const real c = row[m];
 #pragma unroll
-                for (int v = 0; v < V; ++v) Gk[k][v] += c * src[m * st * V + v];
+                for (int v = 0; v < V; ++v) Gk[k][v] += c * x[v];
             }
         }
         real *dst = sGD + (j * NSP + s) * D * V;
 #pragma unroll
-        for (int jd = 0; jd < D; ++jd)
+        for (int jd = 0; jd < D; ++jd) {
+            real g[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                real g = 0;
+                real t = 0;
 #pragma unroll
-                for (int k = 0; k < D; ++k) g += M[k * D + jd] * Gk[k][v];
-                dst[jd * V + v] = g * iJ;
+                for (int k = 0; k < D; ++k) t += M[k * D + jd] * Gk[k][v];
+                g[v] = t * iJ;
             }
+            st_v<V>(dst + jd * V, g);
+        }
     }
     __syncthreads();
     // face phase: Q and the viscous normal flux
-    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         const int64_t e = elem_of<real>(a.elist, e0, j);
         int k, side;
@@ -498,36 +603,33 @@ k_grad(const KArgs<real> a) {
 #pragma unroll
             for (int jd = 0; jd < D; ++jd) {
                 lf[jd] += cg * M[k * D + jd];
+                real g[V];
+                ld_v<V>(gd + jd * V, g);
 #pragma unroll
-                for (int v = 0; v < V; ++v) Q[jd][v] += c * gd[jd * V + v];
+                for (int v = 0; v < V; ++v) Q[jd][v] += c * g[v];
             }
         }
-        const real *dD = sD + (j * NFP + f) * V;
+        real dd[V], ub[V];
+        ld_v<V>(sD + (j * NFP + f) * V, dd);
+        ld_v<V>(sB + (j * NFP + f) * V, ub);
 #pragma unroll
         for (int jd = 0; jd < D; ++jd)
 #pragma unroll
-            for (int v = 0; v < V; ++v) Q[jd][v] += a.eta * lf[jd] * dD[v];
-        const real *ub = sB + (j * NFP + f) * V;
+            for (int v = 0; v < V; ++v) Q[jd][v] += a.eta * lf[jd] * dd[v];
         real Fv[D][V];
         flux_vis<D>(ub, Q, a.gamma, a.mu, a.prandtl, Fv);
-        real n[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) n[d] = a.NRM[(e * NFP + f) * D + d];
         real fvn[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             real t = 0;
 #pragma unroll
-            for (int d = 0; d < D; ++d) t += Fv[d][v] * n[d];
+            for (int d = 0; d < D; ++d) t += Fv[d][v] * nr[it][d];
             fvn[v] = t;
         }
-        const int32_t pt = a.PART[e * NFP + f];
-        const bool wall = pt < 0 && a.BTAG[-1 - pt] == BC_WALL;
+        const bool wall = pt[it] < 0 && a.BTAG[-1 - pt[it]] == BC_WALL;
         if (wall) fvn[V - 1] = 0;
         if (!a.force) {
-            real *dst = a.FV + (e * NFP + f) * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) dst[v] = fvn[v];
+            st_v<V>(a.FV + (e * NFP + f) * V, fvn);
         } else if (wall) {
             // face quadrature weight: product of the free directions' weights
             const int l = f % G::NFPF;
@@ -537,7 +639,7 @@ k_grad(const KArgs<real> a) {
             const int inst = a.EINST[e];
 #pragma unroll
             for (int d = 0; d < D; ++d)
-                atomicAdd(&a.force_acc[inst * 3 + d], wf * ((double)p * (double)n[d] - (double)fvn[1 + d]));
+                atomicAdd(&a.force_acc[inst * 3 + d], wf * ((double)p * (double)nr[it][d] - (double)fvn[1 + d]));
         }
     }
 }
@@ -546,10 +648,12 @@ k_grad(const KArgs<real> a) {
 // K_FLUX: fused common flux + transformed flux + divergence/correction + RK
 // --------------------------------------------------------------------------
 template <int D, int N, typename real, bool VISC>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS)
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, MinBlocks<D, real>::value)
 k_flux(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
+    constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
+    constexpr int ITS = (NE * NSP + G::THREADS - 1) / G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
     real *sU = sOp + pad4(N * N + 4 * N);
@@ -563,79 +667,98 @@ k_flux(const KArgs<real> a) {
     const int64_t e_end = a.elem0 + a.n_elem;
     if (e0 >= e_end) return;
     const int ne = (int)min((int64_t)NE, e_end - e0);
+    const int tid = threadIdx.x;
+    const int mode = a.mode;
+
+    // face data of this thread's flux points, issued first
+    int32_t pt[IT];
+    real nr[IT][D], uR[IT][V], fv[IT][V];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        pt[it] = -1;
+        if (w < ne * NFP) {
+            const int64_t gf = (e0 + w / NFP) * NFP + w % NFP;
+            pt[it] = __ldg(a.PART + gf);
+            ldg_n<D>(a.NRM + gf * D, nr[it]);
+            if (VISC) ldg_v<V>(a.FV + gf * V, fv[it]);
+        } else {
+            pt[it] = INT32_MIN;
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        if (pt[it] >= 0) {
+            ldg_v<V>(a.UFin + (int64_t)pt[it] * V, uR[it]);
+            if (VISC) {
+                real fp[V];
+                ldg_v<V>(a.FV + (int64_t)pt[it] * V, fp);
+#pragma unroll
+                for (int v = 0; v < V; ++v) fv[it][v] = real(0.5) * (fv[it][v] - fp[v]);
+            }
+        }
+    }
+    // RK registers of this thread's solution points
+    real r1[ITS][V], r2[ITS][V];
+    const bool need_r1 = mode == M_LSRK || mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
+    const bool need_r2 = mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
+#pragma unroll
+    for (int it = 0; it < ITS; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w < ne * NSP) {
+            const int64_t g = ((e0 + w / NSP) * NSP + w % NSP) * V;
+            if (need_r1) ld_v<V>(a.R1 + g, r1[it]);
+            if (need_r2) ld_v<V>(a.R2 + g, r2[it]);
+        }
+    }
     load_ops(a, sOp, N);
     load_tile(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP * V);
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
     __syncthreads();
 
     // 1) common normal flux at every own flux point
-    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
-        const int64_t e = e0 + j;
-        int k, side;
-        const int base = G::line_base(f, k, side);
-        const int st = G::stride(k);
-        const real *L = side ? Lp : Lm;
         real uL[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) uL[v] = 0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const real c = L[m];
-            const real *src = sU + (j * NSP + base + m * st) * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) uL[v] += c * src[v];
-        }
-        real n[D];
-#pragma unroll
-        for (int d = 0; d < D; ++d) n[d] = a.NRM[(e * NFP + f) * D + d];
-        const int32_t pt = a.PART[e * NFP + f];
-        real uR[V], ub[V];
-        if (pt >= 0) {
-            const real *src = a.UFin + (int64_t)pt * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) uR[v] = src[v];
-        } else {
-            const int b = -1 - pt;
+        interp_line<D, N, V>(sU, j, f, Lm, Lp, uL);
+        real ub[V], ug[V];
+        const real *uRp = uR[it];
+        if (pt[it] < 0) {
+            const int b = -1 - pt[it];
             real vref[D];
 #pragma unroll
             for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d];
-            bc_states<D>(a.BTAG[b], uL, n, vref, a.gamma, a.rho_inf, a.p_inf, uR, ub);
+            bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, ug, ub);
+            uRp = ug;
         }
         real Fs[V];
-        rusanov<D>(uL, uR, n, a.gamma, Fs);
+        rusanov<D>(uL, uRp, nr[it], a.gamma, Fs);
         if (VISC) {
-            const real *fo = a.FV + (e * NFP + f) * V;
-            real *dD = sD + (j * NFP + f) * V;
-            if (pt >= 0) {
-                const real *fp = a.FV + (int64_t)pt * V;
+            real dd[V];
+            if (pt[it] >= 0) {
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    Fs[v] -= real(0.5) * (fo[v] - fp[v]);
-                    dD[v] = real(0.5) * (uL[v] + uR[v]) - uL[v];
-                }
+                for (int v = 0; v < V; ++v) dd[v] = real(0.5) * (uL[v] + uRp[v]) - uL[v];
             } else {
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    Fs[v] -= fo[v];
-                    dD[v] = ub[v] - uL[v];
-                }
+                for (int v = 0; v < V; ++v) dd[v] = ub[v] - uL[v];
             }
-        }
-        real *dC = sC + (j * NFP + f) * V;
 #pragma unroll
-        for (int v = 0; v < V; ++v) dC[v] = Fs[v];
+            for (int v = 0; v < V; ++v) Fs[v] -= fv[it][v];
+            st_v<V>(sD + (j * NFP + f) * V, dd);
+        }
+        st_v<V>(sC + (j * NFP + f) * V, Fs);
     }
     if (VISC) __syncthreads();
 
     // 2) transformed flux at the solution points
-    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+    for (int w = tid; w < ne * NSP; w += blockDim.x) {
         const int j = w / NSP, s = w % NSP;
         const real *M = sM + (j * NSP + s) * MS;
-        const real *u = sU + (j * NSP + s) * V;
         real uu[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) uu[v] = u[v];
+        ld_v<V>(sU + (j * NSP + s) * V, uu);
         real F[D][V];
         flux_inv<D>(uu, a.gamma - real(1), F);
         if (VISC) {
@@ -646,15 +769,18 @@ k_flux(const KArgs<real> a) {
                 const int ik = G::digit(s, k), st = G::stride(k);
                 const real *row = D1 + ik * N;
                 const real *src = sU + (j * NSP + s - ik * st) * V;
-                const real *dm = sD + (j * NFP + G::fp_of(s, k, 0)) * V;
-                const real *dp = sD + (j * NFP + G::fp_of(s, k, 1)) * V;
+                real dm[V], dp[V];
+                ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 0)) * V, dm);
+                ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 1)) * V, dp);
 #pragma unroll
                 for (int v = 0; v < V; ++v) Gk[k][v] = GL[ik] * dm[v] + GR[ik] * dp[v];
 #pragma unroll
                 for (int m = 0; m < N; ++m) {
+                    real x[V];
+                    ld_v<V>(src + m * st * V, x);
                     const real c = row[m];
 #pragma unroll
-                    for (int v = 0; v < V; ++v) Gk[k][v] += c * src[m * st * V + v];
+                    for (int v = 0; v < V; ++v) Gk[k][v] += c * x[v];
                 }
             }
             real gr[D][V];
@@ -676,20 +802,24 @@ k_flux(const KArgs<real> a) {
         }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
-            real *dst = sF + ((j * D + k) * NSP + s) * V;
+            real t[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                real t = 0;
+                real acc = 0;
 #pragma unroll
-                for (int jd = 0; jd < D; ++jd) t += M[k * D + jd] * F[jd][v];
-                dst[v] = t;
+                for (int jd = 0; jd < D; ++jd) acc += M[k * D + jd] * F[jd][v];
+                t[v] = acc;
             }
+            st_v<V>(sF + ((j * D + k) * NSP + s) * V, t);
         }
     }
     __syncthreads();
 
     // 3) jump = common - discontinuous normal flux (flux polynomial at the face)
-    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         int k, side;
         const int base = G::line_base(f, k, side);
@@ -700,24 +830,30 @@ k_flux(const KArgs<real> a) {
         for (int v = 0; v < V; ++v) fd[v] = 0;
 #pragma unroll
         for (int m = 0; m < N; ++m) {
+            real x[V];
+            ld_v<V>(sF + ((j * D + k) * NSP + base + m * st) * V, x);
             const real c = L[m];
-            const real *src = sF + ((j * D + k) * NSP + base + m * st) * V;
 #pragma unroll
-            for (int v = 0; v < V; ++v) fd[v] += c * src[v];
+            for (int v = 0; v < V; ++v) fd[v] += c * x[v];
         }
-        real *dC = sC + (j * NFP + f) * V;
+        real cc[V];
+        ld_v<V>(sC + (j * NFP + f) * V, cc);
         if (side) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) dC[v] -= fd[v];
+            for (int v = 0; v < V; ++v) cc[v] -= fd[v];
         } else {
 #pragma unroll
-            for (int v = 0; v < V; ++v) dC[v] += fd[v];
+            for (int v = 0; v < V; ++v) cc[v] += fd[v];
         }
+        st_v<V>(sC + (j * NFP + f) * V, cc);
     }
     __syncthreads();
 
     // 4) divergence + correction, residual, RK update
-    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < ITS; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NSP) continue;
         const int j = w / NSP, s = w % NSP;
         const int64_t e = e0 + j;
         real div[V];
@@ -730,105 +866,76 @@ k_flux(const KArgs<real> a) {
             const real *src = sF + ((j * D + k) * NSP + s - ik * st) * V;
 #pragma unroll
             for (int m = 0; m < N; ++m) {
+                real x[V];
+                ld_v<V>(src + m * st * V, x);
                 const real c = row[m];
 #pragma unroll
-                for (int v = 0; v < V; ++v) div[v] += c * src[m * st * V + v];
+                for (int v = 0; v < V; ++v) div[v] += c * x[v];
             }
-            const real *jm = sC + (j * NFP + G::fp_of(s, k, 0)) * V;
-            const real *jp = sC + (j * NFP + G::fp_of(s, k, 1)) * V;
+            real jm[V], jp[V];
+            ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 0)) * V, jm);
+            ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 1)) * V, jp);
 #pragma unroll
             for (int v = 0; v < V; ++v) div[v] += GR[ik] * jp[v] - GL[ik] * jm[v];
         }
         const real iJ = sM[(j * NSP + s) * MS + D * D];
         const int64_t g = (e * NSP + s) * V;
         real *su = sU + (j * NSP + s) * V;
-        switch (a.mode) {
-        case M_LSRK_FIRST:
+        real u0[V], un[V], R[V];
+        ld_v<V>(su, u0);
 #pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const real R = -div[v] * iJ;
-                const real dU = a.dt * R;
-                a.R1[g + v] = dU;
-                const real un = su[v] + a.rk_b * dU;
-                a.U[g + v] = un;
-                su[v] = un;
-            }
-            break;
-        case M_LSRK:
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const real R = -div[v] * iJ;
-                const real dU = a.rk_a * a.R1[g + v] + a.dt * R;
-                a.R1[g + v] = dU;
-                const real un = su[v] + a.rk_b * dU;
-                a.U[g + v] = un;
-                su[v] = un;
-            }
-            break;
-        case M_RK4_1:
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const real R = -div[v] * iJ;
-                a.R1[g + v] = su[v];
-                a.R2[g + v] = R;
-                const real un = su[v] + a.rk_c * R;
-                a.U[g + v] = un;
-                su[v] = un;
-            }
-            break;
-        case M_RK4_2:
-        case M_RK4_3:
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const real R = -div[v] * iJ;
-                a.R2[g + v] = a.R2[g + v] + real(2) * R;
-                const real un = a.R1[g + v] + a.rk_c * R;
-                a.U[g + v] = un;
-                su[v] = un;
-            }
-            break;
-        case M_RK4_4:
-#pragma unroll
-            for (int v = 0; v < V; ++v) {
-                const real R = -div[v] * iJ;
-                const real un = a.R1[g + v] + a.rk_c * (a.R2[g + v] + R);
-                a.U[g + v] = un;
-                su[v] = un;
-            }
-            break;
-        case M_RESIDUAL:
-#pragma unroll
-            for (int v = 0; v < V; ++v) a.RES[g + v] = -div[v] * iJ;
-            break;
-        default:  // M_RESIDUAL_J
-#pragma unroll
-            for (int v = 0; v < V; ++v) a.RES[g + v] = -div[v];
-            break;
+        for (int v = 0; v < V; ++v) R[v] = -div[v] * iJ;
+        if (mode == M_RESIDUAL) {
+            st_v<V>(a.RES + g, R);
+            continue;
         }
+        if (mode == M_RESIDUAL_J) {
+            real jr[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) jr[v] = -div[v];
+            st_v<V>(a.RES + g, jr);
+            continue;
+        }
+        if (mode == M_LSRK_FIRST || mode == M_LSRK) {
+            real dU[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                dU[v] = (mode == M_LSRK) ? a.rk_a * r1[it][v] + a.dt * R[v] : a.dt * R[v];
+                un[v] = u0[v] + a.rk_b * dU[v];
+            }
+            st_v<V>(a.R1 + g, dU);
+        } else if (mode == M_RK4_1) {
+            st_v<V>(a.R1 + g, u0);
+            st_v<V>(a.R2 + g, R);
+#pragma unroll
+            for (int v = 0; v < V; ++v) un[v] = u0[v] + a.rk_c * R[v];
+        } else if (mode == M_RK4_2 || mode == M_RK4_3) {
+            real acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                acc[v] = r2[it][v] + real(2) * R[v];
+                un[v] = r1[it][v] + a.rk_c * R[v];
+            }
+            st_v<V>(a.R2 + g, acc);
+        } else {  // M_RK4_4
+#pragma unroll
+            for (int v = 0; v < V; ++v) un[v] = r1[it][v] + a.rk_c * (r2[it][v] + R[v]);
+        }
+        st_v<V>(a.U + g, un);
+        st_v<V>(su, un);
     }
-    if (a.mode == M_RESIDUAL || a.mode == M_RESIDUAL_J) return;
+    if (mode == M_RESIDUAL || mode == M_RESIDUAL_J) return;
     __syncthreads();
 
     // 5) face values of the new state for the next stage
-    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
-        int k, side;
-        const int base = G::line_base(f, k, side);
-        const int st = G::stride(k);
-        const real *L = side ? Lp : Lm;
         real uf[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) uf[v] = 0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const real c = L[m];
-            const real *src = sU + (j * NSP + base + m * st) * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) uf[v] += c * src[v];
-        }
-        real *dst = a.UFout + ((e0 + j) * NFP + f) * V;
-#pragma unroll
-        for (int v = 0; v < V; ++v) dst[v] = uf[v];
+        interp_line<D, N, V>(sU, j, f, Lm, Lp, uf);
+        st_v<V>(a.UFout + ((e0 + j) * NFP + f) * V, uf);
     }
 }
 
