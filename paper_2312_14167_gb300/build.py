@@ -36,6 +36,11 @@ def _flags(debug=False):
                 "--expt-relaxed-constexpr", "-Xptxas", "-O3"]
     if os.environ.get("FR_PTXAS_VERBOSE"):
         f += ["-Xptxas", "-v"]
+    # tuning knobs for sweeps: minimum CTAs per SM asked of the register
+    # allocator for the 2-D FP32 stage kernels
+    for knob in ("FR_MINB_FLUX_2D_F32", "FR_MINB_GRAD_2D_F32"):
+        if os.environ.get(knob):
+            f += [f"-D{knob}={int(os.environ[knob])}"]
     return f
 
 

@@ -77,8 +77,8 @@ struct KArgs {
     int64_t elem0;             // first element of the launch range
     const int32_t *elist;      // optional element list (force sampling)
     real *U, *R1, *R2, *RES;
-    const real *UFin;
-    real *UFout;
+    const real *UFin;          // [E][NFP][V] inbound: the partner's face state at each own point
+    real *UFout;               // next stage's inbound buffer (written through the partner index)
     real *FV;
     const real *MET;           // [E][NSP][D*D+1]: S[k][j] = J dxi_k/dx_j, then 1/J
     const real *NRM;           // [E][NFP][D] outward normal * |dS|
@@ -449,9 +449,19 @@ __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const 
 }
 
 // minimum CTAs per SM requested from the register allocator
-template <int D, typename real>
+// Measured on the 32-airfoil poll (2-D, p=3, FP32): the flux kernel is
+// fastest at 6 resident CTAs (40 registers, a few spills), the gradient
+// kernel at 8 (32 registers, no spills).
+#ifndef FR_MINB_FLUX_2D_F32
+#define FR_MINB_FLUX_2D_F32 6
+#endif
+#ifndef FR_MINB_GRAD_2D_F32
+#define FR_MINB_GRAD_2D_F32 8
+#endif
+template <int D, typename real, bool GRAD = false>
 struct MinBlocks {
-    static constexpr int value = sizeof(real) == 8 ? 1 : (D == 2 ? 5 : 2);
+    static constexpr int value =
+        sizeof(real) == 8 ? 1 : (D == 2 ? (GRAD ? FR_MINB_GRAD_2D_F32 : FR_MINB_FLUX_2D_F32) : 2);
 };
 
 // --------------------------------------------------------------------------
@@ -465,7 +475,7 @@ struct MinBlocks {
 // the tile load.
 // --------------------------------------------------------------------------
 template <int D, int N, typename real>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, MinBlocks<D, real>::value)
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true>::value))
 k_grad(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
@@ -485,7 +495,9 @@ k_grad(const KArgs<real> a) {
     const int ne = (int)min((int64_t)NE, e_end - e0);
     const int tid = threadIdx.x;
 
-    // face data of this thread's flux points, issued first
+    // face data of this thread's flux points, issued first: partner index,
+    // normal and the partner's face state, which the partner stored in this
+    // element's inbound slot (no dependent gather)
     int32_t pt[IT];
     real nr[IT][D], uR[IT][V];
 #pragma unroll
@@ -497,11 +509,9 @@ k_grad(const KArgs<real> a) {
             const int64_t gf = e * NFP + w % NFP;
             pt[it] = __ldg(a.PART + gf);
             ldg_n<D>(a.NRM + gf * D, nr[it]);
+            ldg_v<V>(a.UFin + gf * V, uR[it]);
         }
     }
-#pragma unroll
-    for (int it = 0; it < IT; ++it)
-        if (pt[it] >= 0) ldg_v<V>(a.UFin + (int64_t)pt[it] * V, uR[it]);
     load_ops(a, sOp, N);
     load_tile(sU, a.U, a.elist, e0, ne, NSP * V);
     load_tile(sM, a.MET, a.elist, e0, ne, NSP * MS);
@@ -670,7 +680,9 @@ k_flux(const KArgs<real> a) {
     const int tid = threadIdx.x;
     const int mode = a.mode;
 
-    // face data of this thread's flux points, issued first
+    // face data of this thread's flux points, issued first: partner index,
+    // normal, the partner's face state from this element's inbound slot, own
+    // viscous normal flux; then the partner's viscous normal flux
     int32_t pt[IT];
     real nr[IT][D], uR[IT][V], fv[IT][V];
 #pragma unroll
@@ -681,6 +693,7 @@ k_flux(const KArgs<real> a) {
             const int64_t gf = (e0 + w / NFP) * NFP + w % NFP;
             pt[it] = __ldg(a.PART + gf);
             ldg_n<D>(a.NRM + gf * D, nr[it]);
+            ldg_v<V>(a.UFin + gf * V, uR[it]);
             if (VISC) ldg_v<V>(a.FV + gf * V, fv[it]);
         } else {
             pt[it] = INT32_MIN;
@@ -689,7 +702,6 @@ k_flux(const KArgs<real> a) {
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
         if (pt[it] >= 0) {
-            ldg_v<V>(a.UFin + (int64_t)pt[it] * V, uR[it]);
             if (VISC) {
                 real fp[V];
                 ldg_v<V>(a.FV + (int64_t)pt[it] * V, fp);
@@ -815,41 +827,10 @@ k_flux(const KArgs<real> a) {
     }
     __syncthreads();
 
-    // 3) jump = common - discontinuous normal flux (flux polynomial at the face)
-#pragma unroll
-    for (int it = 0; it < IT; ++it) {
-        const int w = tid + it * G::THREADS;
-        if (w >= ne * NFP) continue;
-        const int j = w / NFP, f = w % NFP;
-        int k, side;
-        const int base = G::line_base(f, k, side);
-        const int st = G::stride(k);
-        const real *L = side ? Lp : Lm;
-        real fd[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) fd[v] = 0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            real x[V];
-            ld_v<V>(sF + ((j * D + k) * NSP + base + m * st) * V, x);
-            const real c = L[m];
-#pragma unroll
-            for (int v = 0; v < V; ++v) fd[v] += c * x[v];
-        }
-        real cc[V];
-        ld_v<V>(sC + (j * NFP + f) * V, cc);
-        if (side) {
-#pragma unroll
-            for (int v = 0; v < V; ++v) cc[v] -= fd[v];
-        } else {
-#pragma unroll
-            for (int v = 0; v < V; ++v) cc[v] += fd[v];
-        }
-        st_v<V>(sC + (j * NFP + f) * V, cc);
-    }
-    __syncthreads();
-
-    // 4) divergence + correction, residual, RK update
+    // 3) divergence + correction, residual, RK update.  Along each line the
+    // same loaded values give the derivative and the flux polynomial at both
+    // ends; jump = common normal flux - discontinuous normal flux, where the
+    // - face's outward normal flux is minus the polynomial's value there.
 #pragma unroll
     for (int it = 0; it < ITS; ++it) {
         const int w = tid + it * G::THREADS;
@@ -864,19 +845,26 @@ k_flux(const KArgs<real> a) {
             const int ik = G::digit(s, k), st = G::stride(k);
             const real *row = D1 + ik * N;
             const real *src = sF + ((j * D + k) * NSP + s - ik * st) * V;
+            real fm[V], fp[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) { fm[v] = 0; fp[v] = 0; }
 #pragma unroll
             for (int m = 0; m < N; ++m) {
                 real x[V];
                 ld_v<V>(src + m * st * V, x);
-                const real c = row[m];
+                const real c = row[m], cm = Lm[m], cp = Lp[m];
 #pragma unroll
-                for (int v = 0; v < V; ++v) div[v] += c * x[v];
+                for (int v = 0; v < V; ++v) {
+                    div[v] += c * x[v];
+                    fm[v] += cm * x[v];
+                    fp[v] += cp * x[v];
+                }
             }
             real jm[V], jp[V];
             ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 0)) * V, jm);
             ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 1)) * V, jp);
 #pragma unroll
-            for (int v = 0; v < V; ++v) div[v] += GR[ik] * jp[v] - GL[ik] * jm[v];
+            for (int v = 0; v < V; ++v) div[v] += GR[ik] * (jp[v] - fp[v]) - GL[ik] * (jm[v] + fm[v]);
         }
         const real iJ = sM[(j * NSP + s) * MS + D * D];
         const int64_t g = (e * NSP + s) * V;
@@ -927,15 +915,16 @@ k_flux(const KArgs<real> a) {
     if (mode == M_RESIDUAL || mode == M_RESIDUAL_J) return;
     __syncthreads();
 
-    // 5) face values of the new state for the next stage
+    // 4) face values of the new state, stored in the partner's inbound slot
+    // for the next stage (boundary points have no partner)
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
         const int w = tid + it * G::THREADS;
-        if (w >= ne * NFP) continue;
+        if (w >= ne * NFP || pt[it] < 0) continue;
         const int j = w / NFP, f = w % NFP;
         real uf[V];
         interp_line<D, N, V>(sU, j, f, Lm, Lp, uf);
-        st_v<V>(a.UFout + ((e0 + j) * NFP + f) * V, uf);
+        st_v<V>(a.UFout + (int64_t)pt[it] * V, uf);
     }
 }
 
@@ -960,23 +949,11 @@ k_interp(const KArgs<real> a) {
     __syncthreads();
     for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
         const int j = w / NFP, f = w % NFP;
-        int k, side;
-        const int base = G::line_base(f, k, side);
-        const int st = G::stride(k);
-        const real *L = side ? Lp : Lm;
+        const int32_t pt = a.PART[(e0 + j) * NFP + f];
+        if (pt < 0) continue;
         real uf[V];
-#pragma unroll
-        for (int v = 0; v < V; ++v) uf[v] = 0;
-#pragma unroll
-        for (int m = 0; m < N; ++m) {
-            const real c = L[m];
-            const real *src = sU + (j * NSP + base + m * st) * V;
-#pragma unroll
-            for (int v = 0; v < V; ++v) uf[v] += c * src[v];
-        }
-        real *dst = a.UFout + ((e0 + j) * NFP + f) * V;
-#pragma unroll
-        for (int v = 0; v < V; ++v) dst[v] = uf[v];
+        interp_line<D, N, V>(sU, j, f, Lm, Lp, uf);
+        st_v<V>(a.UFout + (int64_t)pt * V, uf);
     }
 }
 
