@@ -128,6 +128,15 @@ struct Geo {
     static constexpr int THREADS = ((NE * NSP + 31) / 32) * 32;
 
     __device__ __forceinline__ static int stride(int k) { return k == 0 ? 1 : (k == 1 ? N : N * N); }
+    // Shared-memory vector slot of point i (element-major) with one pad slot
+    // after every row of N points: the points a quarter-warp reads along a
+    // line in either direction then fall in different banks.
+    __host__ __device__ __forceinline__ static constexpr int prow(int i) { return i + i / N; }
+    static constexpr int PROWS = NSP + NSP / N;   // padded slots per element
+    template <bool PAD>
+    __host__ __device__ __forceinline__ static constexpr int slot(int i) { return PAD ? i + i / N : i; }
+    template <bool PAD>
+    static constexpr int slots() { return PAD ? PROWS : NSP; }
     __device__ __forceinline__ static int digit(int s, int k) { return (s / stride(k)) % N; }
     // flux point at the end (side 0: -1, 1: +1) of the k-line through s
     __device__ __forceinline__ static int fp_of(int s, int k, int side) {
@@ -427,8 +436,21 @@ __device__ __forceinline__ void ldg_n(const real *__restrict__ p, real *o) {
     }
 }
 
+// one V-vector per solution point into the row-padded shared layout
+template <int N, int V, bool PAD, typename real>
+__device__ __forceinline__ void load_state_rows(real *dst, const real *src, const int32_t *elist,
+                                                int64_t e0, int ne, int nsp) {
+    for (int i = threadIdx.x; i < ne * nsp; i += blockDim.x) {
+        const int j = i / nsp, s = i % nsp;
+        const int64_t e = elist ? (int64_t)elist[e0 + j] : e0 + j;
+        real x[V];
+        ldg_v<V>(src + (e * nsp + s) * V, x);
+        st_v<V>(dst + (PAD ? i + i / N : i) * V, x);
+    }
+}
+
 // value at flux point f of the degree-p interpolant along its line
-template <int D, int N, int V, typename real>
+template <int D, int N, int V, bool PAD, typename real>
 __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const real *Lm, const real *Lp,
                                             real *out) {
     using G = Geo<D, N>;
@@ -441,7 +463,7 @@ __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const 
 #pragma unroll
     for (int m = 0; m < N; ++m) {
         real x[V];
-        ld_v<V>(sX + (j * G::NSP + base + m * st) * V, x);
+        ld_v<V>(sX + G::template slot<PAD>(j * G::NSP + base + m * st) * V, x);
         const real c = L[m];
 #pragma unroll
         for (int v = 0; v < V; ++v) out[v] += c * x[v];
@@ -483,10 +505,10 @@ k_grad(const KArgs<real> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
     real *sU = sOp + pad4(N * N + 4 * N);
-    real *sM = sU + pad4(NE * NSP * V);
+    real *sM = sU + pad4(NE * G::PROWS * V);
     real *sD = sM + pad4(NE * NSP * MS);
     real *sB = sD + pad4(NE * NFP * V);
-    real *sGD = sB + pad4(NE * NFP * V);
+    real *sGD = sB + pad4(NE * NFP * V);      // [j][s][jd][v], V pad floats per row
     const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N;
 
     const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
@@ -513,7 +535,7 @@ k_grad(const KArgs<real> a) {
         }
     }
     load_ops(a, sOp, N);
-    load_tile(sU, a.U, a.elist, e0, ne, NSP * V);
+    load_state_rows<N, V, true>(sU, a.U, a.elist, e0, ne, NSP);
     load_tile(sM, a.MET, a.elist, e0, ne, NSP * MS);
     __syncthreads();
 
@@ -524,7 +546,7 @@ k_grad(const KArgs<real> a) {
         if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         real uL[V];
-        interp_line<D, N, V>(sU, j, f, Lm, Lp, uL);
+        interp_line<D, N, V, true>(sU, j, f, Lm, Lp, uL);
         real uc[V], ub[V];
         if (pt[it] >= 0) {
 #pragma unroll
@@ -557,19 +579,19 @@ k_grad(const KArgs<real> a) {
         for (int k = 0; k < D; ++k) {
             const int ik = G::digit(s, k), st = G::stride(k);
             const real *row = D1 + ik * N;
-            const real *src = sU + (j * NSP + s - ik * st) * V;
+            const int q0 = j * NSP + s - ik * st;
 #pragma unroll
             for (int v = 0; v < V; ++v) Gk[k][v] = 0;
 #pragma unroll
             for (int m = 0; m < N; ++m) {
                 real x[V];
-                ld_v<V>(src + m * st * V, x);
+                ld_v<V>(sU + G::prow(q0 + m * st) * V, x);
                 const real c = row[m];
 #pragma unroll
                 for (int v = 0; v < V; ++v) Gk[k][v] += c * x[v];
             }
         }
-        real *dst = sGD + (j * NSP + s) * D * V;
+        real *dst = sGD + (j * NSP + s) * D * V + ((j * NSP + s) / N) * V;
 #pragma unroll
         for (int jd = 0; jd < D; ++jd) {
             real g[V];
@@ -607,7 +629,7 @@ k_grad(const KArgs<real> a) {
         for (int m = 0; m < N; ++m) {
             const int sp = base + m * st;
             const real c = L[m];
-            const real *gd = sGD + (j * NSP + sp) * D * V;
+            const real *gd = sGD + (j * NSP + sp) * D * V + ((j * NSP + sp) / N) * V;
             const real *M = sM + (j * NSP + sp) * MS;
             const real cg = c * Gs[m] * M[D * D];
 #pragma unroll
@@ -670,7 +692,7 @@ k_flux(const KArgs<real> a) {
     real *sM = sU + pad4(NE * NSP * V);
     real *sC = sM + pad4(NE * NSP * MS);
     real *sD = sC + pad4(NE * NFP * V);
-    real *sF = sD + (VISC ? pad4(NE * NFP * V) : 0);
+    real *sF = sD + (VISC ? pad4(NE * NFP * V) : 0);   // [j][k][s][v]
     const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N;
 
     const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
@@ -724,7 +746,7 @@ k_flux(const KArgs<real> a) {
         }
     }
     load_ops(a, sOp, N);
-    load_tile(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP * V);
+    load_state_rows<N, V, false>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
     __syncthreads();
 
@@ -735,7 +757,7 @@ k_flux(const KArgs<real> a) {
         if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         real uL[V];
-        interp_line<D, N, V>(sU, j, f, Lm, Lp, uL);
+        interp_line<D, N, V, false>(sU, j, f, Lm, Lp, uL);
         real ub[V], ug[V];
         const real *uRp = uR[it];
         if (pt[it] < 0) {
@@ -770,7 +792,7 @@ k_flux(const KArgs<real> a) {
         const int j = w / NSP, s = w % NSP;
         const real *M = sM + (j * NSP + s) * MS;
         real uu[V];
-        ld_v<V>(sU + (j * NSP + s) * V, uu);
+        ld_v<V>(sU + G::template slot<false>(j * NSP + s) * V, uu);
         real F[D][V];
         flux_inv<D>(uu, a.gamma - real(1), F);
         if (VISC) {
@@ -780,7 +802,7 @@ k_flux(const KArgs<real> a) {
             for (int k = 0; k < D; ++k) {
                 const int ik = G::digit(s, k), st = G::stride(k);
                 const real *row = D1 + ik * N;
-                const real *src = sU + (j * NSP + s - ik * st) * V;
+                const int q0 = j * NSP + s - ik * st;
                 real dm[V], dp[V];
                 ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 0)) * V, dm);
                 ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 1)) * V, dp);
@@ -789,7 +811,7 @@ k_flux(const KArgs<real> a) {
 #pragma unroll
                 for (int m = 0; m < N; ++m) {
                     real x[V];
-                    ld_v<V>(src + m * st * V, x);
+                    ld_v<V>(sU + G::template slot<false>(q0 + m * st) * V, x);
                     const real c = row[m];
 #pragma unroll
                     for (int v = 0; v < V; ++v) Gk[k][v] += c * x[v];
@@ -822,7 +844,7 @@ k_flux(const KArgs<real> a) {
                 for (int jd = 0; jd < D; ++jd) acc += M[k * D + jd] * F[jd][v];
                 t[v] = acc;
             }
-            st_v<V>(sF + ((j * D + k) * NSP + s) * V, t);
+            st_v<V>(sF + G::template slot<false>((j * D + k) * NSP + s) * V, t);
         }
     }
     __syncthreads();
@@ -844,14 +866,14 @@ k_flux(const KArgs<real> a) {
         for (int k = 0; k < D; ++k) {
             const int ik = G::digit(s, k), st = G::stride(k);
             const real *row = D1 + ik * N;
-            const real *src = sF + ((j * D + k) * NSP + s - ik * st) * V;
+            const int q0 = (j * D + k) * NSP + s - ik * st;
             real fm[V], fp[V];
 #pragma unroll
             for (int v = 0; v < V; ++v) { fm[v] = 0; fp[v] = 0; }
 #pragma unroll
             for (int m = 0; m < N; ++m) {
                 real x[V];
-                ld_v<V>(src + m * st * V, x);
+                ld_v<V>(sF + G::template slot<false>(q0 + m * st) * V, x);
                 const real c = row[m], cm = Lm[m], cp = Lp[m];
 #pragma unroll
                 for (int v = 0; v < V; ++v) {
@@ -868,7 +890,7 @@ k_flux(const KArgs<real> a) {
         }
         const real iJ = sM[(j * NSP + s) * MS + D * D];
         const int64_t g = (e * NSP + s) * V;
-        real *su = sU + (j * NSP + s) * V;
+        real *su = sU + G::template slot<false>(j * NSP + s) * V;
         real u0[V], un[V], R[V];
         ld_v<V>(su, u0);
 #pragma unroll
@@ -923,7 +945,7 @@ k_flux(const KArgs<real> a) {
         if (w >= ne * NFP || pt[it] < 0) continue;
         const int j = w / NFP, f = w % NFP;
         real uf[V];
-        interp_line<D, N, V>(sU, j, f, Lm, Lp, uf);
+        interp_line<D, N, V, false>(sU, j, f, Lm, Lp, uf);
         st_v<V>(a.UFout + (int64_t)pt[it] * V, uf);
     }
 }
@@ -945,14 +967,14 @@ k_interp(const KArgs<real> a) {
     if (e0 >= e_end) return;
     const int ne = (int)min((int64_t)NE, e_end - e0);
     load_ops(a, sOp, N);
-    load_tile(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP * V);
+    load_state_rows<N, V, false>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
     __syncthreads();
     for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
         const int j = w / NFP, f = w % NFP;
         const int32_t pt = a.PART[(e0 + j) * NFP + f];
         if (pt < 0) continue;
         real uf[V];
-        interp_line<D, N, V>(sU, j, f, Lm, Lp, uf);
+        interp_line<D, N, V, false>(sU, j, f, Lm, Lp, uf);
         st_v<V>(a.UFout + (int64_t)pt * V, uf);
     }
 }
@@ -1118,11 +1140,13 @@ size_t smem_bytes(int kind, bool visc) {
     using G = Geo<D, N>;
     constexpr int NE = G::NE, NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS;
     size_t n = pad4(N * N + 4 * N);
+    constexpr int PR = G::PROWS;   // k_grad uses the row-padded layout
     if (kind == K_FLUX) {
         n += pad4(NE * NSP * V) + pad4(NE * NSP * MS) + pad4(NE * NFP * V) * (visc ? 2 : 1) +
              pad4(NE * D * NSP * V);
     } else if (kind == K_GRAD) {
-        n += pad4(NE * NSP * V) + pad4(NE * NSP * MS) + 2 * pad4(NE * NFP * V) + pad4(NE * NSP * D * V);
+        n += pad4(NE * PR * V) + pad4(NE * NSP * MS) + 2 * pad4(NE * NFP * V) +
+             pad4(NE * NSP * D * V + NE * (NSP / N) * V);
     } else if (kind == K_INTERP) {
         n += pad4(NE * NSP * V);
     }
