@@ -56,7 +56,12 @@ WORKLOAD = ("32 NACA 4-digit O-meshes (8k-40k curved quads, seed 2312), p=3, NS 
 # DRAM traffic of one launch of the dominant kernel from an ncu capture,
 # per element, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    # "sha256 of fr_kernels.cuh": {"flux_bytes_per_elem": ..., "grad_bytes_per_elem": ...}
+    # dram__bytes_read.sum + dram__bytes_write.sum per element of one stage launch, ncu
+    # --set full on the 8-airfoil case (243,854 quads; see profiles/k_flux_airfoil8_full.md),
+    # scaled to a launch by the element count
+    "dcfa9ac0a49d66cf875235273ca393571a41e1e42e4909b2e383fe9edf4cb281":
+        {"flux_bytes_per_elem": (316.859904e6 + 154.2336e6) / 243854,
+         "grad_bytes_per_elem": (249.94304e6 + 44.918272e6) / 243854},
 }
 
 
