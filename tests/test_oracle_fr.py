@@ -336,3 +336,80 @@ def test_probe_at_solution_point_and_polynomial_field():
     pt = np.array([1.37, 0.61])
     pr = Probe(d, pt)
     assert np.allclose(pr.state(V), f(pt), atol=1e-13)
+
+
+def test_characteristic_boundary_state_carries_the_right_invariants():
+    """The ghost state keeps the outgoing invariant v_n + 2c/(gamma-1) of the
+    interior, takes the incoming invariant v_n - 2c/(gamma-1) of the reference
+    state, and the entropy p/rho^gamma and tangential velocity of the upwind
+    side."""
+    g = 1.4
+    ph = NavierStokes(2, rho_inf=1.0, v_inf=(1.0, 0.0), p_inf=1 / (g * 0.3 ** 2))
+    rng = np.random.default_rng(11)
+    uL = S.random_state(40, 1, 2, 0.3, amp=0.3, seed=3)[:, 0]
+    n = rng.normal(size=(40, 2))
+    nhat = n / np.linalg.norm(n, axis=1)[:, None]
+    vref = np.broadcast_to(ph.v_inf, (40, 2))
+    ub = ph.riemann_state(uL, nhat, vref)
+    rL, vL, pL = ph.primitives(uL)
+    rb, vb, pb = ph.primitives(ub)
+    cL, cb = np.sqrt(g * pL / rL), np.sqrt(g * pb / rb)
+    c_inf = np.sqrt(g * ph.p_inf / ph.rho_inf)
+    vnL, vnb, vnr = (np.sum(v * nhat, 1) for v in (vL, vb, vref))
+    assert np.allclose(vnb + 2 * cb / (g - 1), vnL + 2 * cL / (g - 1), rtol=1e-12)
+    assert np.allclose(vnb - 2 * cb / (g - 1), vnr - 2 * c_inf / (g - 1), rtol=1e-12, atol=1e-12)
+    out = vnb > 0
+    s_b = pb / rb ** g
+    assert np.allclose(s_b[out], (pL / rL ** g)[out], rtol=1e-12)
+    assert np.allclose(s_b[~out], ph.p_inf / ph.rho_inf ** g, rtol=1e-12)
+    tb = vb - vnb[:, None] * nhat
+    assert np.allclose(tb[out], (vL - vnL[:, None] * nhat)[out], atol=1e-12)
+    assert np.allclose(tb[~out], (vref - vnr[:, None] * nhat)[~out], atol=1e-12)
+
+
+def test_inflow_reference_state_is_the_tanh_profile():
+    """At an inflow point of height y the reference velocity is
+    U tanh(3 (y - y_wall) / delta) along the free stream: an interior state
+    equal to that reference passes through the characteristic construction
+    unchanged, and a state with the uniform free stream does not."""
+    delta, ywall, mach = 0.2, 0.1, 0.15
+    p_inf = 1 / (1.4 * mach ** 2)
+    ph = NavierStokes(2, rho_inf=1.0, v_inf=(1.0, 0.0), p_inf=p_inf, inflow_delta=delta,
+                      inflow_ywall=ywall)
+    y = np.linspace(ywall + 0.01, ywall + 1.0, 25)
+    x = np.stack([np.zeros_like(y), y], -1)
+    n = np.tile([-0.3, 0.0], (y.size, 1))              # inflow face, outward -x
+    prof = np.tanh(3.0 * (y - ywall) / delta)
+    uL = S.primitive_to_conserved(np.ones(y.size), np.stack([prof, 0 * y], -1), np.full(y.size, p_inf))
+    ghost, ub = ph.boundary_states(M.TAG_INFLOW, uL, n, x)
+    assert np.allclose(ghost, uL, rtol=1e-13, atol=1e-13)
+    assert np.allclose(ub, uL, rtol=1e-13, atol=1e-13)
+    uni = S.primitive_to_conserved(np.ones(y.size), np.stack([np.ones(y.size), 0 * y], -1),
+                                   np.full(y.size, p_inf))
+    g2, _ = ph.boundary_states(M.TAG_INFLOW, uni, n, x)
+    low = prof < 0.9
+    assert np.all(np.abs(g2[low, 1] - uni[low, 1]) > 1e-3)
+
+
+def test_wall_force_linear_shear_is_exact():
+    """u = a y over a flat no-slip wall at y = 0: the wall shear stress is
+    mu a, so the x-force on a wall of length L is mu a L (p uniform gives no
+    net x-force; the linear field is represented exactly for p >= 1)."""
+    a, mu, L = 0.7, 0.01, 2.0
+    m = M.periodic_box(2, (4, 2), (0.0, 0.0), (L, 1.0))
+    m.face_tag = m.face_tag.copy()
+    for e in range(m.n_elem):
+        xs = m.xyz[m.elem_vert[e]]
+        if np.isclose(xs[:, 1].min(), 0.0):
+            m.face_tag[e, 2] = M.TAG_WALL
+        if np.isclose(xs[:, 1].max(), 1.0):
+            m.face_tag[e, 3] = M.TAG_FARFIELD
+    ph = NavierStokes(2, mu=mu, viscous=True, rho_inf=1.0, v_inf=(1.0, 0.0), p_inf=10.0)
+    d = FRDiscretisation(m, 2, ph)
+    x = d.sol_coords()
+    U = S.primitive_to_conserved(np.ones(x.shape[:-1]), np.stack([a * x[..., 1], 0 * x[..., 1]], -1),
+                                 np.full(x.shape[:-1], 10.0))
+    F = d.wall_force(U)
+    assert abs(F[0] - mu * a * L) < 1e-12
+    # pressure on the wall pushes into it (-y is the fluid's outward normal)
+    assert abs(F[1] - (-10.0 * L)) < 1e-11
