@@ -74,6 +74,20 @@ def physics():
     return dict(mu=1.0 / RE, p_inf=1.0 / (GAMMA * MACH ** 2), v_inf=(1.0, 0.0))
 
 
+def combine_ranks(dist, ms, units, device="cpu"):
+    """Whole-job figures over ranks: the slowest rank's time and the sum of
+    the units every rank processed (no data-path collective: candidates are
+    independent; only these two scalars cross ranks)."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(u)
+    return float(t.item()), float(u.item())
+
+
 def make_meshes(rank=0):
     from synth import meshes as M
     return M.airfoil_batch(N_INST, seed=2312 + rank, e_lo=8000, e_hi=40000, p_geo=P)[:CANDIDATES]
@@ -302,15 +316,7 @@ def run_gpu(args):
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     launches = sol.last_launch_count()
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        tot = torch.tensor([float(E)], device="cuda")
-        dist.all_reduce(tot)
-        E_all = tot.item()
-    else:
-        E_all = E
+    ms, E_all = combine_ranks(dist, ms, E, device="cuda")
     upd_all = E_all * NSP * STAGES * args.steps
     value = upd_all / (ms / 1e3)
     # observer results of the timed window

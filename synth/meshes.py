@@ -294,10 +294,19 @@ def cavity_mesh(target_elems: int = 32000, LD: float = 0.5, seed: int = 2312) ->
 
     tags = _tag_unmatched(elem_vert, xyz, 2, classify)
     probe = np.array([0.5 * LD, 7.16])
+    # dense sampling of the walls: plate, cavity sides and floor
+    hs = 0.25 * h0
+    seg = lambda a, b: np.linspace(a, b, max(2, int(np.linalg.norm(np.subtract(b, a)) / hs)))
+    wall = np.concatenate([
+        np.stack([seg(x_in, 0.0), np.zeros(len(seg(x_in, 0.0)))], 1),
+        np.stack([np.zeros(len(seg(0.0, -1.0))), seg(0.0, -1.0)], 1),
+        np.stack([seg(0.0, LD), np.full(len(seg(0.0, LD)), -1.0)], 1),
+        np.stack([np.full(len(seg(-1.0, 0.0)), LD), seg(-1.0, 0.0)], 1),
+        np.stack([seg(LD, x_out), np.zeros(len(seg(LD, x_out)))], 1)])
     return Mesh(dim=2, xyz=xyz, elem_vert=elem_vert, face_tag=tags,
                 periodic_shift=np.zeros((0, 2)),
                 info={"kind": "cavity", "LD": LD, "h0": h0, "probe": probe,
-                      "wall_y": 0.0, "x_inflow": x_in})
+                      "wall_y": 0.0, "x_inflow": x_in, "wall_points": wall})
 
 
 # ---------------------------------------------------------------------------

@@ -111,7 +111,7 @@ def tgv_case(n=4, p=3):
 
 def cavity_case(target=1500, p=3):
     m = M.cavity_mesh(target)
-    return Case("cavity", [m], p, True, 1.0 / 1500.0, 0.15, dt=2e-4,
+    return Case("cavity", [m], p, True, 1.0 / 1500.0, 0.15, dt=cfl_dt([m], 0.15, p),
                 inflow_delta=0.2, inflow_ywall=0.0)
 
 

@@ -1,0 +1,52 @@
+"""Multi-rank (N > 1) logic of bench.py on CPU with the gloo backend,
+world size 2: each rank works on its own seeded poll, and the whole-job
+figures are the slowest rank's time and the sum of the ranks' units."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    p = s.getsockname()[1]
+    s.close()
+    return p
+
+
+def _worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    import torch.distributed as dist
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # rank-dependent work: rank r times (r + 1) ms on (r + 1) * 1000 units
+    ms, units = bench.combine_ranks(dist, 1.0 + rank, 1000.0 * (rank + 1), device="cpu")
+    # each rank's poll is drawn from its own seed
+    from synth import meshes as M
+    m = M.airfoil_batch(1, seed=2312 + rank, e_lo=300, e_hi=400)[0]
+    out[rank] = (ms, units, float(m.info["m"]), m.n_elem)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_combine_ranks_world_size_2_gloo():
+    port = _free_port()
+    mgr = mp.Manager()
+    out = mgr.dict()
+    ctx = mp.get_context("spawn")
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, out)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert out[0][:2] == out[1][:2] == (2.0, 3000.0)
+    assert out[0][2] != out[1][2]          # different candidates per rank
+
+
+def test_combine_ranks_single_process_passthrough():
+    import bench
+    assert bench.combine_ranks(None, 3.5, 77) == (3.5, 77)
