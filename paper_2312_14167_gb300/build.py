@@ -63,7 +63,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         if force or _stale(o, s):
             cmd = [nvcc] + _flags() + ["-c", s, "-o", o]
             if src.endswith(".cpp"):
-                cmd = [nvcc, "-x", "cu"] + _flags() + ["-c", s, "-o", o]
+                cmd = [nvcc, "-x", "cu"] + _flags() + ["-Xcompiler", "-fopenmp", "-c", s, "-o", o]
             jobs.append((src, cmd))
 
     def run(job):
@@ -81,7 +81,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     objs = [os.path.join(BUILD, s + ".o") for s in SOURCES]
     if force or jobs or not os.path.exists(LIB):
         tmp = LIB + ".tmp"
-        cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+        cmd = [nvcc] + ARCH + ["-shared", "-Xcompiler", "-fopenmp", "-o", tmp] + objs + ["-lcudart", "-lgomp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)

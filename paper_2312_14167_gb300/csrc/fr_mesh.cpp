@@ -189,6 +189,55 @@ struct MapEval {
     }
 };
 
+// Shape functions of the map and their derivatives tabulated at a fixed set
+// of reference points (the same for every element).
+struct MapTable {
+    int dim = 0, nn = 0, npts = 0;
+    std::vector<double> N, dN;   // N[p*nn + a], dN[(p*nn + a)*3 + k]
+    MapTable(const MapEval &me, const std::vector<double> &xi, int npts_) : dim(me.dim), nn(me.nn), npts(npts_) {
+        N.assign((size_t)npts * nn, 0.0);
+        dN.assign((size_t)npts * nn * 3, 0.0);
+        // evaluate with unit node vectors: x = sum_a N_a X_a picks N_a
+        std::vector<double> unit((size_t)nn * dim, 0.0);
+        for (int pt = 0; pt < npts; ++pt) {
+            double L[3][8], dL[3][8];
+            for (int a = 0; a < dim; ++a)
+                for (int m = 0; m <= me.q; ++m) {
+                    L[a][m] = lagrange_1d(me.eq.data(), me.q + 1, m, xi[(size_t)pt * dim + a]);
+                    dL[a][m] = lagrange_1d_deriv(me.eq.data(), me.q + 1, m, xi[(size_t)pt * dim + a]);
+                }
+            for (int a = 0; a < nn; ++a) {
+                int idx[3] = {0, 0, 0}, t = a;
+                for (int d = 0; d < dim; ++d) { idx[d] = t % (me.q + 1); t /= (me.q + 1); }
+                double n = 1.0;
+                for (int d = 0; d < dim; ++d) n *= L[d][idx[d]];
+                N[(size_t)pt * nn + a] = n;
+                for (int k = 0; k < dim; ++k) {
+                    double v = 1.0;
+                    for (int d = 0; d < dim; ++d) v *= (d == k) ? dL[d][idx[d]] : L[d][idx[d]];
+                    dN[((size_t)pt * nn + a) * 3 + k] = v;
+                }
+            }
+        }
+    }
+    // same arithmetic as MapEval::eval (offsets from node 0), tabulated
+    void eval(const double *nodes, int pt, double *x, double A[3][3]) const {
+        for (int j = 0; j < dim; ++j) {
+            x[j] = 0.0;
+            for (int k = 0; k < dim; ++k) A[j][k] = 0.0;
+        }
+        const double *n = &N[(size_t)pt * nn];
+        const double *dn = &dN[(size_t)pt * nn * 3];
+        for (int a = 0; a < nn; ++a)
+            for (int j = 0; j < dim; ++j) {
+                const double X = nodes[(size_t)a * dim + j] - nodes[j];
+                x[j] += n[a] * X;
+                for (int k = 0; k < dim; ++k) A[j][k] += dn[a * 3 + k] * X;
+            }
+        for (int j = 0; j < dim; ++j) x[j] += nodes[j];
+    }
+};
+
 // S[k][j] = J dxi_k / dx_j (adjugate of A), returns J
 double adjugate(int dim, const double A[3][3], double S[3][3]) {
     if (dim == 2) {
@@ -322,16 +371,21 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
     m->x_fp.resize((size_t)n_elem * nfp * dim);
     m->partner.assign((size_t)n_elem * nfp, -1);
     m->bctag.assign((size_t)n_elem * nfp, 0);
+    const fr::MapTable tsp(me, r.sp_xi, nsp), tfp(me, r.fp_xi, nfp);
+    int64_t bad_elem = -1;
+    // elements are independent: one host thread per chunk of elements
+#pragma omp parallel for schedule(static)
     for (int64_t e = 0; e < n_elem; ++e) {
         const double *nd = &m->nodes[(size_t)e * me.nn * dim];
         for (int s = 0; s < nsp; ++s) {
             double x[3], A[3][3], S[3][3];
-            me.eval(nd, &r.sp_xi[(size_t)s * dim], x, A);
+            tsp.eval(nd, s, x, A);
             const double J = fr::adjugate(dim, A, S);
             if (!(J > 0.0)) {
-                delete m;
-                fr::set_error("fr_mesh_create: non-positive Jacobian in element " + std::to_string(e));
-                return FR_ERR_MESH;
+#pragma omp critical
+                {
+                    if (bad_elem < 0 || e < bad_elem) bad_elem = e;
+                }
             }
             m->J[(size_t)e * nsp + s] = J;
             for (int j = 0; j < dim; ++j) m->x_sp[((size_t)e * nsp + s) * dim + j] = x[j];
@@ -341,7 +395,7 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
         }
         for (int f = 0; f < nfp; ++f) {
             double x[3], A[3][3], S[3][3];
-            me.eval(nd, &r.fp_xi[(size_t)f * dim], x, A);
+            tfp.eval(nd, f, x, A);
             fr::adjugate(dim, A, S);
             const int k = r.fp_dir[f];
             const double sg = r.fp_side[f] ? 1.0 : -1.0;
@@ -350,6 +404,11 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
                 m->x_fp[((size_t)e * nfp + f) * dim + j] = x[j];
             }
         }
+    }
+    if (bad_elem >= 0) {
+        delete m;
+        fr::set_error("fr_mesh_create: non-positive Jacobian in element " + std::to_string(bad_elem));
+        return FR_ERR_MESH;
     }
 
     // ---- face connectivity -------------------------------------------------
@@ -438,37 +497,57 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
             }
         }
     }
-    // pair flux points by physical position
+    // Pair flux points by physical position.  A face's points form an n x n
+    // (3-D) or n (2-D) tensor grid, so the partner's numbering is one of the
+    // 8 (3-D) or 2 (2-D) orientations of that grid: choose it on three
+    // reference points, then check every point.
+    const int nn1 = r.n;
+    auto orient = [&](int o, int a) -> int {
+        if (dim == 2) return o ? nn1 - 1 - a : a;
+        int i = a % nn1, j = a / nn1;
+        if (o & 4) std::swap(i, j);
+        if (o & 1) i = nn1 - 1 - i;
+        if (o & 2) j = nn1 - 1 - j;
+        return i + nn1 * j;
+    };
+    const int n_orient = dim == 2 ? 2 : 8;
+    const int refs[3] = {0, nfpf - 1, dim == 2 ? nfpf / 2 : nn1 - 1};
     for (const Pair &pr : pairs) {
         const double *xa = &m->x_fp[((size_t)pr.e * nfp + pr.fc * nfpf) * dim];
         const double *xb = &m->x_fp[((size_t)pr.e2 * nfp + pr.fc2 * nfpf) * dim];
+        auto d2 = [&](int a, int b) {
+            double t = 0;
+            for (int c = 0; c < dim; ++c) {
+                const double dd = xa[a * dim + c] + pr.sh[c] - xb[b * dim + c];
+                t += dd * dd;
+            }
+            return t;
+        };
         double hmin = 1e300;
         for (int i = 0; i < ncf; ++i)
             for (int j = i + 1; j < ncf; ++j) {
-                double d2 = 0;
+                double q2 = 0;
                 for (int c = 0; c < dim; ++c) {
                     double dd = xyz[corners(pr.e, pr.fc, i) * dim + c] - xyz[corners(pr.e, pr.fc, j) * dim + c];
-                    d2 += dd * dd;
+                    q2 += dd * dd;
                 }
-                hmin = std::min(hmin, std::sqrt(d2));
+                hmin = std::min(hmin, std::sqrt(q2));
             }
+        int best = 0;
+        double bd = 1e300;
+        for (int o = 0; o < n_orient; ++o) {
+            double t = 0;
+            for (int rr = 0; rr < 3; ++rr) t += d2(refs[rr], orient(o, refs[rr]));
+            if (t < bd) { bd = t; best = o; }
+        }
         for (int a = 0; a < nfpf; ++a) {
-            int best = -1;
-            double bd = 1e300;
-            for (int b = 0; b < nfpf; ++b) {
-                double d2 = 0;
-                for (int c = 0; c < dim; ++c) {
-                    double dd = xa[a * dim + c] + pr.sh[c] - xb[b * dim + c];
-                    d2 += dd * dd;
-                }
-                if (d2 < bd) { bd = d2; best = b; }
-            }
-            if (std::sqrt(bd) > 1e-6 * hmin) {
+            const int b = orient(best, a);
+            if (std::sqrt(d2(a, b)) > 1e-6 * hmin) {
                 delete m;
                 fr::set_error("fr_mesh_create: flux points of a connected face do not coincide");
                 return FR_ERR_MESH;
             }
-            m->partner[(size_t)pr.e * nfp + pr.fc * nfpf + a] = pr.e2 * nfp + pr.fc2 * nfpf + best;
+            m->partner[(size_t)pr.e * nfp + pr.fc * nfpf + a] = pr.e2 * nfp + pr.fc2 * nfpf + b;
         }
     }
     for (int64_t e = 0; e < n_elem; ++e)

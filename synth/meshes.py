@@ -501,3 +501,226 @@ def airfoil_batch(n_inst: int = 32, seed: int = 2312, e_lo: int = 8000,
 
 def concat_info(meshes):
     return [mm.info for mm in meshes]
+
+
+# ---------------------------------------------------------------------------
+# G5: spanwise-extruded tandem cylinders (3-D hexes)
+# ---------------------------------------------------------------------------
+
+def _graded_from(x0, x1, h, r_res, dist_res, r_buf):
+    """Nodes from x0 towards x1 (either direction): spacing h growing by
+    r_res for dist_res, then by r_buf (buffer) to x1."""
+    sgn = 1.0 if x1 > x0 else -1.0
+    L = abs(x1 - x0)
+    nodes = [0.0]
+    hh = h
+    while nodes[-1] + hh < L - 1e-12:
+        nodes.append(nodes[-1] + hh)
+        hh *= r_res if nodes[-1] < dist_res else r_buf
+    if L - nodes[-1] < 0.5 * hh and len(nodes) > 1:
+        nodes[-1] = L
+    else:
+        nodes.append(L)
+    return x0 + sgn * np.asarray(nodes)
+
+
+def tandem_cylinders_2d(s_gap: float, r_ratio: float, target_quads: int, q: int = 2):
+    """2-D section: cylinders of diameters D1 = 1 (centre at the origin) and
+    D2 = r_ratio, surface gap s_gap (rear of the upstream to the front of the
+    downstream cylinder), each inside an O-ring that ends on a square hole of
+    a Cartesian background; inlet 5 D1 upstream, outlet 55 D1 downstream of
+    the second cylinder, +-10 D1 laterally; stretching 1.05 (resolved) and
+    1.075 (buffer).  Returns (xyz, elem_vert, geo_nodes (q), wall/outflow
+    edge tags, info)."""
+    R1, R2 = 0.5, 0.5 * r_ratio
+    x1, x2 = 0.0, R1 + s_gap + R2
+    x_in, x_out, y_max = x1 - 5.0, x2 + 55.0, 10.0
+
+    def count(h):
+        m1 = max(4, 2 * int(round(1.5 * R1 * 2 / h / 2)))
+        m2 = max(4, 2 * int(round(1.5 * R2 * 2 / h / 2)))
+        H1, H2 = 0.5 * m1 * h, 0.5 * m2 * h
+        gap = (x2 - H2) - (x1 + H1)
+        ng = max(1, int(round(gap / h)))
+        nr = max(3, int(round(0.6 * m1)))
+        Ymax = max(H1, H2)
+        xs_core = (x2 + H2) - (x1 - H1)
+        ny_core = 2 * int(round(Ymax / h))
+        xs = len(_graded_from(0, 5 - H1, h, 1.05, 3.0, 1.075)) + \
+            len(_graded_from(0, 55 - H2, h, 1.05, 12.0, 1.075)) + int(round(xs_core / h))
+        ys = ny_core + 2 * len(_graded_from(0, y_max - Ymax, h, 1.05, 3.0, 1.075))
+        return xs * ys - m1 * m1 - m2 * m2 + 4 * m1 * nr + 4 * m2 * nr
+
+    lo, hi = 0.01, 1.0
+    for _ in range(50):
+        mid = np.sqrt(lo * hi)
+        if count(mid) > target_quads:
+            lo = mid
+        else:
+            hi = mid
+    h0 = hi
+    m1 = max(4, 2 * int(round(1.5 * R1 * 2 / h0 / 2)))
+    m2 = max(4, 2 * int(round(1.5 * R2 * 2 / h0 / 2)))
+    # one spacing for both holes: the gap between them a whole number of cells
+    H1g, H2g = 0.5 * m1 * h0, 0.5 * m2 * h0
+    ng = max(1, int(round(((x2 - H2g) - (x1 + H1g)) / h0)))
+    h = ((x2 - x1)) / (0.5 * m1 + ng + 0.5 * m2)
+    H1, H2 = 0.5 * m1 * h, 0.5 * m2 * h
+    Ymax = max(H1, H2)
+    ny2 = int(round(Ymax / h))
+    # x and y nodes: uniform core, graded outside
+    core_x = x1 - H1 + h * np.arange(m1 + ng + m2 + 1)
+    up = _graded_from(core_x[0], x_in, h * 1.05, 1.05, 3.0, 1.075)[::-1]
+    down = _graded_from(core_x[-1], x_out, h * 1.05, 1.05, 12.0, 1.075)
+    xs = np.concatenate([up[:-1], core_x, down[1:]])
+    core_y = h * np.arange(-ny2, ny2 + 1)
+    top = _graded_from(core_y[-1], y_max, h * 1.05, 1.05, 3.0, 1.075)
+    ys = np.concatenate([-top[::-1][:-1], core_y, top[1:]])
+    nx, ny = len(xs), len(ys)
+    i0 = len(up) - 1            # index of core_x[0] in xs
+    j0 = len(top) - 1           # index of core_y[0] in ys
+    vid_bg = lambda i, j: i + nx * j
+    X, Y = np.meshgrid(xs, ys, indexing="ij")
+    pts = [np.stack([X.ravel(order="F"), Y.ravel(order="F")], 1)]
+    nvert = nx * ny
+    # holes in background index space: cells [a, b) x [c, d)
+    holes = []
+    for (xc, m) in ((x1, m1), (x2, m2)):
+        ia = i0 + int(round((xc - 0.5 * m * h - core_x[0]) / h))
+        ja = j0 + ny2 - m // 2
+        holes.append((ia, ia + m, ja, ja + m))
+    elems, nodes = [], []
+    a = np.linspace(0.0, 1.0, q + 1)
+    # background quads (straight): nodes by bilinear interpolation
+    for j in range(ny - 1):
+        for i in range(nx - 1):
+            if any(hx0 <= i < hx1 and hy0 <= j < hy1 for hx0, hx1, hy0, hy1 in holes):
+                continue
+            c = [vid_bg(i, j), vid_bg(i + 1, j), vid_bg(i, j + 1), vid_bg(i + 1, j + 1)]
+            elems.append(c)
+            B, T_ = np.meshgrid(a, a, indexing="ij")   # [xi, eta]
+            xx = xs[i] + (xs[i + 1] - xs[i]) * B
+            yy = ys[j] + (ys[j + 1] - ys[j]) * T_
+            nodes.append(np.stack([xx.T.ravel(), yy.T.ravel()], 1))
+    # O-rings
+    for (xc, R, m, (hx0, hx1, hy0, hy1)) in ((x1, R1, m1, holes[0]), (x2, R2, m2, holes[1])):
+        H = 0.5 * m * h
+        nr = max(3, int(round(0.6 * m)))
+        ratio = 1.15
+
+        def frac(r):      # radial fraction, geometric from the wall
+            return (ratio ** (r * nr) - 1.0) / (ratio ** nr - 1.0)
+
+        def square(t):    # perimeter parameter t in [0, 4m) -> point, counter-clockwise
+            t = np.asarray(t, float) % (4 * m)
+            side = np.floor(t / m).astype(int)
+            u = t / m - side
+            px = np.select([side == 0, side == 1, side == 2, side == 3],
+                           [H + 0 * u, H - 2 * H * u, -H + 0 * u, -H + 2 * H * u])
+            py = np.select([side == 0, side == 1, side == 2, side == 3],
+                           [-H + 2 * H * u, H + 0 * u, H - 2 * H * u, -H + 0 * u])
+            return px, py
+
+        def ring_map(t, r):
+            sx, sy = square(t)
+            ang = np.arctan2(sy, sx)
+            cx, cy = R * np.cos(ang), R * np.sin(ang)
+            f = frac(r)
+            return xc + cx + f * (sx - cx), cy + f * (sy - cy)
+
+        # vertices: perimeter index k (0..4m-1), ring index l (0..nr); l = nr on the hole
+        def hole_vid(k):
+            sx, sy = square(k)
+            i = hx0 + int(round((sx + H) / h))
+            jj = hy0 + int(round((sy + H) / h))
+            return vid_bg(i, jj)
+        base = nvert
+        inner = np.zeros((4 * m, nr), np.int64)
+        newp = []
+        for l in range(nr):
+            for k in range(4 * m):
+                px, py = ring_map(k, l / nr)
+                newp.append((px, py))
+                inner[k, l] = base + l * 4 * m + k
+        pts.append(np.asarray(newp))
+        nvert += nr * 4 * m
+
+        def rv(k, l):
+            k = k % (4 * m)
+            return hole_vid(k) if l == nr else inner[k, l]
+        for l in range(nr):
+            for k in range(4 * m):
+                # xi clockwise along the perimeter, eta outward (positive J)
+                elems.append([rv(k + 1, l), rv(k, l), rv(k + 1, l + 1), rv(k, l + 1)])
+                T_, Rr = np.meshgrid(k + 1 - a, (l + a) / nr, indexing="ij")
+                gx, gy = ring_map(T_, Rr)
+                nodes.append(np.stack([gx.T.ravel(), gy.T.ravel()], 1))
+    xyz = np.concatenate(pts, 0)
+    elem_vert = np.asarray(elems, np.int64)
+    info = {"h": h, "m1": m1, "m2": m2, "x2": x2, "R1": R1, "R2": R2, "x_in": x_in,
+            "x_out": x_out, "y_max": y_max}
+    return xyz, elem_vert, np.asarray(nodes), info
+
+
+def tandem_cylinders(s_gap: float, r_ratio: float, n_hex: int, n_span: int = 16,
+                     q: int = 2) -> Mesh:
+    """Spanwise extrusion of ``tandem_cylinders_2d`` over pi D1 with n_span
+    periodic layers (about n_hex hexes in total); walls on the cylinders,
+    characteristic far field at the inlet and the lateral boundaries,
+    outflow at the outlet; observers 2 D1 above the upstream cylinder."""
+    xyz2, ev2, nodes2, info = tandem_cylinders_2d(s_gap, r_ratio, max(16, n_hex // n_span), q)
+    span = np.pi
+    z = np.linspace(0.0, span, n_span + 1)
+    nv2 = xyz2.shape[0]
+    xyz = np.concatenate([np.concatenate([xyz2, np.full((nv2, 1), zz)], 1) for zz in z], 0)
+    ne2 = ev2.shape[0]
+    ev = np.concatenate([np.concatenate([ev2 + k * nv2, ev2 + (k + 1) * nv2], 1)
+                         for k in range(n_span)], 0)
+    a = np.linspace(0.0, 1.0, q + 1)
+    nodes = []
+    for k in range(n_span):
+        zz = z[k] + (z[k + 1] - z[k]) * a                      # (q+1,)
+        nz = np.repeat(zz, (q + 1) ** 2)                        # zeta slowest
+        n3 = np.concatenate([np.tile(nodes2, (1, q + 1, 1)),
+                             np.broadcast_to(nz[None, :, None], (ne2, (q + 1) ** 3, 1))], 2)
+        nodes.append(n3)
+    geo = np.concatenate(nodes, 0)
+
+    x_in, x_out, y_max = info["x_in"], info["x_out"], info["y_max"]
+
+    def classify(c, f):
+        if f in (4, 5):
+            return TAG_PERIODIC
+        if abs(c[0] - x_out) < 1e-9:
+            return TAG_OUTFLOW
+        if abs(c[0] - x_in) < 1e-9 or abs(abs(c[1]) - y_max) < 1e-9:
+            return TAG_FARFIELD
+        return TAG_WALL
+
+    tags = _tag_unmatched(ev, xyz, 3, classify)
+    probes = np.array([[0.0, 2.0, (kk + 0.5) * span / n_span] for kk in range(n_span)])
+    # wall sampling for wall-damped starts
+    th = np.linspace(0, 2 * np.pi, 400, endpoint=False)
+    ring = lambda xc, R: np.stack([xc + R * np.cos(th), R * np.sin(th)], 1)
+    w2 = np.concatenate([ring(0.0, info["R1"]), ring(info["x2"], info["R2"])], 0)
+    wall = np.concatenate([np.concatenate([w2, np.full((len(w2), 1), zz)], 1)
+                           for zz in np.linspace(0, span, 33)], 0)
+    info.update({"kind": "tandem", "s": s_gap, "r": r_ratio, "probes": probes,
+                 "wall_points": wall})
+    return Mesh(dim=3, xyz=xyz, elem_vert=ev, face_tag=tags,
+                periodic_shift=np.array([[0.0, 0.0, span]]), geo_order=q, geo_nodes=geo,
+                info=info)
+
+
+def tandem_batch(n_inst: int = 16, seed: int = 2312, h_lo: int = 60000, h_hi: int = 150000,
+                 n_span: int = 16, q: int = 2):
+    """One poll of tandem-cylinder candidates: gap s/D1 ~ U[2, 5], diameter
+    ratio D2/D1 ~ U[0.5, 1.5], hex count ~ U[h_lo, h_hi]."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_inst):
+        s = rng.uniform(2.0, 5.0)
+        r = rng.uniform(0.5, 1.5)
+        nh = int(rng.uniform(h_lo, h_hi))
+        out.append(tandem_cylinders(s, r, nh, n_span, q))
+    return out

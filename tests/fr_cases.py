@@ -118,3 +118,13 @@ def cavity_case(target=1500, p=3):
 def airfoil_case(n_inst=3, e_lo=300, e_hi=700, p=3, seed=7):
     ms = M.airfoil_batch(n_inst, seed=seed, e_lo=e_lo, e_hi=e_hi, p_geo=p)
     return Case("airfoil", ms, p, True, 1.0 / 23000.0, 0.2, dt=cfl_dt(ms, 0.2, p))
+
+
+def tandem_case(n_inst=2, n_hex=1200, n_span=4, p=4, seed=7):
+    """Tandem cylinders, 3-D hexes at p = 4, Re = 1000, M = 0.2."""
+    import numpy as _np
+    rng = _np.random.default_rng(seed)
+    ms = [M.tandem_cylinders(rng.uniform(2.0, 5.0), rng.uniform(0.5, 1.5), n_hex, n_span, q=2)
+          for _ in range(n_inst)]
+    return Case("tandem", ms, p, True, 1.0 / 1000.0, 0.2, dt=cfl_dt(ms, 0.2, p),
+                v_inf=(1.0, 0.0, 0.0))

@@ -137,3 +137,20 @@ def test_airfoil_poll_full_size_sampled_parity():
             s.set_state(i, u)
     for inst in (0, 17, 31):
         _check_sampled(case, inst, sols, us)
+
+
+def test_tandem_candidate_full_size_sampled_parity():
+    """One tandem-cylinder candidate at the top of the poll's size range
+    (about 150k curved hexes, p = 4: 18.75 M solution points)."""
+    m = M.tandem_cylinders(3.1, 1.3, 150000, 16, q=2)
+    assert 120000 < m.n_elem < 170000
+    case = FC.Case("tandem", [m], 4, True, 1.0 / 1000.0, 0.2, dt=FC.cfl_dt([m], 0.2, 4),
+                   v_inf=(1.0, 0.0, 0.0))
+    sols = {p: FC.lib_solver(case, p) for p in ("fp64", "fp32")}
+    u = FC.initial_state(case, sols["fp64"].meshes[0].sol_coords())
+    for s in sols.values():
+        s.set_state(0, u)
+    _check_sampled(case, 0, sols, [u])
+    sols["fp32"].rk_step(3)
+    _, bad = sols["fp32"].integral(0)
+    assert bad == 0

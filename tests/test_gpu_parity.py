@@ -241,3 +241,44 @@ def test_wall_force_matches_oracle():
     gross = case.p_inf * 2.2
     print("force gpu", got, "oracle", want)
     assert np.all(np.abs(got - want) < 1e-12 * gross)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_tandem_cylinders_3d_p4_batch_residual(precision):
+    """Two extruded tandem-cylinder candidates (curved hexes, p = 4, walls,
+    far field, outflow, spanwise periodic) batched in one solver."""
+    case = FC.tandem_case(n_inst=2, n_hex=900, n_span=3)
+    sol = FC.lib_solver(case, precision)
+    us = []
+    for i in range(2):
+        disc = FC.oracle_disc(case, i)
+        u = FC.initial_state(case, disc.sol_coords(), i)
+        sol.set_state(i, u)
+        us.append(u)
+    for i in range(2):
+        disc = FC.oracle_disc(case, i)
+        if precision == "fp64":
+            assert FC.rel_l2(sol.residual(i), disc.residual(us[i])) < 1e-12
+        else:
+            u32 = us[i].astype(np.float32).astype(np.float64)
+            R32, mag = disc.residual(u32, magnitude=True)
+            err = FC.rel_l2(sol.residual(i), R32)
+            bound = C_FP32 * EPS32 * np.linalg.norm(mag) / np.linalg.norm(R32)
+            print(f"tandem[{i}] fp32: {err:.3e} (bound {bound:.3e})")
+            assert err < bound
+
+
+def test_tandem_cylinders_lsrk45_steps_fp64():
+    case = FC.tandem_case(n_inst=1, n_hex=700, n_span=3)
+    sol = FC.lib_solver(case, "fp64")
+    disc = FC.oracle_disc(case)
+    u = FC.initial_state(case, disc.sol_coords())
+    sol.set_state(0, u)
+    pid = sol.probe_add(0, case.meshes[0].info["probes"][1])
+    sol.rk_step(2)
+    ur = u
+    for _ in range(2):
+        ur = T.lsrk45_step(disc.residual, ur, case.dt)
+    assert FC.rel_l2(sol.get_state(0), ur) < 1e-12
+    pr = Probe(disc, case.meshes[0].info["probes"][1])
+    assert abs(sol.probe_pressure(pid) - pr.pressure(ur)) < 1e-11 * pr.pressure(ur)

@@ -46,6 +46,7 @@ def test_library_exports_every_declared_function(fr):
     (lambda: M.tgv_mesh(3), 2),
     (lambda: M.cavity_mesh(800), 3),
     (lambda: M.naca_omesh(0.04, 0.3, 0.1, 2.0, 500), 3),
+    (lambda: M.tandem_cylinders(2.5, 0.8, 900, 3), 4),
 ])
 def test_host_geometry_matches_oracle(fr, maker, p):
     from oracle.fr import FRDiscretisation
