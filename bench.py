@@ -43,15 +43,75 @@ import numpy as np  # noqa: E402
 METRIC = "sol-pt RK-stage updates/s, batched mixed-prec vs plain FP64 FR, same GB300"
 UNIT = "sol-pt RK-stage updates/s"
 GAMMA, PR = 1.4, 0.71
-RE, MACH, P = 23000.0, 0.2, 3
-N_INST = 32
-CANDIDATES = N_INST      # --candidates: a smaller poll for profiling captures
 STAGES = 5
-NSP = (P + 1) ** 2
-NFP = 4 * (P + 1)
-V = 4
-WORKLOAD = ("32 NACA 4-digit O-meshes (8k-40k curved quads, seed 2312), p=3, NS BR2, "
-            "Re_c=23000, M=0.2, LSRK45, one probe per candidate")
+
+
+class Workload:
+    """One configuration: dimension, degree, physics, seeded meshes, start."""
+
+    def __init__(self, name, dim, p, re, mach, candidates, desc, make, v_inf, inflow_delta=0.0,
+                 start="wall_damped"):
+        self.name, self.dim, self.p, self.re, self.mach = name, dim, p, re, mach
+        self.candidates, self.desc, self.make = candidates, desc, make
+        self.v_inf, self.inflow_delta, self.start = v_inf, inflow_delta, start
+        n = p + 1
+        self.nsp = n ** dim
+        self.nfp = 2 * dim * n ** (dim - 1)
+        self.V = dim + 2
+        self.MS = dim * dim + 1
+
+    def physics(self):
+        return dict(mu=1.0 / self.re, p_inf=1.0 / (GAMMA * self.mach ** 2), v_inf=self.v_inf)
+
+
+def _airfoils(rank, n):
+    from synth import meshes as M
+    return M.airfoil_batch(32, seed=2312 + rank, e_lo=8000, e_hi=40000, p_geo=3)[:n]
+
+
+def _tandems(rank, n):
+    from synth import meshes as M
+    return M.tandem_batch(16, seed=2312 + rank)[:n] if n == 16 else \
+        [M.tandem_cylinders(*a) for a in _tandem_draws(rank)[:n]]
+
+
+def _tandem_draws(rank):
+    rng = np.random.default_rng(2312 + rank)
+    out = []
+    for _ in range(16):
+        s, r, nh = rng.uniform(2.0, 5.0), rng.uniform(0.5, 1.5), int(rng.uniform(60000, 150000))
+        out.append((s, r, nh))
+    return out
+
+
+def _cavity(rank, n):
+    from synth import meshes as M
+    return [M.cavity_mesh(32000)]
+
+
+def _tgv(rank, n):
+    from synth import meshes as M
+    return [M.tgv_mesh(64)]
+
+
+WORKLOADS = {
+    "airfoil": Workload("airfoil", 2, 3, 23000.0, 0.2, 32,
+                        "32 NACA 4-digit O-meshes (8k-40k curved quads, seed 2312), p=3, NS BR2, "
+                        "Re_c=23000, M=0.2, LSRK45, one probe per candidate", _airfoils, (1.0, 0.0)),
+    "tandem": Workload("tandem", 3, 4, 1000.0, 0.2, 16,
+                       "16 tandem-cylinder candidates (60k-150k curved hexes, 16 spanwise layers, "
+                       "seed 2312), p=4, NS BR2, Re=1000, M=0.2, LSRK45, 16 spanwise probes each",
+                       _tandems, (1.0, 0.0, 0.0)),
+    "cavity": Workload("cavity", 2, 3, 1500.0, 0.15, 1,
+                       "2-D deep-cavity proxy (~32k quads, L/D=0.5), p=3, NS BR2, Re_D=1500, M=0.15, "
+                       "tanh inflow, LSRK45, one probe", _cavity, (1.0, 0.0), inflow_delta=0.2),
+    "tgv": Workload("tgv", 3, 3, 1600.0, 0.1, 1,
+                    "Taylor-Green vortex 64^3 hexes, p=3, NS BR2, Re=1600, M=0.1, LSRK45", _tgv,
+                    (0.0, 0.0, 0.0), start="tgv"),
+}
+W = WORKLOADS["airfoil"]
+CANDIDATES = W.candidates     # --candidates: a smaller poll (profiling captures)
+
 
 # DRAM traffic of one launch of the dominant kernel from an ncu capture,
 # per element, valid only for the kernel source it was taken on.
@@ -70,10 +130,6 @@ def kernel_source_hash():
         return hashlib.sha256(f.read()).hexdigest()
 
 
-def physics():
-    return dict(mu=1.0 / RE, p_inf=1.0 / (GAMMA * MACH ** 2), v_inf=(1.0, 0.0))
-
-
 def combine_ranks(dist, ms, units, device="cpu"):
     """Whole-job figures over ranks: the slowest rank's time and the sum of
     the units every rank processed (no data-path collective: candidates are
@@ -89,28 +145,49 @@ def combine_ranks(dist, ms, units, device="cpu"):
 
 
 def make_meshes(rank=0):
-    from synth import meshes as M
-    return M.airfoil_batch(N_INST, seed=2312 + rank, e_lo=8000, e_hi=40000, p_geo=P)[:CANDIDATES]
+    return W.make(rank, CANDIDATES)
 
 
 def cfl_dt(meshes, cfl=0.4):
     """Fixed step from a CFL estimate: smallest corner-edge length over
     (|v| + c) (p+1)^2, the same dt for every candidate."""
-    c = np.sqrt(GAMMA * physics()["p_inf"])
+    c = np.sqrt(GAMMA * W.physics()["p_inf"])
     hmin = np.inf
+    pairs = ((0, 1), (0, 2), (1, 3), (2, 3)) if W.dim == 2 else ((0, 1), (0, 2), (0, 4))
     for m in meshes:
         X = m.xyz[m.elem_vert]
-        for a, b in ((0, 1), (0, 2), (1, 3), (2, 3)):
+        for a, b in pairs:
             hmin = min(hmin, np.linalg.norm(X[:, a] - X[:, b], axis=1).min())
-    return cfl * hmin / ((1.0 + c) * (P + 1) ** 2)
+    return cfl * hmin / ((1.0 + c) * (W.p + 1) ** 2)
 
 
 def initial_state(x, inst, mesh):
     """Seeded start: free stream with 1 % smooth perturbations, velocity
-    damped to zero within about 0.05 chord of the wall (no impulsive start)."""
+    damped to zero within about 0.05 of the walls (no impulsive start); the
+    Taylor-Green field for that workload."""
     from synth import states as S
-    u = S.smooth_perturbed(x, 2, MACH, amp=0.01, seed=7 + inst)
-    return S.wall_damped(x, mesh.info["wall_points"], 0.05, u)
+    if W.start == "tgv":
+        return S.taylor_green(x, mach=W.mach)
+    u = S.smooth_perturbed(x, W.dim, W.mach, amp=0.01, seed=7 + inst)
+    if "wall_points" in mesh.info:
+        u = S.wall_damped(x, mesh.info["wall_points"], 0.05, u)
+    return u
+
+
+def probe_points(mesh):
+    if "probes" in mesh.info:
+        return list(mesh.info["probes"])
+    if "probe" in mesh.info:
+        return [mesh.info["probe"]]
+    return []
+
+
+def oracle_phys():
+    from oracle.physics import NavierStokes
+    ph = W.physics()
+    return NavierStokes(W.dim, gamma=GAMMA, mu=ph["mu"], prandtl=PR, viscous=True, rho_inf=1.0,
+                        v_inf=ph["v_inf"], p_inf=ph["p_inf"], inflow_delta=W.inflow_delta,
+                        inflow_ywall=0.0)
 
 
 # --------------------------------------------------------------------------
@@ -121,10 +198,7 @@ def oracle_sample_rate(mesh, n_sample, n_steps, dt):
     """Time the FP64 oracle's LSRK45 stages restricted to a sample of
     elements of one candidate: returns (updates/s, seconds, sample text)."""
     from oracle.fr import FRDiscretisation
-    from oracle.physics import NavierStokes
-    ph = physics()
-    disc = FRDiscretisation(mesh, P, NavierStokes(2, gamma=GAMMA, mu=ph["mu"], prandtl=PR, viscous=True,
-                                                  rho_inf=1.0, v_inf=ph["v_inf"], p_inf=ph["p_inf"]))
+    disc = FRDiscretisation(mesh, W.p, oracle_phys())
     U = initial_state(disc.sol_coords(), 0, mesh)
     rng = np.random.default_rng(0)
     elems = np.sort(rng.choice(mesh.n_elem, size=min(n_sample, mesh.n_elem), replace=False))
@@ -133,13 +207,13 @@ def oracle_sample_rate(mesh, n_sample, n_steps, dt):
     B = [float(b) for b in LSRK45_B]
     t0 = time.perf_counter()
     for _ in range(n_steps):
-        du = np.zeros((elems.size, NSP, V))
+        du = np.zeros((elems.size, W.nsp, W.V))
         for s in range(STAGES):
             R = disc.residual(U, elems)
             du = A[s] * du + dt * R
             U[elems] = U[elems] + B[s] * du
     sec = time.perf_counter() - t0
-    upd = elems.size * NSP * STAGES * n_steps
+    upd = elems.size * W.nsp * STAGES * n_steps
     return upd / sec, sec, (f"{elems.size} of {mesh.n_elem} elements of candidate 0 "
                             f"(their 2-ring neighbourhood evaluated), {n_steps} LSRK45 steps")
 
@@ -156,7 +230,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "data": "synthetic", "config": {"workload": workload_text(), "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -223,12 +297,12 @@ def algorithmic_bytes(E, s, kind):
     metrics, normals, partner indices, the partner's face state, own and
     partner viscous normal flux, new face state; gradient: state, metrics,
     normals, partner indices, partner face state, viscous normal flux."""
-    MS = 5
+    NSP, NFP, V, MS, D = W.nsp, W.nfp, W.V, W.MS, W.dim
     if kind == "flux":
-        per = (NSP * V * s * (3 + 0.8) + NSP * MS * s + NFP * 2 * s + NFP * 4 + NFP * V * s
+        per = (NSP * V * s * (3 + 0.8) + NSP * MS * s + NFP * D * s + NFP * 4 + NFP * V * s
                + 2 * NFP * V * s + NFP * V * s)
     else:
-        per = NSP * V * s + NSP * MS * s + NFP * 2 * s + NFP * 4 + NFP * V * s + NFP * V * s
+        per = NSP * V * s + NSP * MS * s + NFP * D * s + NFP * 4 + NFP * V * s + NFP * V * s
     return per * E
 
 
@@ -237,14 +311,10 @@ def sampled_parity(fr, meshes, fms, sol, n_sample=48):
     residual vs the FP64 oracle on the FP32-rounded input (within the forward
     error bound) and vs the exact input."""
     from oracle.fr import FRDiscretisation
-    from oracle.physics import NavierStokes
-    ph = physics()
     out = []
     eps = 2.0 ** -24
     for inst in sorted({0, len(fms) // 2, len(fms) - 1}):
-        disc = FRDiscretisation(meshes[inst], P, NavierStokes(2, gamma=GAMMA, mu=ph["mu"], prandtl=PR,
-                                                              viscous=True, rho_inf=1.0,
-                                                              v_inf=ph["v_inf"], p_inf=ph["p_inf"]))
+        disc = FRDiscretisation(meshes[inst], W.p, oracle_phys())
         u = initial_state(fms[inst].sol_coords(), inst, meshes[inst])
         sol.set_state(inst, u)
         Rg = sol.residual(inst)
@@ -282,12 +352,12 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2312_14167_gb300 import fr
-    ph = physics()
-    cfg32 = fr.make_config(2, gamma=GAMMA, prandtl=PR, mu=ph["mu"], rho_inf=1.0, v_inf=ph["v_inf"],
-                           p_inf=ph["p_inf"], dt=dt, viscous=True, rk=fr.FR_LSRK45, precision=fr.FR_FP32)
-    cfg64 = fr.make_config(2, gamma=GAMMA, prandtl=PR, mu=ph["mu"], rho_inf=1.0, v_inf=ph["v_inf"],
-                           p_inf=ph["p_inf"], dt=dt, viscous=True, rk=fr.FR_LSRK45, precision=fr.FR_FP64)
-    fms = [fr.Mesh(m, P) for m in meshes]
+    ph = W.physics()
+    common = dict(gamma=GAMMA, prandtl=PR, mu=ph["mu"], rho_inf=1.0, v_inf=ph["v_inf"], p_inf=ph["p_inf"],
+                  inflow_delta=W.inflow_delta, inflow_ywall=0.0, dt=dt, viscous=True, rk=fr.FR_LSRK45)
+    cfg32 = fr.make_config(W.dim, precision=fr.FR_FP32, **common)
+    cfg64 = fr.make_config(W.dim, precision=fr.FR_FP64, **common)
+    fms = [fr.Mesh(m, W.p) for m in meshes]
     E = sum(m.n_elem for m in fms)
     sol = fr.Solver(fms, cfg32)
     states = [initial_state(m.sol_coords(), i, meshes[i]) for i, m in enumerate(fms)]
@@ -296,7 +366,7 @@ def run_gpu(args):
         parity = sampled_parity(fr, meshes, fms, sol)
     for i, u in enumerate(states):
         sol.set_state(i, u)
-    pids = [sol.probe_add(i, meshes[i].info["probe"]) for i in range(len(fms))]
+    pids = [[sol.probe_add(i, x) for x in probe_points(meshes[i])] for i in range(len(fms))]
     st = sol.stream
     # warm-up (captures the graph), then the timed steps
     sol.rk_step(args.warmup)
@@ -317,11 +387,12 @@ def run_gpu(args):
     ms = e0.elapsed_time(e1)
     launches = sol.last_launch_count()
     ms, E_all = combine_ranks(dist, ms, E, device="cuda")
-    upd_all = E_all * NSP * STAGES * args.steps
+    upd_all = E_all * W.nsp * STAGES * args.steps
     value = upd_all / (ms / 1e3)
     # observer results of the timed window
-    oaspl = [sol.oaspl([pid], p_ref=2e-5, p_scale=101325.0 / ph["p_inf"], mean_mode=0) for pid in pids[:4]]
-    forces = [list(sol.forces(i)) for i in range(2)]
+    oaspl = [sol.oaspl(ids, p_ref=2e-5, p_scale=101325.0 / ph["p_inf"], mean_mode=0)
+             for ids in pids[:4] if ids]
+    forces = [list(sol.forces(i)) for i in range(min(2, len(fms)))]
     tot, bad = sol.integral(0)
     # per-kernel times (CUDA events around each launch, no graph)
     kms, kcnt = sol.profile_steps(3)
@@ -340,9 +411,9 @@ def run_gpu(args):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     traffic = None
     rec = NCU_TRAFFIC.get(kernel_source_hash())
-    if rec:
+    if rec and W.name == rec.get("workload", "airfoil"):
         traffic = rec[f"{dom}_bytes_per_elem"] * E
-    roof = {"bound": "hbm", "kernel": f"k_{dom}<2,4,float>", "achieved": achieved, "peak": peak,
+    roof = {"bound": "hbm", "kernel": f"k_{dom}<{W.dim},{W.p + 1},float>", "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
             "algorithmic_bytes_per_launch": alg, "launch_ms": float(kms[kdx]),
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800",
@@ -372,7 +443,7 @@ def run_gpu(args):
             outs[i][...] = sol.get_state(i)
     sol.synchronize()
     e2e_sec = time.perf_counter() - t0
-    e2e_val = E * NSP * STAGES * n_e2e / e2e_sec * (E_all / E)
+    e2e_val = E * W.nsp * STAGES * n_e2e / e2e_sec * (E_all / E)
     state_bytes = sum(u.nbytes for u in states)
     del sol
     torch.cuda.empty_cache()
@@ -392,7 +463,7 @@ def run_gpu(args):
         b.synchronize()
         t64 += a.elapsed_time(b)
         del s64
-    fp64_val = E * NSP * STAGES * n64 / (t64 / 1e3)
+    fp64_val = E * W.nsp * STAGES * n64 / (t64 / 1e3)
 
     if dist:
         dist.barrier()
@@ -400,10 +471,9 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD if CANDIDATES == N_INST else
-                           WORKLOAD.replace("32 NACA", f"{CANDIDATES} of the 32 NACA"),
+                "config": {"workload": workload_text(),
                            "candidates_per_gpu": len(fms), "elements_per_gpu": E,
-                           "sol_pts_per_gpu": E * NSP, "p": P, "dt": dt,
+                           "sol_pts_per_gpu": E * W.nsp, "p": W.p, "dt": dt,
                            "l2": "inputs larger than L2 (FP32 working set %.2f GB > 129 MB), no flush"
                                  % (sol_bytes(E) / 1e9)},
                 "roofline": roof,
@@ -429,7 +499,14 @@ def run_gpu(args):
 
 def sol_bytes(E):
     s = 4
-    return E * (NSP * V * s * 4 + NFP * V * s * 3 + NSP * 5 * s + NFP * 2 * s + NFP * 4)
+    NSP, NFP, V = W.nsp, W.nfp, W.V
+    return E * (NSP * V * s * 4 + NFP * V * s * 3 + NSP * W.MS * s + NFP * W.dim * s + NFP * 4)
+
+
+def workload_text():
+    if CANDIDATES == W.candidates:
+        return W.desc
+    return f"{CANDIDATES} of the " + W.desc
 
 
 def main():
@@ -440,10 +517,12 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--candidates", type=int, default=N_INST)
+    ap.add_argument("--workload", default="airfoil", choices=sorted(WORKLOADS))
+    ap.add_argument("--candidates", type=int, default=0)
     args = ap.parse_args()
-    global CANDIDATES
-    CANDIDATES = max(1, min(N_INST, args.candidates))
+    global CANDIDATES, W
+    W = WORKLOADS[args.workload]
+    CANDIDATES = W.candidates if args.candidates <= 0 else max(1, min(W.candidates, args.candidates))
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     if args.impl == "reference":
