@@ -58,6 +58,9 @@ typedef int fr_status;
 #define FR_RK4 0            /* classical 4-stage RK */
 #define FR_LSRK45 1         /* Carpenter-Kennedy 5-stage 4th-order 2N-storage */
 
+#define FR_FLUX_RUSANOV 0   /* local Lax-Friedrichs: max |v.n| + c of both sides */
+#define FR_FLUX_ROE 1       /* Roe averages, Harten entropy fix on the acoustic waves */
+
 #define FR_FP64 0           /* plain FP64 state, geometry and arithmetic */
 #define FR_FP32 1           /* FP32 state/fluxes/contractions; geometry computed in
                                FP64 then cast; FP64 probe/force/conservation sums */
@@ -81,7 +84,7 @@ typedef struct fr_config {
     int viscous;           /* 0: Euler, 1: Navier-Stokes (BR2) */
     int rk;                /* FR_RK4 or FR_LSRK45 */
     int precision;         /* FR_FP64 or FR_FP32 */
-    int reserved;
+    int flux;              /* inviscid interface flux: FR_FLUX_RUSANOV or FR_FLUX_ROE */
 } fr_config;
 
 /* Build one mesh (host, FP64).  The FR discretisation is Huynh's Flux

@@ -188,7 +188,7 @@ class FRDiscretisation:
             fk = kf == k
             Fdisc[:, fk, :] = np.einsum("fs,esv->efv", ref.M0[fk], Fhat[:, :, k, :])
         Fdisc *= ref.fp_sign[None, :, None]
-        Fstar = phys.rusanov(uLA, uRA, nA)
+        Fstar = phys.common_inviscid(uLA, uRA, nA)
         if phys.viscous:
             part = self.partner[A]
             pe = np.where(part >= 0, part // nfp, 0)

@@ -21,6 +21,8 @@ Secs. 3.1.1 and 4.1.1 but not their formulas; these are the readings used):
 
 * Rusanov: F* n = 1/2 (F(u_L) + F(u_R)) . n - 1/2 lambda |n| (u_R - u_L),
   lambda = max over both sides of |v . n_hat| + c;
+* Roe (alternative): Roe-averaged state, acoustic, entropy and shear waves,
+  Harten's entropy fix (delta = 0.1 c) on the acoustic waves;
 * no-slip adiabatic wall: inviscid ghost with mirrored velocity and the same
   density and pressure; wall state for gradients with zero velocity, the
   interior density and interior internal energy; viscous normal flux from
@@ -40,7 +42,7 @@ import numpy as np
 class NavierStokes:
     def __init__(self, dim, gamma=1.4, mu=0.0, prandtl=0.71, viscous=False,
                  rho_inf=1.0, v_inf=None, p_inf=1.0, inflow_delta=0.0,
-                 inflow_ywall=0.0):
+                 inflow_ywall=0.0, flux="rusanov"):
         self.dim = dim
         self.nvar = dim + 2
         self.gamma = gamma
@@ -52,6 +54,9 @@ class NavierStokes:
         self.p_inf = p_inf
         self.inflow_delta = inflow_delta
         self.inflow_ywall = inflow_ywall
+        if flux not in ("rusanov", "roe"):
+            raise ValueError(flux)
+        self.flux = flux
 
     # -- primitive variables -------------------------------------------------
     def primitives(self, u):
@@ -122,6 +127,72 @@ class NavierStokes:
         lam = np.maximum(np.abs(np.sum(vL * nhat, -1)) + self.sound_speed(rL, pL),
                          np.abs(np.sum(vR * nhat, -1)) + self.sound_speed(rR, pR))
         return 0.5 * (FL + FR) - 0.5 * (lam * nmag)[..., None] * (uR - uL)
+
+    def roe_waves(self, uL, uR, nhat):
+        """Roe-averaged state and the wave decomposition of u_R - u_L along
+        the unit normal: returns (lambdas, strengths, eigenvectors) with
+        eigenvectors[..., k, :] the k-th right eigenvector (conserved
+        variables).  Waves: v_n - c, v_n (entropy), v_n + c, and the shear
+        jump (v_n; its 'strength' 1 and 'eigenvector' the shear vector)."""
+        g1 = self.gamma - 1.0
+        d = self.dim
+        rL, vL, pL = self.primitives(uL)
+        rR, vR, pR = self.primitives(uR)
+        HL = (uL[..., -1] + pL) / rL
+        HR = (uR[..., -1] + pR) / rR
+        sL, sR = np.sqrt(rL), np.sqrt(rR)
+        wL, wR = sL / (sL + sR), sR / (sL + sR)
+        rt = sL * sR
+        vt = wL[..., None] * vL + wR[..., None] * vR
+        Ht = wL * HL + wR * HR
+        q2 = np.sum(vt * vt, -1)
+        ct = np.sqrt(g1 * (Ht - 0.5 * q2))
+        vnt = np.sum(vt * nhat, -1)
+        drho = rR - rL
+        dp = pR - pL
+        dv = vR - vL
+        dvn = np.sum(dv * nhat, -1)
+        dvt = dv - dvn[..., None] * nhat
+        a1 = (dp - rt * ct * dvn) / (2 * ct * ct)
+        a2 = drho - dp / (ct * ct)
+        a3 = (dp + rt * ct * dvn) / (2 * ct * ct)
+        shape = uL.shape[:-1]
+        R = np.zeros(shape + (4, self.nvar))
+        R[..., 0, 0] = 1.0
+        R[..., 0, 1:1 + d] = vt - ct[..., None] * nhat
+        R[..., 0, -1] = Ht - vnt * ct
+        R[..., 1, 0] = 1.0
+        R[..., 1, 1:1 + d] = vt
+        R[..., 1, -1] = 0.5 * q2
+        R[..., 2, 0] = 1.0
+        R[..., 2, 1:1 + d] = vt + ct[..., None] * nhat
+        R[..., 2, -1] = Ht + vnt * ct
+        R[..., 3, 1:1 + d] = rt[..., None] * dvt
+        R[..., 3, -1] = rt * np.sum(vt * dvt, -1)
+        lam = np.stack([vnt - ct, vnt, vnt + ct, vnt], -1)
+        alpha = np.stack([a1, a2, a3, np.ones_like(a1)], -1)
+        return lam, alpha, R, ct
+
+    def roe(self, uL, uR, n):
+        """Roe's approximate Riemann solver (normal n scaled by |dS|):
+        1/2 (F_L + F_R).n - 1/2 |n| sum_k |lambda_k| alpha_k r_k, with
+        Harten's entropy fix on the two acoustic waves: |lambda| replaced by
+        (lambda^2 + delta^2) / (2 delta) below delta = 0.1 c."""
+        nmag = np.linalg.norm(n, axis=-1)
+        nhat = n / nmag[..., None]
+        FL = np.einsum("...jv,...j->...v", self.inviscid_flux(uL), n)
+        FR = np.einsum("...jv,...j->...v", self.inviscid_flux(uR), n)
+        lam, alpha, R, ct = self.roe_waves(uL, uR, nhat)
+        alam = np.abs(lam)
+        delta = 0.1 * ct
+        for k in (0, 2):
+            small = alam[..., k] < delta
+            alam[..., k] = np.where(small, (lam[..., k] ** 2 + delta ** 2) / (2 * delta), alam[..., k])
+        diss = np.einsum("...k,...kv->...v", alam * alpha, R)
+        return 0.5 * (FL + FR) - 0.5 * nmag[..., None] * diss
+
+    def common_inviscid(self, uL, uR, n):
+        return self.roe(uL, uR, n) if self.flux == "roe" else self.rusanov(uL, uR, n)
 
     # -- boundary states ----------------------------------------------------------
     def wall_ghost(self, uL, nhat):
@@ -200,4 +271,7 @@ class ScalarDiffusion:
         return self.nu * grad
 
     def rusanov(self, uL, uR, n):
+        return np.zeros_like(uL)
+
+    def common_inviscid(self, uL, uR, n):
         return np.zeros_like(uL)

@@ -143,6 +143,7 @@ fr_status check_batch(fr_mesh *const *meshes, int n_inst, const fr_config *cfg) 
     }
     if (cfg->rk != FR_RK4 && cfg->rk != FR_LSRK45) { set_error("unknown rk scheme"); return FR_ERR_INVALID_ARG; }
     if (cfg->precision != FR_FP64 && cfg->precision != FR_FP32) { set_error("unknown precision"); return FR_ERR_INVALID_ARG; }
+    if (cfg->flux != FR_FLUX_RUSANOV && cfg->flux != FR_FLUX_ROE) { set_error("unknown interface flux"); return FR_ERR_INVALID_ARG; }
     if (!(cfg->gamma > 1.0) || !(cfg->rho_inf > 0.0) || !(cfg->p_inf > 0.0) || cfg->mu < 0.0 ||
         (cfg->viscous && !(cfg->prandtl > 0.0))) {
         set_error("invalid physical constants");
@@ -191,6 +192,7 @@ void fill_args(const fr_solver *s, frk::KArgs<real> &a) {
     a.rho_inf = (real)s->cfg.rho_inf;
     a.p_inf = (real)s->cfg.p_inf;
     a.dt = (real)s->cfg.dt;
+    a.flux = s->cfg.flux;
     a.probes = s->probes;
     a.pacc = s->pacc;
     a.n_probe = s->n_probe;

@@ -88,6 +88,7 @@ struct KArgs {
     const int32_t *EINST;      // [E] instance of each element
     // physics
     real gamma, prandtl, mu, eta, rho_inf, p_inf;
+    int flux;                  // 0 Rusanov, 1 Roe
     // stage
     int mode, force;
     real rk_a, rk_b, rk_c, dt;
@@ -210,6 +211,71 @@ __device__ __forceinline__ void rusanov(const real *uL, const real *uR, const re
     const real lam = fmax(fabs(vnL) / nm + sqrt(c2L), fabs(vnR) / nm + sqrt(c2R));
 #pragma unroll
     for (int v = 0; v < V; ++v) F[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * (lam * nm) * (uR[v] - uL[v]);
+}
+
+// Roe's approximate Riemann solver (n scaled by |dS|): Roe-averaged state,
+// acoustic / entropy / shear waves, Harten's entropy fix (delta = 0.1 c) on the
+// acoustic waves.
+template <int D, typename real>
+__device__ __forceinline__ void roe(const real *uL, const real *uR, const real *n, real gamma, real *F) {
+    constexpr int V = D + 2;
+    const real gm1 = gamma - real(1);
+    real nn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn += n[j] * n[j];
+    const real nm = sqrt(nn), inm = real(1) / nm;
+    real nh[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) nh[j] = n[j] * inm;
+    real FL[V], FR[V], vnL, vnR, c2L, c2R;
+    flux_normal<D>(uL, n, gm1, FL, vnL, c2L, gamma);
+    flux_normal<D>(uR, n, gm1, FR, vnR, c2R, gamma);
+    real rL, vL[D], pL, rR, vR[D], pR;
+    primitives<D>(uL, gm1, rL, vL, pL);
+    primitives<D>(uR, gm1, rR, vR, pR);
+    const real HL = (uL[V - 1] + pL) / rL, HR = (uR[V - 1] + pR) / rR;
+    const real sL = sqrt(rL), sR = sqrt(rR), isum = real(1) / (sL + sR);
+    const real wL = sL * isum, wR = sR * isum, rt = sL * sR;
+    real vt[D], q2 = 0, vnt = 0, dvn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        vt[j] = wL * vL[j] + wR * vR[j];
+        q2 += vt[j] * vt[j];
+        vnt += vt[j] * nh[j];
+        dvn += (vR[j] - vL[j]) * nh[j];
+    }
+    const real Ht = wL * HL + wR * HR;
+    const real ct = sqrt(gm1 * (Ht - real(0.5) * q2));
+    const real ic2 = real(1) / (ct * ct);
+    const real drho = rR - rL, dp = pR - pL;
+    const real a1 = (dp - rt * ct * dvn) * real(0.5) * ic2;
+    const real a2 = drho - dp * ic2;
+    const real a3 = (dp + rt * ct * dvn) * real(0.5) * ic2;
+    real l1 = fabs(vnt - ct), l2 = fabs(vnt), l3 = fabs(vnt + ct);
+    const real del = real(0.1) * ct;
+    if (l1 < del) l1 = ((vnt - ct) * (vnt - ct) + del * del) / (real(2) * del);
+    if (l3 < del) l3 = ((vnt + ct) * (vnt + ct) + del * del) / (real(2) * del);
+    // sum_k |lambda_k| alpha_k r_k
+    real diss[V];
+    const real w1 = l1 * a1, w2 = l2 * a2, w3 = l3 * a3;
+    diss[0] = w1 + w2 + w3;
+    real vdt = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const real dvt = (vR[j] - vL[j]) - dvn * nh[j];
+        vdt += vt[j] * dvt;
+        diss[1 + j] = w1 * (vt[j] - ct * nh[j]) + w2 * vt[j] + w3 * (vt[j] + ct * nh[j]) + l2 * rt * dvt;
+    }
+    diss[V - 1] = w1 * (Ht - vnt * ct) + w2 * real(0.5) * q2 + w3 * (Ht + vnt * ct) + l2 * rt * vdt;
+#pragma unroll
+    for (int v = 0; v < V; ++v) F[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * nm * diss[v];
+}
+
+template <int D, typename real>
+__device__ __forceinline__ void common_inviscid(int flux, const real *uL, const real *uR, const real *n,
+                                                real gamma, real *F) {
+    if (flux == 1) roe<D>(uL, uR, n, gamma, F);
+    else rusanov<D>(uL, uR, n, gamma, F);
 }
 
 // inviscid flux F_j, j = 0..D-1
@@ -769,7 +835,7 @@ k_flux(const KArgs<real> a) {
             uRp = ug;
         }
         real Fs[V];
-        rusanov<D>(uL, uRp, nr[it], a.gamma, Fs);
+        common_inviscid<D>(a.flux, uL, uRp, nr[it], a.gamma, Fs);
         if (VISC) {
             real dd[V];
             if (pt[it] >= 0) {

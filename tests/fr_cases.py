@@ -27,6 +27,7 @@ class Case:
     v_inf: tuple = (1.0, 0.0)
     inflow_delta: float = 0.0
     inflow_ywall: float = 0.0
+    flux: str = "rusanov"
 
     @property
     def dim(self):
@@ -42,7 +43,8 @@ def oracle_disc(case: Case, inst: int = 0):
     from oracle.physics import NavierStokes
     ph = NavierStokes(case.dim, gamma=GAMMA, mu=case.mu, prandtl=PR, viscous=case.viscous,
                       rho_inf=1.0, v_inf=case.v_inf[:case.dim], p_inf=case.p_inf,
-                      inflow_delta=case.inflow_delta, inflow_ywall=case.inflow_ywall)
+                      inflow_delta=case.inflow_delta, inflow_ywall=case.inflow_ywall,
+                      flux=case.flux)
     return FRDiscretisation(case.meshes[inst], case.p, ph)
 
 
@@ -52,7 +54,8 @@ def lib_config(case: Case, precision: str):
                           v_inf=case.v_inf, p_inf=case.p_inf, inflow_delta=case.inflow_delta,
                           inflow_ywall=case.inflow_ywall, dt=case.dt, viscous=case.viscous,
                           rk=fr.FR_RK4 if case.rk == "rk4" else fr.FR_LSRK45,
-                          precision=fr.FR_FP64 if precision == "fp64" else fr.FR_FP32)
+                          precision=fr.FR_FP64 if precision == "fp64" else fr.FR_FP32,
+                          flux=fr.FR_FLUX_ROE if case.flux == "roe" else fr.FR_FLUX_RUSANOV)
 
 
 def lib_solver(case: Case, precision: str):

@@ -282,3 +282,28 @@ def test_tandem_cylinders_lsrk45_steps_fp64():
     assert FC.rel_l2(sol.get_state(0), ur) < 1e-12
     pr = Probe(disc, case.meshes[0].info["probes"][1])
     assert abs(sol.probe_pressure(pid) - pr.pressure(ur)) < 1e-11 * pr.pressure(ur)
+
+
+@pytest.mark.parametrize("maker", [lambda: FC.cavity_case(target=1500, p=3),
+                                   lambda: FC.tgv_case(n=3, p=3),
+                                   lambda: FC.airfoil_case(n_inst=2)])
+def test_roe_flux_residual_fp64_and_fp32(maker):
+    import dataclasses
+    case = dataclasses.replace(maker(), flux="roe")
+    _, _, _, Rg, Rr = _residual_pair(case, "fp64")
+    assert FC.rel_l2(Rg, Rr) < 1e-12
+    _fp32_check(case, "roe " + case.name)
+
+
+def test_roe_flux_steps_fp64():
+    import dataclasses
+    case = dataclasses.replace(FC.periodic_ns_case(n=5, p=3), flux="roe")
+    sol = FC.lib_solver(case, "fp64")
+    disc = FC.oracle_disc(case)
+    u = FC.initial_state(case, disc.sol_coords())
+    sol.set_state(0, u)
+    sol.rk_step(3)
+    ur = u
+    for _ in range(3):
+        ur = T.lsrk45_step(disc.residual, ur, case.dt)
+    assert FC.rel_l2(sol.get_state(0), ur) < 1e-12

@@ -413,3 +413,66 @@ def test_wall_force_linear_shear_is_exact():
     assert abs(F[0] - mu * a * L) < 1e-12
     # pressure on the wall pushes into it (-y is the fluid's outward normal)
     assert abs(F[1] - (-10.0 * L)) < 1e-11
+
+
+def test_roe_wave_decomposition_reproduces_the_flux_jump():
+    """Roe's property: the signed wave sum sum_k lambda_k alpha_k r_k of the
+    Roe-averaged linearisation equals (F(u_R) - F(u_L)) . n_hat exactly."""
+    for dim in (2, 3):
+        ph = NavierStokes(dim, flux="roe")
+        rng = np.random.default_rng(dim)
+        uL = S.random_state(30, 1, dim, 0.5, amp=0.4, seed=5)[:, 0]
+        uR = S.random_state(30, 1, dim, 0.5, amp=0.4, seed=6)[:, 0]
+        n = rng.normal(size=(30, dim))
+        nhat = n / np.linalg.norm(n, axis=1)[:, None]
+        lam, alpha, R, _ = ph.roe_waves(uL, uR, nhat)
+        jump = np.einsum("ek,ek,ekv->ev", lam, alpha, R)
+        dF = np.einsum("ejv,ej->ev", ph.inviscid_flux(uR) - ph.inviscid_flux(uL), nhat)
+        assert np.allclose(jump, dF, rtol=1e-12, atol=1e-12 * np.abs(dF).max())
+        # and the strengths decompose the state jump itself
+        du = np.einsum("ek,ekv->ev", alpha, R)
+        assert np.allclose(du, uR - uL, rtol=1e-12, atol=1e-12)
+
+
+def test_roe_consistency_skew_symmetry_and_upwinding():
+    ph = NavierStokes(2, flux="roe")
+    rng = np.random.default_rng(9)
+    uL = S.random_state(20, 1, 2, 0.4, amp=0.2, seed=1)[:, 0]
+    uR = S.random_state(20, 1, 2, 0.4, amp=0.2, seed=2)[:, 0]
+    n = rng.normal(size=(20, 2))
+    assert np.allclose(ph.roe(uL, uL, n), np.einsum("ejv,ej->ev", ph.inviscid_flux(uL), n),
+                       rtol=1e-14, atol=1e-12)
+    assert np.allclose(ph.roe(uL, uR, n), -ph.roe(uR, uL, -n), rtol=1e-13, atol=1e-12)
+    # supersonic flow along +n: the common flux is the upwind (left) flux
+    sup = S.primitive_to_conserved(np.ones(3), np.array([[3.0, 0.0]] * 3), np.ones(3))
+    sup2 = S.primitive_to_conserved(np.full(3, 1.1), np.array([[3.2, 0.1]] * 3), np.full(3, 1.2))
+    nx = np.array([[1.0, 0.0]] * 3)
+    assert np.allclose(ph.roe(sup, sup2, nx), np.einsum("ejv,ej->ev", ph.inviscid_flux(sup), nx))
+
+
+@pytest.mark.parametrize("flux", ["roe"])
+def test_roe_scheme_preserves_free_stream_conserves_and_matches_dgsem(flux):
+    m = M.vortex_mesh(4, jitter=0.2)
+    d = FRDiscretisation(m, 3, NavierStokes(2, mu=0.02, viscous=True, flux=flux))
+    assert _fs_max(d) < 1e-11
+    g = d.geometry()
+    U = S.random_state(m.n_elem, d.ref.nsp, 2, 0.3, amp=0.1)
+    R = d.residual(U)
+    tot = np.einsum("es,s,esv->v", g.J, d.ref.sp_w, R)
+    scale = np.einsum("es,s,esv->v", g.J, d.ref.sp_w, np.abs(R))
+    assert np.all(np.abs(tot) < 1e-13 * scale)
+
+
+@pytest.mark.slow
+def test_roe_vortex_converges_at_design_order():
+    def err(n):
+        m = M.vortex_mesh(n)
+        d = FRDiscretisation(m, 3, NavierStokes(2, flux="roe"))
+        x = d.sol_coords()
+        U = S.isentropic_vortex(x)
+        for _ in range(20):
+            U = T.rk4_step(d.residual, U, 5e-3)
+        ex = S.isentropic_vortex(x, t=0.1)
+        g = d.geometry()
+        return np.sqrt(np.einsum("es,s,es->", g.J, d.ref.sp_w, (U - ex)[..., 0] ** 2))
+    assert np.log2(err(16) / err(32)) > 3.6
