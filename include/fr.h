@@ -150,6 +150,11 @@ fr_status fr_rk_step(fr_solver *solver, int n_steps);
 fr_status fr_probe_add(fr_solver *solver, int inst, const double *x, int *probe_id);
 /* Pressure at the probe after the last completed step (synchronises). */
 fr_status fr_probe_pressure(fr_solver *solver, int probe_id, double *p_latest);
+/* The most recent pressure samples of one probe since the last reset, oldest
+ * first: min(count, 4096, max_n) values into out (host), their number in
+ * *n_out (the device keeps a 4096-sample ring per probe), for spectra of the
+ * observer signal (Welch PSD, Secs. 3.2, 4.2, 5.2 figures).  Synchronises. */
+fr_status fr_probe_history(fr_solver *solver, int probe_id, double *out, int max_n, int *n_out);
 /* Start a new averaging window: zero all probe and force accumulators. */
 fr_status fr_probe_reset(fr_solver *solver);
 /* OASPL in dB (Sec. 3.1.2, Eqs. 9-12) over the samples since the last reset:

@@ -68,6 +68,7 @@ struct fr_solver {
     double *stage64 = nullptr, *force_acc = nullptr, *partials = nullptr, *reduce_out = nullptr;
     frk::ProbeDesc *probes = nullptr;
     frk::ProbeAcc *pacc = nullptr;
+    double *phist = nullptr;
     int n_probe = 0;
     std::vector<int> probe_inst;
     int parity = 0;
@@ -97,7 +98,7 @@ namespace {
 
 struct Layout {
     size_t U, R1, R2, RES, UF0, UF1, FV, MET, NRM, PART, EINST, BTAG, BVREF, WALL, STAGE, PROBES,
-        PACC, FORCE, PART_SUMS, RED, total;
+        PACC, PHIST, FORCE, PART_SUMS, RED, total;
 };
 
 Layout make_layout(int dim, int nsp, int nfp, int64_t E, int64_t nb, int64_t nw, int64_t max_e,
@@ -125,6 +126,7 @@ Layout make_layout(int dim, int nsp, int nfp, int64_t E, int64_t nb, int64_t nw,
     L.STAGE = take((size_t)max_e * nsp * V * 8);
     L.PROBES = take(sizeof(frk::ProbeDesc) * kMaxProbes);
     L.PACC = take(sizeof(frk::ProbeAcc) * kMaxProbes);
+    L.PHIST = take(sizeof(double) * kMaxProbes * frk::kHistLen);
     L.FORCE = take((size_t)n_inst * 3 * 8);
     L.PART_SUMS = take((size_t)kPartialBlocks * (2 * V + 1) * 8);
     L.RED = take((size_t)(V + 1) * 8);
@@ -195,6 +197,7 @@ void fill_args(const fr_solver *s, frk::KArgs<real> &a) {
     a.flux = s->cfg.flux;
     a.probes = s->probes;
     a.pacc = s->pacc;
+    a.phist = s->phist;
     a.n_probe = s->n_probe;
     a.force_acc = s->force_acc;
     a.partials = s->partials;
@@ -457,6 +460,7 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
     s->stage64 = (double *)(w + L.STAGE);
     s->probes = (frk::ProbeDesc *)(w + L.PROBES);
     s->pacc = (frk::ProbeAcc *)(w + L.PACC);
+    s->phist = (double *)(w + L.PHIST);
     s->force_acc = (double *)(w + L.FORCE);
     s->partials = (double *)(w + L.PART_SUMS);
     s->reduce_out = (double *)(w + L.RED);
@@ -737,6 +741,25 @@ extern "C" fr_status fr_probe_stats(fr_solver *s, int probe_id, double *out4) {
     out4[1] = a.count > 0 ? (a.sum + a.sum_c) / a.count : 0.0;
     out4[2] = a.sq0 + a.sq0_c;
     out4[3] = a.m2 + a.m2_c;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_probe_history(fr_solver *s, int probe_id, double *out, int max_n, int *n_out) {
+    if (!out || !n_out || max_n < 0) { set_error("invalid fr_probe_history arguments"); return FR_ERR_INVALID_ARG; }
+    frk::ProbeAcc a;
+    fr_status st = read_acc(s, probe_id, &a);
+    if (st != FR_OK) return st;
+    const int64_t count = (int64_t)a.count;
+    const int64_t keep = std::min<int64_t>(std::min<int64_t>(count, frk::kHistLen), max_n);
+    const double *ring = s->phist + (size_t)probe_id * frk::kHistLen;
+    // the most recent `keep` samples, oldest first: ring index (count - keep + i) % len
+    const int64_t first = (count - keep) % frk::kHistLen;
+    const int64_t n1 = std::min<int64_t>(keep, frk::kHistLen - first);
+    if (n1 > 0) FR_CK(cudaMemcpyAsync(out, ring + first, n1 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    if (keep > n1)
+        FR_CK(cudaMemcpyAsync(out + n1, ring, (keep - n1) * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+    FR_CK(cudaStreamSynchronize(s->stream));
+    *n_out = (int)keep;
     return FR_OK;
 }
 

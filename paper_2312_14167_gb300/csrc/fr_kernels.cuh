@@ -31,6 +31,7 @@
 namespace frk {
 
 constexpr int kMaxN = 5;
+constexpr int kHistLen = 4096;   // samples kept per observer (ring buffer)
 
 enum Kind : int {
     K_FLUX = 0,      // fused common flux / divergence / RK update
@@ -95,6 +96,7 @@ struct KArgs {
     // auxiliaries
     const ProbeDesc *probes;
     ProbeAcc *pacc;
+    double *phist;             // [probe][kHistLen] ring buffer of sampled pressures
     int n_probe;
     double *force_acc;         // [n_inst][3]
     const double *stage64;     // FP64 staging in
@@ -1093,6 +1095,7 @@ __global__ void k_probe(const KArgs<real> a) {
     A.mean += delta / n;
     neumaier_add(A.m2, A.m2_c, delta * (p - A.mean));
     A.last = p;
+    a.phist[(int64_t)pr * kHistLen + ((int64_t)n - 1) % kHistLen] = p;
 }
 
 // --------------------------------------------------------------------------

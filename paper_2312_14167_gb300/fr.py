@@ -27,6 +27,7 @@ STATUS = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_MESH", 3: "FR_ERR_UNSU
 EXPORTED = ["fr_mesh_create", "fr_mesh_destroy", "fr_mesh_info", "fr_mesh_sol_coords",
             "fr_workspace_bytes", "fr_solver_create", "fr_solver_destroy", "fr_set_state",
             "fr_get_state", "fr_residual", "fr_rk_step", "fr_probe_add", "fr_probe_pressure",
+            "fr_probe_history",
             "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
             "fr_integral", "fr_integral_static", "fr_last_launch_count", "fr_profile_steps",
             "fr_last_error"]
@@ -92,6 +93,7 @@ def lib():
     L.fr_probe_add.argtypes = [P, I, dp, C.POINTER(I)]
     L.fr_probe_pressure.argtypes = [P, I, dp]
     L.fr_probe_reset.argtypes = [P]
+    L.fr_probe_history.argtypes = [P, I, dp, I, C.POINTER(I)]
     L.fr_oaspl.argtypes = [P, C.POINTER(I), I, D, D, I, dp]
     L.fr_probe_stats.argtypes = [P, I, dp]
     L.fr_forces.argtypes = [P, I, dp]
@@ -228,6 +230,12 @@ class Solver:
         v = C.c_double()
         _check(lib().fr_probe_pressure(self.handle, pid, C.byref(v)), "fr_probe_pressure")
         return v.value
+
+    def probe_history(self, pid, max_n=4096):
+        out = np.empty(max_n)
+        n = C.c_int()
+        _check(lib().fr_probe_history(self.handle, pid, _dptr(out), max_n, C.byref(n)), "fr_probe_history")
+        return out[:n.value].copy()
 
     def probe_stats(self, pid):
         out = np.empty(4)

@@ -202,6 +202,12 @@ def test_probe_and_oaspl_match_oracle():
         assert abs(got - want) < 1e-6
     st = sol.probe_stats(ids[0])
     assert st[0] == 12
+    # the device ring buffer holds the same samples, oldest first
+    for k in range(2):
+        h = sol.probe_history(ids[k])
+        assert h.size == 12
+        assert np.allclose(h, hist[k], rtol=1e-11, atol=0.0)
+        assert np.array_equal(sol.probe_history(ids[k], max_n=5), h[-5:])
     assert abs(np.sqrt(st[2] / 12) - p_rms(hist[0], 0)) < 1e-9 * max(p_rms(hist[0], 0), 1e-30)
 
 
