@@ -126,8 +126,12 @@ NCU_TRAFFIC = {
 
 
 def kernel_source_hash():
-    with open(os.path.join(ROOT, "paper_2312_14167_gb300", "csrc", "fr_kernels.cuh"), "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    """sha256 of the kernel source and the build script (its flags)."""
+    h = hashlib.sha256()
+    for rel in (("csrc", "fr_kernels.cuh"), ("build.py",)):
+        with open(os.path.join(ROOT, "paper_2312_14167_gb300", *rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 def combine_ranks(dist, ms, units, device="cpu"):

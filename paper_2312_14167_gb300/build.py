@@ -62,6 +62,10 @@ def build(force: bool = False, verbose: bool = False) -> str:
         o = os.path.join(BUILD, src + ".o")
         if force or _stale(o, s):
             cmd = [nvcc] + _flags() + ["-c", s, "-o", o]
+            if src.endswith("_f32.cu") and os.environ.get("FR_F32_FAST", "1") == "1":
+                # FP32 kernels: approximate division / square root (a few ulp)
+                # and flush-to-zero; the FP32 parity tests bound the result
+                cmd = cmd[:1] + ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"] + cmd[1:]
             if src.endswith(".cpp"):
                 cmd = [nvcc, "-x", "cu"] + _flags() + ["-Xcompiler", "-fopenmp", "-c", s, "-o", o]
             jobs.append((src, cmd))
