@@ -61,6 +61,16 @@ typedef int fr_status;
 #define FR_FLUX_RUSANOV 0   /* local Lax-Friedrichs: max |v.n| + c of both sides */
 #define FR_FLUX_ROE 1       /* Roe averages, Harten entropy fix on the acoustic waves */
 
+/* viscous interface scheme.  BR2: face gradient = interpolated uncorrected
+ * gradient + eta x lifting of that face's jump, central viscous flux.  LDG:
+ * each interface has a fixed left side (the point with the smaller global
+ * index, s = +1 there, -1 on the other side); common solution
+ * (1/2 + s beta) u_own + (1/2 - s beta) u_other, face gradient = the corrected
+ * gradient interpolated to the face, common viscous normal flux
+ * (1/2 - s beta) F_own.n + (1/2 + s beta) F_other.n - tau |n| (u_own - u_other). */
+#define FR_VISC_BR2 0
+#define FR_VISC_LDG 1
+
 #define FR_FP64 0           /* plain FP64 state, geometry and arithmetic */
 #define FR_FP32 1           /* FP32 state/fluxes/contractions; geometry computed in
                                FP64 then cast; FP64 probe/force/conservation sums */
@@ -85,6 +95,10 @@ typedef struct fr_config {
     int rk;                /* FR_RK4 or FR_LSRK45 */
     int precision;         /* FR_FP64 or FR_FP32 */
     int flux;              /* inviscid interface flux: FR_FLUX_RUSANOV or FR_FLUX_ROE */
+    int viscous_scheme;    /* FR_VISC_BR2 or FR_VISC_LDG */
+    int reserved;
+    double ldg_beta;       /* LDG: one-sidedness of the common solution (0.5: upwind) */
+    double ldg_tau;        /* LDG: penalty on the solution jump */
 } fr_config;
 
 /* Build one mesh (host, FP64).  The FR discretisation is Huynh's Flux

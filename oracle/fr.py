@@ -33,7 +33,17 @@ from .geometry import Geometry, connectivity
 
 
 class FRDiscretisation:
-    def __init__(self, mesh, p, phys, br2_eta=None):
+    """``viscous_scheme``: "br2" (default) or "ldg".  LDG reading: every
+    interface has a fixed left side, the side whose flux point has the
+    smaller index (element * nfp + point); with s = +1 there and -1 on the
+    other side, the common solution is (1/2 + s beta) u_own + (1/2 - s beta)
+    u_other, the face gradient is the corrected gradient interpolated to the
+    face (no lifting), and the common viscous normal flux is
+    (1/2 - s beta) F_v,own . n + (1/2 + s beta) F_v,other . n
+    - tau |n| (u_own - u_other); boundary points as for BR2."""
+
+    def __init__(self, mesh, p, phys, br2_eta=None, viscous_scheme="br2", ldg_beta=0.5,
+                 ldg_tau=0.1):
         self.mesh = mesh
         self.ref = RefElement(mesh.dim, p)
         self.phys = phys
@@ -41,6 +51,12 @@ class FRDiscretisation:
         nfp = self.ref.nfp
         self.partner_elem = np.where(self.partner >= 0, self.partner // nfp, -1)
         self.eta = float(2 * mesh.dim if br2_eta is None or br2_eta <= 0 else br2_eta)
+        if viscous_scheme not in ("br2", "ldg"):
+            raise ValueError(viscous_scheme)
+        self.scheme = viscous_scheme
+        self.beta, self.tau = ldg_beta, ldg_tau
+        own = np.arange(mesh.n_elem)[:, None] * nfp + np.arange(nfp)[None, :]
+        self.side = np.where(own < self.partner, 1.0, -1.0)     # +1 on an interface's left side
         self._geo_all = None
 
     # -- geometry ---------------------------------------------------------------
@@ -89,7 +105,12 @@ class FRDiscretisation:
         nfp = ref.nfp
         rowsB = loc[B]
         uLB, uRB, uBB, bcsB = self._outer_state(ctx, B)
-        uc = np.where((bcsB > 0)[..., None], uBB, 0.5 * (uLB + uRB))
+        if self.scheme == "ldg":
+            bs = (self.beta * self.side[B])[..., None]
+            uc_int = (0.5 + bs) * uLB + (0.5 - bs) * uRB
+        else:
+            uc_int = 0.5 * (uLB + uRB)
+        uc = np.where((bcsB > 0)[..., None], uBB, uc_int)
         dU = uc - uLB                                                # (nB, nfp, V)
         SB, JB = geoC.S[rowsB], geoC.J[rowsB]
         Du = np.einsum("kst,etv->eskv", ref.D, UC[rowsB])            # D_k u
@@ -107,6 +128,8 @@ class FRDiscretisation:
             fk = kf == k
             Lf[:, fk, :] = np.einsum("fs,esj->efj", W[fk], SB[:, :, k, :] / JB[:, :, None])
         Q = Qd + self.eta * Lf[..., :, None] * dU[..., None, :]
+        if self.scheme == "ldg":
+            Q = np.einsum("fs,esjv->efjv", ref.M0, grad)             # corrected, no lifting
         nB = geoC.n[rowsB]
         fv_own = np.einsum("efjv,efj->efv", phys.viscous_flux(uLB, Q), nB)
         for tag in (2, 3, 4, 5):
@@ -194,7 +217,13 @@ class FRDiscretisation:
             pe = np.where(part >= 0, part // nfp, 0)
             pf = np.where(part >= 0, part % nfp, 0)
             fvR = fv_own[locB[pe], pf]
-            fv_common = np.where((bcsA > 0)[..., None], fvA, 0.5 * (fvA - fvR))
+            if self.scheme == "ldg":
+                bs = (self.beta * self.side[A])[..., None]
+                nmag = np.linalg.norm(nA, axis=-1)[..., None]
+                interior = (0.5 - bs) * fvA - (0.5 + bs) * fvR - self.tau * nmag * (uLA - uRA)
+            else:
+                interior = 0.5 * (fvA - fvR)
+            fv_common = np.where((bcsA > 0)[..., None], fvA, interior)
             Fstar = Fstar - fv_common
         jump = Fstar - Fdisc                                         # step 6
         div = np.einsum("kst,etkv->esv", ref.D, Fhat) + np.einsum("sf,efv->esv", ref.Cdiv, jump)

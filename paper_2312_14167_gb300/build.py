@@ -38,7 +38,8 @@ def _flags(debug=False):
         f += ["-Xptxas", "-v"]
     # tuning knobs for sweeps: minimum CTAs per SM asked of the register
     # allocator for the 2-D FP32 stage kernels
-    for knob in ("FR_MINB_FLUX_2D_F32", "FR_MINB_GRAD_2D_F32"):
+    for knob in ("FR_MINB_FLUX_2D_F32", "FR_MINB_GRAD_2D_F32", "FR_MINB_FLUX_3D_F32",
+                 "FR_MINB_GRAD_3D_F32"):
         if os.environ.get(knob):
             f += [f"-D{knob}={int(os.environ[knob])}"]
     return f

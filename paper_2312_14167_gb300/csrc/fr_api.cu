@@ -146,6 +146,7 @@ fr_status check_batch(fr_mesh *const *meshes, int n_inst, const fr_config *cfg) 
     if (cfg->rk != FR_RK4 && cfg->rk != FR_LSRK45) { set_error("unknown rk scheme"); return FR_ERR_INVALID_ARG; }
     if (cfg->precision != FR_FP64 && cfg->precision != FR_FP32) { set_error("unknown precision"); return FR_ERR_INVALID_ARG; }
     if (cfg->flux != FR_FLUX_RUSANOV && cfg->flux != FR_FLUX_ROE) { set_error("unknown interface flux"); return FR_ERR_INVALID_ARG; }
+    if (cfg->viscous_scheme != FR_VISC_BR2 && cfg->viscous_scheme != FR_VISC_LDG) { set_error("unknown viscous scheme"); return FR_ERR_INVALID_ARG; }
     if (!(cfg->gamma > 1.0) || !(cfg->rho_inf > 0.0) || !(cfg->p_inf > 0.0) || cfg->mu < 0.0 ||
         (cfg->viscous && !(cfg->prandtl > 0.0))) {
         set_error("invalid physical constants");
@@ -195,6 +196,9 @@ void fill_args(const fr_solver *s, frk::KArgs<real> &a) {
     a.p_inf = (real)s->cfg.p_inf;
     a.dt = (real)s->cfg.dt;
     a.flux = s->cfg.flux;
+    a.ldg = s->cfg.viscous_scheme == FR_VISC_LDG ? 1 : 0;
+    a.ldg_beta = (real)s->cfg.ldg_beta;
+    a.ldg_tau = (real)s->cfg.ldg_tau;
     a.probes = s->probes;
     a.pacc = s->pacc;
     a.phist = s->phist;

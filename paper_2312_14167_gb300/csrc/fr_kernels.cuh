@@ -90,6 +90,8 @@ struct KArgs {
     // physics
     real gamma, prandtl, mu, eta, rho_inf, p_inf;
     int flux;                  // 0 Rusanov, 1 Roe
+    int ldg;                   // viscous scheme: 0 BR2, 1 LDG
+    real ldg_beta, ldg_tau;
     // stage
     int mode, force;
     real rk_a, rk_b, rk_c, dt;
@@ -548,10 +550,21 @@ __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const 
 #ifndef FR_MINB_GRAD_2D_F32
 #define FR_MINB_GRAD_2D_F32 8
 #endif
-template <int D, typename real, bool GRAD = false>
+// 3-D FP32 (TGV p=3, tandem cylinders p=4): flux kernel best at 3 CTAs for
+// p <= 3 and 4 for p = 4, gradient kernel at 4.
+#ifndef FR_MINB_FLUX_3D_F32
+#define FR_MINB_FLUX_3D_F32 0
+#endif
+#ifndef FR_MINB_GRAD_3D_F32
+#define FR_MINB_GRAD_3D_F32 4
+#endif
+template <int D, typename real, bool GRAD = false, int N = 4>
 struct MinBlocks {
+    static constexpr int flux3 = FR_MINB_FLUX_3D_F32 > 0 ? FR_MINB_FLUX_3D_F32 : (N >= 5 ? 4 : 3);
     static constexpr int value =
-        sizeof(real) == 8 ? 1 : (D == 2 ? (GRAD ? FR_MINB_GRAD_2D_F32 : FR_MINB_FLUX_2D_F32) : 2);
+        sizeof(real) == 8 ? 1
+        : (D == 2 ? (GRAD ? FR_MINB_GRAD_2D_F32 : FR_MINB_FLUX_2D_F32)
+                  : (GRAD ? FR_MINB_GRAD_3D_F32 : flux3));
 };
 
 // --------------------------------------------------------------------------
@@ -565,7 +578,7 @@ struct MinBlocks {
 // the tile load.
 // --------------------------------------------------------------------------
 template <int D, int N, typename real>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true>::value))
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true, N>::value))
 k_grad(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
@@ -617,9 +630,12 @@ k_grad(const KArgs<real> a) {
         interp_line<D, N, V, true>(sU, j, f, Lm, Lp, uL);
         real uc[V], ub[V];
         if (pt[it] >= 0) {
+            // LDG: one-sided common solution, left side = smaller point index
+            const int64_t gf = elem_of<real>(a.elist, e0, j) * NFP + f;
+            const real bs = a.ldg ? (gf < pt[it] ? a.ldg_beta : -a.ldg_beta) : real(0);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
-                uc[v] = real(0.5) * (uL[v] + uR[it][v]);
+                uc[v] = (real(0.5) + bs) * uL[v] + (real(0.5) - bs) * uR[it][v];
                 ub[v] = uL[v];
             }
         } else {
@@ -637,7 +653,9 @@ k_grad(const KArgs<real> a) {
         st_v<V>(sD + (j * NFP + f) * V, dd);
         st_v<V>(sB + (j * NFP + f) * V, ub);
     }
-    // solution-point phase: uncorrected physical gradient (1/J) S^T D u
+    // solution-point phase: physical gradient (1/J) S^T (D u [+ correction]):
+    // uncorrected for BR2 (its face value adds the lifting), corrected for LDG
+    if (a.ldg) __syncthreads();
     for (int w = tid; w < ne * NSP; w += blockDim.x) {
         const int j = w / NSP, s = w % NSP;
         const real *M = sM + (j * NSP + s) * MS;
@@ -650,6 +668,13 @@ k_grad(const KArgs<real> a) {
             const int q0 = j * NSP + s - ik * st;
 #pragma unroll
             for (int v = 0; v < V; ++v) Gk[k][v] = 0;
+            if (a.ldg) {
+                real dm[V], dp[V];
+                ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 0)) * V, dm);
+                ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 1)) * V, dp);
+#pragma unroll
+                for (int v = 0; v < V; ++v) Gk[k][v] = GL[ik] * dm[v] + GR[ik] * dp[v];
+            }
 #pragma unroll
             for (int m = 0; m < N; ++m) {
                 real x[V];
@@ -712,10 +737,11 @@ k_grad(const KArgs<real> a) {
         real dd[V], ub[V];
         ld_v<V>(sD + (j * NFP + f) * V, dd);
         ld_v<V>(sB + (j * NFP + f) * V, ub);
+        const real eta = a.ldg ? real(0) : a.eta;    // LDG: no lifting
 #pragma unroll
         for (int jd = 0; jd < D; ++jd)
 #pragma unroll
-            for (int v = 0; v < V; ++v) Q[jd][v] += a.eta * lf[jd] * dd[v];
+            for (int v = 0; v < V; ++v) Q[jd][v] += eta * lf[jd] * dd[v];
         real Fv[D][V];
         flux_vis<D>(ub, Q, a.gamma, a.mu, a.prandtl, Fv);
         real fvn[V];
@@ -748,7 +774,7 @@ k_grad(const KArgs<real> a) {
 // K_FLUX: fused common flux + transformed flux + divergence/correction + RK
 // --------------------------------------------------------------------------
 template <int D, int N, typename real, bool VISC>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, MinBlocks<D, real>::value)
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N>::value))
 k_flux(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
@@ -793,10 +819,14 @@ k_flux(const KArgs<real> a) {
     for (int it = 0; it < IT; ++it) {
         if (pt[it] >= 0) {
             if (VISC) {
+                // common viscous normal flux without the LDG penalty:
+                // BR2 1/2 (own - partner); LDG (1/2 - s beta) own - (1/2 + s beta) partner
                 real fp[V];
                 ldg_v<V>(a.FV + (int64_t)pt[it] * V, fp);
+                const int64_t gf = (e0 + (tid + it * G::THREADS) / NFP) * NFP + (tid + it * G::THREADS) % NFP;
+                const real bs = a.ldg ? (gf < pt[it] ? a.ldg_beta : -a.ldg_beta) : real(0);
 #pragma unroll
-                for (int v = 0; v < V; ++v) fv[it][v] = real(0.5) * (fv[it][v] - fp[v]);
+                for (int v = 0; v < V; ++v) fv[it][v] = (real(0.5) - bs) * fv[it][v] - (real(0.5) + bs) * fp[v];
             }
         }
     }
@@ -826,23 +856,34 @@ k_flux(const KArgs<real> a) {
         const int j = w / NFP, f = w % NFP;
         real uL[V];
         interp_line<D, N, V, false>(sU, j, f, Lm, Lp, uL);
-        real ub[V], ug[V];
-        const real *uRp = uR[it];
+        real ub[V], uRp[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) uRp[v] = uR[it][v];
         if (pt[it] < 0) {
             const int b = -1 - pt[it];
             real vref[D];
 #pragma unroll
             for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d];
-            bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, ug, ub);
-            uRp = ug;
+            bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, uRp, ub);
         }
         real Fs[V];
         common_inviscid<D>(a.flux, uL, uRp, nr[it], a.gamma, Fs);
         if (VISC) {
             real dd[V];
             if (pt[it] >= 0) {
+                const int64_t gf = (e0 + j) * NFP + f;
+                const real bs = a.ldg ? (gf < pt[it] ? a.ldg_beta : -a.ldg_beta) : real(0);
 #pragma unroll
-                for (int v = 0; v < V; ++v) dd[v] = real(0.5) * (uL[v] + uRp[v]) - uL[v];
+                for (int v = 0; v < V; ++v)
+                    dd[v] = (real(0.5) + bs) * uL[v] + (real(0.5) - bs) * uRp[v] - uL[v];
+                if (a.ldg) {
+                    real nn = 0;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) nn += nr[it][d] * nr[it][d];
+                    const real pen = a.ldg_tau * sqrt(nn);
+#pragma unroll
+                    for (int v = 0; v < V; ++v) Fs[v] += pen * (uL[v] - uRp[v]);
+                }
             } else {
 #pragma unroll
                 for (int v = 0; v < V; ++v) dd[v] = ub[v] - uL[v];

@@ -20,6 +20,7 @@ FR_TAG_FARFIELD, FR_TAG_INFLOW, FR_TAG_OUTFLOW = 3, 4, 5
 FR_RK4, FR_LSRK45 = 0, 1
 FR_FP64, FR_FP32 = 0, 1
 FR_FLUX_RUSANOV, FR_FLUX_ROE = 0, 1
+FR_VISC_BR2, FR_VISC_LDG = 0, 1
 
 STATUS = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_MESH", 3: "FR_ERR_UNSUPPORTED",
           4: "FR_ERR_CUDA", 5: "FR_ERR_NONFINITE", 6: "FR_ERR_TIMEOUT", 7: "FR_ERR_WORKSPACE"}
@@ -44,12 +45,15 @@ class Config(C.Structure):
                 ("rho_inf", C.c_double), ("v_inf", C.c_double * 3), ("p_inf", C.c_double),
                 ("inflow_delta", C.c_double), ("inflow_ywall", C.c_double),
                 ("br2_eta", C.c_double), ("dt", C.c_double), ("viscous", C.c_int),
-                ("rk", C.c_int), ("precision", C.c_int), ("flux", C.c_int)]
+                ("rk", C.c_int), ("precision", C.c_int), ("flux", C.c_int),
+                ("viscous_scheme", C.c_int), ("reserved", C.c_int), ("ldg_beta", C.c_double),
+                ("ldg_tau", C.c_double)]
 
 
 def make_config(dim, gamma=1.4, prandtl=0.71, mu=0.0, rho_inf=1.0, v_inf=None, p_inf=1.0,
                 inflow_delta=0.0, inflow_ywall=0.0, br2_eta=0.0, dt=1e-3, viscous=False,
-                rk=FR_LSRK45, precision=FR_FP64, flux=FR_FLUX_RUSANOV) -> Config:
+                rk=FR_LSRK45, precision=FR_FP64, flux=FR_FLUX_RUSANOV,
+                viscous_scheme=FR_VISC_BR2, ldg_beta=0.5, ldg_tau=0.1) -> Config:
     c = Config()
     c.gamma, c.prandtl, c.mu = gamma, prandtl, mu
     c.rho_inf, c.p_inf = rho_inf, p_inf
@@ -59,6 +63,7 @@ def make_config(dim, gamma=1.4, prandtl=0.71, mu=0.0, rho_inf=1.0, v_inf=None, p
     c.inflow_delta, c.inflow_ywall = inflow_delta, inflow_ywall
     c.br2_eta, c.dt = br2_eta, dt
     c.viscous, c.rk, c.precision, c.flux = int(bool(viscous)), rk, precision, flux
+    c.viscous_scheme, c.ldg_beta, c.ldg_tau = viscous_scheme, ldg_beta, ldg_tau
     return c
 
 

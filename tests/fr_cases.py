@@ -28,6 +28,7 @@ class Case:
     inflow_delta: float = 0.0
     inflow_ywall: float = 0.0
     flux: str = "rusanov"
+    viscous_scheme: str = "br2"
 
     @property
     def dim(self):
@@ -45,7 +46,7 @@ def oracle_disc(case: Case, inst: int = 0):
                       rho_inf=1.0, v_inf=case.v_inf[:case.dim], p_inf=case.p_inf,
                       inflow_delta=case.inflow_delta, inflow_ywall=case.inflow_ywall,
                       flux=case.flux)
-    return FRDiscretisation(case.meshes[inst], case.p, ph)
+    return FRDiscretisation(case.meshes[inst], case.p, ph, viscous_scheme=case.viscous_scheme)
 
 
 def lib_config(case: Case, precision: str):
@@ -55,7 +56,8 @@ def lib_config(case: Case, precision: str):
                           inflow_ywall=case.inflow_ywall, dt=case.dt, viscous=case.viscous,
                           rk=fr.FR_RK4 if case.rk == "rk4" else fr.FR_LSRK45,
                           precision=fr.FR_FP64 if precision == "fp64" else fr.FR_FP32,
-                          flux=fr.FR_FLUX_ROE if case.flux == "roe" else fr.FR_FLUX_RUSANOV)
+                          flux=fr.FR_FLUX_ROE if case.flux == "roe" else fr.FR_FLUX_RUSANOV,
+                          viscous_scheme=fr.FR_VISC_LDG if case.viscous_scheme == "ldg" else fr.FR_VISC_BR2)
 
 
 def lib_solver(case: Case, precision: str):

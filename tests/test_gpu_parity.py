@@ -313,3 +313,29 @@ def test_roe_flux_steps_fp64():
     for _ in range(3):
         ur = T.lsrk45_step(disc.residual, ur, case.dt)
     assert FC.rel_l2(sol.get_state(0), ur) < 1e-12
+
+
+@pytest.mark.parametrize("maker", [lambda: FC.periodic_ns_case(n=5, p=3),
+                                   lambda: FC.cavity_case(target=1500, p=3),
+                                   lambda: FC.tgv_case(n=3, p=3),
+                                   lambda: FC.tandem_case(n_inst=1, n_hex=700, n_span=3)])
+def test_ldg_viscous_scheme_residual_fp64_and_fp32(maker):
+    import dataclasses
+    case = dataclasses.replace(maker(), viscous_scheme="ldg")
+    _, _, _, Rg, Rr = _residual_pair(case, "fp64")
+    assert FC.rel_l2(Rg, Rr) < 1e-12
+    _fp32_check(case, "ldg " + case.name)
+
+
+def test_ldg_steps_fp64():
+    import dataclasses
+    case = dataclasses.replace(FC.periodic_ns_case(n=5, p=3), viscous_scheme="ldg")
+    sol = FC.lib_solver(case, "fp64")
+    disc = FC.oracle_disc(case)
+    u = FC.initial_state(case, disc.sol_coords())
+    sol.set_state(0, u)
+    sol.rk_step(3)
+    ur = u
+    for _ in range(3):
+        ur = T.lsrk45_step(disc.residual, ur, case.dt)
+    assert FC.rel_l2(sol.get_state(0), ur) < 1e-12

@@ -476,3 +476,39 @@ def test_roe_vortex_converges_at_design_order():
         g = d.geometry()
         return np.sqrt(np.einsum("es,s,es->", g.J, d.ref.sp_w, (U - ex)[..., 0] ** 2))
     assert np.log2(err(16) / err(32)) > 3.6
+
+
+def test_ldg_conserves_preserves_free_stream_and_has_single_valued_common_solution():
+    m = M.vortex_mesh(4, jitter=0.2)
+    d = FRDiscretisation(m, 3, NavierStokes(2, mu=0.03, viscous=True), viscous_scheme="ldg")
+    assert _fs_max(d) < 1e-11
+    g = d.geometry()
+    U = S.random_state(m.n_elem, d.ref.nsp, 2, 0.3, amp=0.1)
+    R = d.residual(U)
+    tot = np.einsum("es,s,esv->v", g.J, d.ref.sp_w, R)
+    scale = np.einsum("es,s,esv->v", g.J, d.ref.sp_w, np.abs(R))
+    assert np.all(np.abs(tot) < 1e-13 * scale)
+    # every interface has exactly one left side
+    own = np.arange(m.n_elem)[:, None] * d.ref.nfp + np.arange(d.ref.nfp)[None, :]
+    pe, pf = d.partner // d.ref.nfp, d.partner % d.ref.nfp
+    assert np.all(d.side + d.side[pe, pf] == 0)
+    assert np.all((d.side > 0) == (own < d.partner))
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("p", [2, 3])
+def test_ldg_heat_equation_decay_converges(p):
+    nu, t_end, steps = 0.1, 1.0, 400
+    errs = []
+    for n in (4, 8):
+        m = M.periodic_box(2, (n, n), (0, 0), (2 * np.pi, 2 * np.pi))
+        d = FRDiscretisation(m, p, ScalarDiffusion(2, nu), viscous_scheme="ldg")
+        x = d.sol_coords()
+        U = (np.sin(x[..., 0]) * np.sin(x[..., 1]))[..., None]
+        for _ in range(steps):
+            U = T.rk4_step(d.residual, U, t_end / steps)
+        ex = np.exp(-2 * nu * t_end) * np.sin(x[..., 0]) * np.sin(x[..., 1])
+        g = d.geometry()
+        errs.append(np.sqrt(np.einsum("es,s,es->", g.J, d.ref.sp_w, (U[..., 0] - ex) ** 2)))
+    assert errs[1] < 0.05
+    assert np.log2(errs[0] / errs[1]) > p + 0.5
