@@ -348,7 +348,8 @@ def run_gpu(args):
     cpu_base = None
     if world == 1 and not args.no_cpu_baseline:
         # the oracle runs before the first CUDA call of this process
-        rate, sec, sample = oracle_sample_rate(meshes[0], 64, 12, dt)
+        # about 10-30 s of oracle work on one host core
+        rate, sec, sample = oracle_sample_rate(meshes[0], 256, 30, dt)
         cpu_base = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                     "seconds": sec}
     torch.cuda.set_device(local)
