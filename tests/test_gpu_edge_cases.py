@@ -1,0 +1,134 @@
+"""Edge cases of the CUDA path, against the oracle where there is a result:
+ragged element tiles for every degree and dimension, single-element
+periodic meshes (an element that is its own neighbour on every face), an
+element whose every face is a boundary, p = 1; empty / no-op calls and
+argument errors; non-finite detection; checkpoint and resume through
+fr_get_state / fr_set_state bitwise equal to an uninterrupted run."""
+import numpy as np
+import pytest
+
+from tests import fr_cases as FC
+from synth import meshes as M, states as S
+from oracle import timestep as T
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _case(mesh, p, visc=True):
+    v_inf = (1.0, 0.0) if mesh.dim == 2 else (1.0, 0.0, 0.0)
+    return FC.Case("edge", [mesh], p, visc, 0.01 if visc else 0.0, 0.3, dt=1e-3, v_inf=v_inf)
+
+
+def _parity(case, tol=1e-12):
+    sol = FC.lib_solver(case, "fp64")
+    disc = FC.oracle_disc(case)
+    u = S.smooth_perturbed(disc.sol_coords(), case.dim, case.mach, amp=0.05, seed=3)
+    sol.set_state(0, u)
+    err = FC.rel_l2(sol.residual(0), disc.residual(u))
+    assert err < tol, err
+    sol.rk_step(2)
+    ur = u
+    for _ in range(2):
+        ur = T.lsrk45_step(disc.residual, ur, case.dt)
+    assert FC.rel_l2(sol.get_state(0), ur) < tol
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_ragged_tiles_2d(p):
+    """Element counts that leave a partial last tile (tiles hold 256/(p+1)^2 elements)."""
+    ne = 256 // (p + 1) ** 2
+    nx = ne + 1
+    _parity(_case(M.periodic_box(2, (nx, 1), (0, 0), (1.0 * nx, 1.0), jitter=0.0), p))
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+def test_ragged_tiles_3d(p):
+    _parity(_case(M.periodic_box(3, (3, 2, 1), (0, 0, 0), (1.5, 1.0, 0.7), jitter=0.0), p))
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_single_element_periodic_in_every_direction(dim):
+    box = M.periodic_box(dim, (1,) * dim, (0,) * dim, (1.0,) * dim)
+    _parity(_case(box, 3))
+
+
+def test_element_with_every_face_on_a_boundary():
+    m = M.periodic_box(2, (1, 1), (0, 0), (1, 1))
+    m.face_tag = m.face_tag.copy()
+    m.face_tag[0] = [M.TAG_FARFIELD, M.TAG_OUTFLOW, M.TAG_WALL, M.TAG_FARFIELD]
+    _parity(_case(m, 3))
+
+
+def test_no_op_and_argument_errors():
+    from paper_2312_14167_gb300 import fr
+    case = _case(M.vortex_mesh(3), 2)
+    sol = FC.lib_solver(case, "fp64")
+    disc = FC.oracle_disc(case)
+    u = FC.initial_state(case, disc.sol_coords())
+    sol.set_state(0, u)
+    sol.rk_step(0)                                   # no steps: state unchanged
+    assert np.array_equal(sol.get_state(0), u)
+    # no instance 1: the binding's list index refuses it, and so does the C ABI
+    with pytest.raises(IndexError):
+        sol.set_state(1, u)
+    assert fr.lib().fr_set_state(sol.handle, 1, fr._dptr(u)) == 1
+    assert fr.lib().fr_set_state(sol.handle, -1, fr._dptr(u)) == 1
+    with pytest.raises(fr.FRError) as e:
+        sol.probe_add(0, np.array([100.0, 100.0]))   # outside the mesh
+    assert e.value.status == 1
+    with pytest.raises(fr.FRError):
+        sol.oaspl([0])                               # no probe 0 yet
+    with pytest.raises(ValueError):
+        sol.set_state(0, u[:-1])                     # wrong shape, refused by the binding
+    empty = M.vortex_mesh(3)
+    empty.elem_vert = empty.elem_vert[:0]
+    empty.face_tag = empty.face_tag[:0]
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(empty, 2)                            # an empty mesh is refused
+    assert e.value.status == 1
+
+
+def test_non_finite_state_is_reported():
+    case = _case(M.vortex_mesh(4), 2)
+    sol = FC.lib_solver(case, "fp32")
+    disc = FC.oracle_disc(case)
+    u = FC.initial_state(case, disc.sol_coords())
+    u[5, 3, 1] = np.nan
+    u[7, 0, 0] = np.inf
+    sol.set_state(0, u)
+    _, bad = sol.integral(0)
+    assert bad == 2
+    _, bad2 = sol.integral_static(0)
+    assert bad2 == 2
+
+
+@pytest.mark.parametrize("rk", ["lsrk45", "rk4"])
+def test_checkpoint_resume_is_bitwise_equal(rk):
+    import dataclasses
+    case = dataclasses.replace(FC.airfoil_case(n_inst=2), rk=rk)
+    full = FC.lib_solver(case, "fp32")
+    us = []
+    for i in range(2):
+        disc = FC.oracle_disc(case, i)
+        u = FC.initial_state(case, disc.sol_coords(), i)
+        full.set_state(i, u)
+        us.append(u)
+    full.rk_step(6)
+    first = FC.lib_solver(case, "fp32")
+    for i in range(2):
+        first.set_state(i, us[i])
+    first.rk_step(3)
+    ckpt = [first.get_state(i) for i in range(2)]    # FP64 copies of the FP32 state: exact
+    resumed = FC.lib_solver(case, "fp32")
+    for i in range(2):
+        resumed.set_state(i, ckpt[i])
+    resumed.rk_step(3)
+    for i in range(2):
+        assert np.array_equal(resumed.get_state(i), full.get_state(i))
