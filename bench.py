@@ -119,9 +119,9 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per element of one stage launch, ncu
     # --set full on the 8-airfoil case (243,854 quads; see profiles/k_flux_airfoil8_full.md),
     # scaled to a launch by the element count
-    "dcfa9ac0a49d66cf875235273ca393571a41e1e42e4909b2e383fe9edf4cb281":
-        {"flux_bytes_per_elem": (316.859904e6 + 154.2336e6) / 243854,
-         "grad_bytes_per_elem": (249.94304e6 + 44.918272e6) / 243854},
+    "8604a4f7492eb257985022f891afe006f399f942de4ccb7f3b49a5d7688f7832":
+        {"flux_bytes_per_elem": (313.369344e6 + 148.510976e6) / 243854,
+         "grad_bytes_per_elem": (249.985536e6 + 45.448192e6) / 243854},
 }
 
 
