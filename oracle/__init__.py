@@ -7,6 +7,7 @@ its Python binding) never does, and shares no code with it.
 Modules: ``basis`` (Gauss-Legendre points, Lagrange, DG correction),
 ``element`` (tensor reference element and dense operators), ``geometry``
 (element maps, metrics, face connectivity), ``physics`` (Navier-Stokes
-fluxes, Rusanov, boundary states), ``fr`` (residual), ``timestep`` (RK4,
+fluxes, Rusanov, boundary states), ``fr`` (residual), ``fr_var`` (residual
+with a degree per element, mortar coupling of unequal faces), ``timestep`` (RK4,
 LSRK45), ``acoustics`` (probe, OASPL).
 """

@@ -110,18 +110,15 @@ def _face_key_ids(ev, loc):
     return tuple(sorted(int(ev[c]) for c in loc))
 
 
-def connectivity(mesh, ref, tol=1e-8):
-    """Partner of every flux point.
-
-    Returns (partner, bc): partner[e, f] = e2 * nfp + f2 for connected flux
-    points, or -1 for boundary points; bc[e, f] = face tag (2..5) at boundary
-    points, 0 elsewhere."""
+def face_pairs(mesh):
+    """Every connected face seen from both sides: a list of (e, face, e2,
+    face2, shift) with the corners of (e, face) + shift on those of (e2,
+    face2).  Interior faces share their corner vertices; periodic faces are
+    matched by corner coordinates after adding or subtracting one of the
+    mesh's periodic shifts."""
     dim = mesh.dim
     faces = _QUAD_FACES if dim == 2 else _HEX_FACES
     E = mesh.n_elem
-    nfp, nfpf = ref.nfp, ref.nfpf
-    partner = np.full((E, nfp), -1, dtype=np.int64)
-    bc = np.zeros((E, nfp), dtype=np.int32)
     ev = mesh.elem_vert
     tags = mesh.face_tag
 
@@ -166,6 +163,22 @@ def connectivity(mesh, ref, tol=1e-8):
                 raise ValueError("periodic face without partner")
             (b, fb), sh = found
             pairs.append((e, fc, b, fb, sh))
+    return pairs
+
+
+def connectivity(mesh, ref, tol=1e-8):
+    """Partner of every flux point.
+
+    Returns (partner, bc): partner[e, f] = e2 * nfp + f2 for connected flux
+    points, or -1 for boundary points; bc[e, f] = face tag (2..5) at boundary
+    points, 0 elsewhere."""
+    dim = mesh.dim
+    E = mesh.n_elem
+    nfp, nfpf = ref.nfp, ref.nfpf
+    partner = np.full((E, nfp), -1, dtype=np.int64)
+    bc = np.zeros((E, nfp), dtype=np.int32)
+    tags = mesh.face_tag
+    pairs = face_pairs(mesh)
 
     if pairs:
         pe = np.array([p[0] for p in pairs])

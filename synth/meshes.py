@@ -724,3 +724,82 @@ def tandem_batch(n_inst: int = 16, seed: int = 2312, h_lo: int = 60000, h_hi: in
         nh = int(rng.uniform(h_lo, h_hi))
         out.append(tandem_cylinders(s, r, nh, n_span, q))
     return out
+
+
+# ---------------------------------------------------------------------------
+# element relabelling and per-element degree (input bookkeeping only)
+# ---------------------------------------------------------------------------
+
+def _rotations(dim):
+    """Signed permutation matrices with determinant +1 (the rotations of the
+    reference square / cube): 4 in 2-D, 24 in 3-D."""
+    import itertools
+    out = []
+    for perm in itertools.permutations(range(dim)):
+        for signs in itertools.product((1, -1), repeat=dim):
+            R = np.zeros((dim, dim), dtype=np.int64)
+            for r, (c, sg) in enumerate(zip(perm, signs)):
+                R[r, c] = sg
+            if round(np.linalg.det(R)) == 1:
+                out.append(R)
+    return out
+
+
+def reorient(mesh: Mesh, seed: int = 2312) -> Mesh:
+    """The same mesh with every element's local frame replaced by a seeded
+    random rotation of its reference element: the corner list and the face
+    tags are relabelled, the physical element is unchanged, so neighbouring
+    faces meet in every relative orientation.  Straight-sided (q = 1) meshes
+    only."""
+    if mesh.geo_nodes is not None:
+        raise ValueError("reorient: straight-sided meshes only")
+    dim = mesh.dim
+    rots = _rotations(dim)
+    rng = np.random.default_rng(seed)
+    pick = rng.integers(0, len(rots), size=mesh.n_elem)
+    corner_pos = np.array([[2 * ((c >> a) & 1) - 1 for a in range(dim)] for c in range(1 << dim)])
+
+    def corner_index(y):
+        return int(sum(((int(y[a]) + 1) // 2) << a for a in range(dim)))
+
+    def face_index(normal):
+        k = int(np.nonzero(normal)[0][0])
+        return 2 * k + (1 if normal[k] > 0 else 0)
+
+    ev = np.empty_like(mesh.elem_vert)
+    ft = np.empty_like(mesh.face_tag)
+    for e in range(mesh.n_elem):
+        R = rots[pick[e]]
+        for c in range(1 << dim):
+            ev[e, c] = mesh.elem_vert[e, corner_index(R.T @ corner_pos[c])]
+        for f in range(2 * dim):
+            nrm = np.zeros(dim, dtype=np.int64)
+            nrm[f // 2] = 1 if f % 2 else -1
+            ft[e, f] = mesh.face_tag[e, face_index(R.T @ nrm)]
+    return Mesh(mesh.dim, mesh.xyz, ev, ft, mesh.periodic_shift, 1, None, dict(mesh.info))
+
+
+def element_centroids(mesh: Mesh) -> np.ndarray:
+    return mesh.node_coords().mean(axis=1)
+
+
+def checker_degrees(mesh: Mesh, degrees=(2, 3), seed: int | None = None) -> np.ndarray:
+    """Per-element degree: a seeded random choice among ``degrees`` (or, with
+    seed None, alternating along the element numbering), so that most faces
+    join elements of different degree."""
+    if seed is None:
+        return np.asarray(degrees, dtype=np.int32)[np.arange(mesh.n_elem) % len(degrees)]
+    rng = np.random.default_rng(seed)
+    return np.asarray(degrees, dtype=np.int32)[rng.integers(0, len(degrees), size=mesh.n_elem)]
+
+
+def sponge_degrees(mesh: Mesh, centre, radii, degrees) -> np.ndarray:
+    """Per-element degree by distance of the element centroid from
+    ``centre``: degrees[0] inside radii[0], degrees[i] between radii[i-1]
+    and radii[i], the last degree beyond (the lower-degree far-field
+    sponge layers of the paper's airfoil grids, Sec. 5.1)."""
+    r = np.linalg.norm(element_centroids(mesh)[:, :len(centre)] - np.asarray(centre, float), axis=1)
+    out = np.full(mesh.n_elem, degrees[-1], dtype=np.int32)
+    for rad, deg in reversed(list(zip(radii, degrees))):
+        out[r < rad] = deg
+    return out
