@@ -50,10 +50,12 @@ class Workload:
     """One configuration: dimension, degree, physics, seeded meshes, start."""
 
     def __init__(self, name, dim, p, re, mach, candidates, desc, make, v_inf, inflow_delta=0.0,
-                 start="wall_damped"):
+                 start="wall_damped", degrees=None):
         self.name, self.dim, self.p, self.re, self.mach = name, dim, p, re, mach
         self.candidates, self.desc, self.make = candidates, desc, make
         self.v_inf, self.inflow_delta, self.start = v_inf, inflow_delta, start
+        # degrees(mesh) -> degree of every element (p is then the highest)
+        self.degrees = degrees
         n = p + 1
         self.nsp = n ** dim
         self.nfp = 2 * dim * n ** (dim - 1)
@@ -62,6 +64,16 @@ class Workload:
 
     def physics(self):
         return dict(mu=1.0 / self.re, p_inf=1.0 / (GAMMA * self.mach ** 2), v_inf=self.v_inf)
+
+    def elem_degrees(self, mesh):
+        if self.degrees is None:
+            return np.full(mesh.n_elem, self.p, dtype=np.int32)
+        return self.degrees(mesh)
+
+    def sizes(self, p):
+        """(solution points, flux points) of one element of degree p."""
+        n = p + 1
+        return n ** self.dim, 2 * self.dim * n ** (self.dim - 1)
 
 
 def _airfoils(rank, n):
@@ -84,6 +96,13 @@ def _tandem_draws(rank):
     return out
 
 
+def _sponge(mesh):
+    """Variable degree of the airfoil grids (Sec. 5.1): p = 3 within 4 chords
+    of the mid-chord, p = 2 out to 8 chords, p = 1 in the outer far field."""
+    from synth import meshes as M
+    return M.sponge_degrees(mesh, (0.5, 0.0), (4.0, 8.0), (3, 2, 1))
+
+
 def _cavity(rank, n):
     from synth import meshes as M
     return [M.cavity_mesh(32000)]
@@ -98,6 +117,11 @@ WORKLOADS = {
     "airfoil": Workload("airfoil", 2, 3, 23000.0, 0.2, 32,
                         "32 NACA 4-digit O-meshes (8k-40k curved quads, seed 2312), p=3, NS BR2, "
                         "Re_c=23000, M=0.2, LSRK45, one probe per candidate", _airfoils, (1.0, 0.0)),
+    "airfoil_sponge": Workload("airfoil_sponge", 2, 3, 23000.0, 0.2, 32,
+                               "32 NACA 4-digit O-meshes (8k-40k curved quads, seed 2312) with a "
+                               "variable degree: p=3 within 4c, p=2 to 8c, p=1 beyond (mortar "
+                               "coupling), NS BR2, Re_c=23000, M=0.2, LSRK45, one probe per candidate",
+                               _airfoils, (1.0, 0.0), degrees=_sponge),
     "tandem": Workload("tandem", 3, 4, 1000.0, 0.2, 16,
                        "16 tandem-cylinder candidates (60k-150k curved hexes, 16 spanwise layers, "
                        "seed 2312), p=4, NS BR2, Re=1000, M=0.2, LSRK45, 16 spanwise probes each",
@@ -200,7 +224,11 @@ def oracle_phys():
 
 def oracle_sample_rate(mesh, n_sample, n_steps, dt):
     """Time the FP64 oracle's LSRK45 stages restricted to a sample of
-    elements of one candidate: returns (updates/s, seconds, sample text)."""
+    elements of one candidate: returns (updates/s, seconds, sample text).
+    A variable-degree workload times the variable-degree oracle on the whole
+    candidate (it evaluates no element subsets)."""
+    if W.degrees is not None:
+        return oracle_varp_rate(mesh, max(1, n_steps // 10), dt)
     from oracle.fr import FRDiscretisation
     disc = FRDiscretisation(mesh, W.p, oracle_phys())
     U = initial_state(disc.sol_coords(), 0, mesh)
@@ -222,15 +250,37 @@ def oracle_sample_rate(mesh, n_sample, n_steps, dt):
                             f"(their 2-ring neighbourhood evaluated), {n_steps} LSRK45 steps")
 
 
+def oracle_varp_rate(mesh, n_steps, dt):
+    from oracle.fr_var import VarFRDiscretisation
+    from oracle.timestep import lsrk45_step
+    disc = VarFRDiscretisation(mesh, W.elem_degrees(mesh), oracle_phys())
+    U = initial_state(disc.sol_coords(), 0, mesh)
+    t0 = time.perf_counter()
+    for _ in range(n_steps):
+        U = lsrk45_step(disc.residual, U, dt)
+    sec = time.perf_counter() - t0
+    upd = disc.n_sp * STAGES * n_steps
+    return upd / sec, sec, (f"all {mesh.n_elem} elements ({disc.n_sp} solution points) of one "
+                            f"candidate, {n_steps} LSRK45 steps of the variable-degree oracle")
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     meshes = make_meshes(0)
     dt = cfl_dt(meshes)
+    if W.degrees is None:
+        m0, steps = meshes[0], args.steps
+    else:
+        # variable degree: whole-candidate oracle steps of the smallest
+        # candidate, at most 3 of them (a few seconds each)
+        m0 = min(meshes, key=lambda m: m.n_elem)
+        args.steps = steps = max(1, min(args.steps, 3))
     # warm-up steps are untimed, then K timed steps of the bounded sample
-    oracle_sample_rate(meshes[0], 64, max(args.warmup, 1), dt)
-    rate, sec, sample = oracle_sample_rate(meshes[0], 64, args.steps, dt)
+    if W.degrees is None:
+        oracle_sample_rate(m0, 64, max(args.warmup, 1), dt)
+    rate, sec, sample = oracle_sample_rate(m0, 64, steps * (10 if W.degrees is not None else 1), dt)
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -295,13 +345,14 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def algorithmic_bytes(E, s, kind):
+def algorithmic_bytes(E, s, kind, p=None):
     """Compulsory DRAM bytes of one launch (the kernel's design, per element):
     flux: state read+write, RK register write (+read in 4 of 5 stages),
     metrics, normals, partner indices, the partner's face state, own and
     partner viscous normal flux, new face state; gradient: state, metrics,
     normals, partner indices, partner face state, viscous normal flux."""
-    NSP, NFP, V, MS, D = W.nsp, W.nfp, W.V, W.MS, W.dim
+    NSP, NFP = W.sizes(W.p if p is None else p)
+    V, MS, D = W.V, W.MS, W.dim
     if kind == "flux":
         per = (NSP * V * s * (3 + 0.8) + NSP * MS * s + NFP * D * s + NFP * 4 + NFP * V * s
                + 2 * NFP * V * s + NFP * V * s)
@@ -317,6 +368,8 @@ def sampled_parity(fr, meshes, fms, sol, n_sample=48):
     from oracle.fr import FRDiscretisation
     out = []
     eps = 2.0 ** -24
+    if W.degrees is not None:
+        return sampled_parity_varp(meshes, fms, sol)
     for inst in sorted({0, len(fms) // 2, len(fms) - 1}):
         disc = FRDiscretisation(meshes[inst], W.p, oracle_phys())
         u = initial_state(fms[inst].sol_coords(), inst, meshes[inst])
@@ -337,6 +390,29 @@ def sampled_parity(fr, meshes, fms, sol, n_sample=48):
     return out
 
 
+def sampled_parity_varp(meshes, fms, sol):
+    """Variable degree: the whole residual of the smallest candidate and of
+    the last one (FP32 library vs the variable-degree oracle)."""
+    from oracle.fr_var import VarFRDiscretisation
+    eps = 2.0 ** -24
+    out = []
+    small = min(range(len(fms)), key=lambda i: meshes[i].n_elem)
+    for inst in sorted({small, len(fms) - 1}):
+        disc = VarFRDiscretisation(meshes[inst], W.elem_degrees(meshes[inst]), oracle_phys())
+        u = initial_state(fms[inst].sol_coords(), inst, meshes[inst])
+        sol.set_state(inst, u)
+        Rg = sol.residual(inst)
+        u32 = u.astype(np.float32).astype(np.float64)
+        R32, mag = disc.residual(u32, magnitude=True)
+        R64 = disc.residual(u)
+        out.append({"inst": inst, "elements": int(meshes[inst].n_elem), "degrees": "per element",
+                    "rel_l2_vs_oracle_fp32_input": float(np.linalg.norm(Rg - R32) / np.linalg.norm(R32)),
+                    "bound": float(16 * eps * np.linalg.norm(mag) / np.linalg.norm(R32)),
+                    "rel_l2_vs_oracle_exact_input": float(np.linalg.norm(Rg - R64) / np.linalg.norm(R64)),
+                    "pointwise_within_bound": bool(np.all(np.abs(Rg - R32) <= 16 * eps * mag))})
+    return out
+
+
 def run_gpu(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -349,7 +425,8 @@ def run_gpu(args):
     if world == 1 and not args.no_cpu_baseline:
         # the oracle runs before the first CUDA call of this process
         # about 10-30 s of oracle work on one host core
-        rate, sec, sample = oracle_sample_rate(meshes[0], 256, 30, dt)
+        m_cpu = min(meshes, key=lambda m: m.n_elem) if W.degrees is not None else meshes[0]
+        rate, sec, sample = oracle_sample_rate(m_cpu, 256, 30, dt)
         cpu_base = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                     "seconds": sec}
     torch.cuda.set_device(local)
@@ -362,8 +439,10 @@ def run_gpu(args):
                   inflow_delta=W.inflow_delta, inflow_ywall=0.0, dt=dt, viscous=True, rk=fr.FR_LSRK45)
     cfg32 = fr.make_config(W.dim, precision=fr.FR_FP32, **common)
     cfg64 = fr.make_config(W.dim, precision=fr.FR_FP64, **common)
-    fms = [fr.Mesh(m, W.p) for m in meshes]
+    fms = [fr.Mesh(m, W.p if W.degrees is None else W.elem_degrees(m)) for m in meshes]
     E = sum(m.n_elem for m in fms)
+    NSPT = sum(m.n_sp for m in fms)                   # solution points of the poll
+    by_p = np.bincount(np.concatenate([m.elem_p for m in fms]), minlength=5)
     sol = fr.Solver(fms, cfg32)
     states = [initial_state(m.sol_coords(), i, meshes[i]) for i, m in enumerate(fms)]
     parity = None
@@ -391,8 +470,8 @@ def run_gpu(args):
     clocks = clk.stop()
     ms = e0.elapsed_time(e1)
     launches = sol.last_launch_count()
-    ms, E_all = combine_ranks(dist, ms, E, device="cuda")
-    upd_all = E_all * W.nsp * STAGES * args.steps
+    ms, NSPT_all = combine_ranks(dist, ms, NSPT, device="cuda")
+    upd_all = NSPT_all * STAGES * args.steps
     value = upd_all / (ms / 1e3)
     # observer results of the timed window
     oaspl = [sol.oaspl(ids, p_ref=2e-5, p_scale=101325.0 / ph["p_inf"], mean_mode=0)
@@ -400,13 +479,16 @@ def run_gpu(args):
     forces = [list(sol.forces(i)) for i in range(min(2, len(fms)))]
     tot, bad = sol.integral(0)
     # per-kernel times (CUDA events around each launch, no graph)
-    kms, kcnt = sol.profile_steps(3)
+    n_prof = 3
+    kms, kcnt = sol.profile_steps(n_prof)
     kinds = ["flux", "grad", "probe", "force", "other"]
     share = {kinds[k]: float(kms[k] * kcnt[k]) for k in range(5)}
     dom = max(("flux", "grad"), key=lambda k: share[k])
     kdx = kinds.index(dom)
-    alg = algorithmic_bytes(E, 4, dom)
-    achieved = alg / (kms[kdx] / 1e3) / 1e9
+    # one stage's launches of the dominant kind (one per degree group)
+    alg = sum(algorithmic_bytes(int(by_p[q]), 4, dom, q) for q in range(1, 5) if by_p[q])
+    stage_kernel_ms = float(kms[kdx] * kcnt[kdx]) / (n_prof * STAGES)
+    achieved = alg / (stage_kernel_ms / 1e3) / 1e9
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -418,9 +500,13 @@ def run_gpu(args):
     rec = NCU_TRAFFIC.get(kernel_source_hash())
     if rec and W.name == rec.get("workload", "airfoil"):
         traffic = rec[f"{dom}_bytes_per_elem"] * E
-    roof = {"bound": "hbm", "kernel": f"k_{dom}<{W.dim},{W.p + 1},float>", "achieved": achieved, "peak": peak,
+    groups = [q for q in range(1, 5) if by_p[q]]
+    kname = (f"k_{dom}<{W.dim},{W.p + 1},float>" if len(groups) == 1 else
+             f"k_{dom}<{W.dim},N,float> over the degree groups N = {[q + 1 for q in groups]}, "
+             "one launch each per stage")
+    roof = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak,
             "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
-            "algorithmic_bytes_per_launch": alg, "launch_ms": float(kms[kdx]),
+            "algorithmic_bytes_per_launch": alg, "launch_ms": stage_kernel_ms,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks else "fallback 6800",
             "stage_ms": float(kms[0] + kms[1]),
             "kernel_ms": {kinds[k]: float(kms[k]) for k in range(5)}}
@@ -448,7 +534,7 @@ def run_gpu(args):
             outs[i][...] = sol.get_state(i)
     sol.synchronize()
     e2e_sec = time.perf_counter() - t0
-    e2e_val = E * W.nsp * STAGES * n_e2e / e2e_sec * (E_all / E)
+    e2e_val = NSPT * STAGES * n_e2e / e2e_sec * (NSPT_all / NSPT)
     state_bytes = sum(u.nbytes for u in states)
     del sol
     torch.cuda.empty_cache()
@@ -468,7 +554,7 @@ def run_gpu(args):
         b.synchronize()
         t64 += a.elapsed_time(b)
         del s64
-    fp64_val = E * W.nsp * STAGES * n64 / (t64 / 1e3)
+    fp64_val = NSPT * STAGES * n64 / (t64 / 1e3)
 
     if dist:
         dist.barrier()
@@ -478,9 +564,10 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_text(),
                            "candidates_per_gpu": len(fms), "elements_per_gpu": E,
-                           "sol_pts_per_gpu": E * W.nsp, "p": W.p, "dt": dt,
+                           "sol_pts_per_gpu": NSPT, "p": W.p, "dt": dt,
+                           "elements_by_degree": {str(q): int(by_p[q]) for q in range(1, 5) if by_p[q]},
                            "l2": "inputs larger than L2 (FP32 working set %.2f GB > 129 MB), no flush"
-                                 % (sol_bytes(E) / 1e9)},
+                                 % (sum(sol_bytes(int(by_p[q]), q) for q in range(1, 5)) / 1e9)},
                 "roofline": roof,
                 "cpu_baseline": cpu_base,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
@@ -502,9 +589,10 @@ def run_gpu(args):
     return 0
 
 
-def sol_bytes(E):
+def sol_bytes(E, p=None):
     s = 4
-    NSP, NFP, V = W.nsp, W.nfp, W.V
+    NSP, NFP = W.sizes(W.p if p is None else p)
+    V = W.V
     return E * (NSP * V * s * 4 + NFP * V * s * 3 + NSP * W.MS * s + NFP * W.dim * s + NFP * 4)
 
 

@@ -22,7 +22,9 @@
  *  - work is issued on the caller's CUDA stream; calls that return host data
  *    synchronise that stream before returning;
  *  - state layout on the host is [element][solution point][variable] in
- *    FP64, variables [rho, rho*v_x, rho*v_y(, rho*v_z), rho*E];
+ *    FP64, variables [rho, rho*v_x, rho*v_y(, rho*v_z), rho*E]; on a mesh
+ *    whose degree varies (fr_mesh_create_varp) each element contributes its
+ *    own (p_e+1)^dim points, element after element;
  *  - solution points are the tensor product of the p+1 Gauss-Legendre
  *    points, xi index fastest; element corners in tensor order (xi fastest);
  *    faces numbered -xi, +xi, -eta, +eta(, -zeta, +zeta).
@@ -41,7 +43,7 @@ typedef int fr_status;
 #define FR_OK 0
 #define FR_ERR_INVALID_ARG 1   /* null pointer, out-of-range index or size */
 #define FR_ERR_MESH 2          /* unmatched face, non-positive Jacobian, ... */
-#define FR_ERR_UNSUPPORTED 3   /* p outside 1..4, mixed dims/orders in a batch */
+#define FR_ERR_UNSUPPORTED 3   /* p outside 1..4, mixed dimensions in a batch */
 #define FR_ERR_CUDA 4          /* a CUDA runtime call failed */
 #define FR_ERR_NONFINITE 5     /* NaN/Inf found in the state */
 #define FR_ERR_TIMEOUT 6       /* a bounded device wait gave up */
@@ -124,16 +126,40 @@ fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_vert, const do
                          const double *geo_nodes, const int32_t *face_tag, int n_shift,
                          const double *periodic_shift);
 void fr_mesh_destroy(fr_mesh *mesh);
-/* Number of elements, solution points per element and flux points per element. */
+/* A mesh whose polynomial degree is chosen per element (Sec. 5.1: the
+ * airfoil grids run with a variable solution degree, P0-P3 / P0-P4, lower
+ * degrees in the outer zones to damp waves before the boundaries).  Same
+ * arguments as fr_mesh_create with ``elem_p`` (n_elem degrees, 1..4) in place
+ * of p.  The paper does not say how a face joining two degrees is treated;
+ * this library uses the conservative mortar coupling: the mortar is the
+ * higher side's set of flux points, the lower side's face trace is evaluated
+ * there, the higher side's trace reaches the lower side as its L2 projection
+ * onto the lower degree, the common normal flux is formed on the mortar and
+ * the lower side receives minus its projection (which keeps the face
+ * integral); on such a face the lower-degree side is LDG's left side.
+ * Errors: as fr_mesh_create; FR_ERR_MESH also when the corners of a face
+ * joining two degrees do not coincide. */
+fr_status fr_mesh_create_varp(fr_mesh **out, int dim, const int32_t *elem_p, int64_t n_vert,
+                              const double *xyz, int64_t n_elem, const int64_t *elem_vert,
+                              int geo_order, const double *geo_nodes, const int32_t *face_tag,
+                              int n_shift, const double *periodic_shift);
+/* Number of elements, solution points per element and flux points per
+ * element (nsp = nfp = 0 when the degree varies between elements). */
 fr_status fr_mesh_info(const fr_mesh *mesh, int64_t *n_elem, int *nsp, int *nfp);
-/* Physical coordinates of all solution points, n_elem * nsp * dim FP64. */
+/* Degree of every element (elem_p: n_elem int32, may be NULL) and the total
+ * number of solution points of the mesh (may be NULL). */
+fr_status fr_mesh_degrees(const fr_mesh *mesh, int32_t *elem_p, int64_t *n_sol_points);
+/* Physical coordinates of all solution points, element after element, FP64
+ * (n_sol_points * dim values). */
 fr_status fr_mesh_sol_coords(const fr_mesh *mesh, double *xyz);
 
 /* Workspace (device bytes) a solver over these meshes needs; 0 on error. */
 size_t fr_workspace_bytes(fr_mesh *const *meshes, int n_inst, const fr_config *cfg);
 
-/* Create a batch solver: the n_inst meshes (same dim and p) are advanced
- * together, one element tile table over all of them.  ``workspace`` is a
+/* Create a batch solver: the n_inst meshes (same dim; degrees may differ
+ * between and within meshes) are advanced together: the elements of each
+ * degree form one group, one element tile table over all instances, and the
+ * faces joining two degrees are coupled by mortar kernels.  ``workspace`` is a
  * device buffer of ``ws_bytes`` >= fr_workspace_bytes() aligned to 256 bytes,
  * owned by the caller and kept alive until fr_solver_destroy; ``stream`` is a
  * cudaStream_t (NULL: legacy default stream).  Meshes may be destroyed after

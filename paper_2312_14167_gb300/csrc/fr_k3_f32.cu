@@ -34,4 +34,8 @@ cudaError_t prepare_3_f32(int N, bool visc) {
     }
 }
 
+cudaError_t mortar_3_f32(const MArgs<float> &a, cudaStream_t s) {
+    return launch_mortar<3, float>(a, s);
+}
+
 }  // namespace frk

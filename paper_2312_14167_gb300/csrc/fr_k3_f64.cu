@@ -34,4 +34,8 @@ cudaError_t prepare_3_f64(int N, bool visc) {
     }
 }
 
+cudaError_t mortar_3_f64(const MArgs<double> &a, cudaStream_t s) {
+    return launch_mortar<3, double>(a, s);
+}
+
 }  // namespace frk

@@ -58,8 +58,8 @@ enum Mode : int {
 enum BcTag : int { BC_WALL = 2, BC_FARFIELD = 3, BC_INFLOW = 4, BC_OUTFLOW = 5 };
 
 struct ProbeDesc {
-    int64_t elem;      // global element index
-    int32_t inst, pad;
+    int64_t elem;      // element index within its degree group
+    int32_t inst, group;
     double w[125];     // tensor Lagrange weights of the solution points
 };
 
@@ -83,10 +83,16 @@ struct KArgs {
     real *FV;
     const real *MET;           // [E][NSP][D*D+1]: S[k][j] = J dxi_k/dx_j, then 1/J
     const real *NRM;           // [E][NFP][D] outward normal * |dS|
-    const int32_t *PART;       // [E][NFP] partner flux point, or -1-b (boundary b)
+    const int32_t *PART;       // [E][NFP] partner flux point, or -1-b (boundary b); an index
+                               // >= fp_real is an outbox row of a mortar face (faces joining
+                               // elements of different degree)
     const int32_t *BTAG;       // [nb] boundary tag
     const real *BVREF;         // [nb][D] reference velocity at boundary points
     const int32_t *EINST;      // [E] instance of each element
+    int64_t fp_real;           // E * NFP: rows above are mortar outbox rows
+    int64_t fp_lo_end;         // outbox rows below this one belong to the lower-degree side
+    const real *MFLUX;         // [outbox rows][V] common normal flux of mortar points
+    int group;                 // degree group of the launch (probe filter)
     // physics
     real gamma, prandtl, mu, eta, rho_inf, p_inf;
     int flux;                  // 0 Rusanov, 1 Roe
@@ -120,6 +126,14 @@ struct KArgs {
 // shared-memory regions are padded to multiples of 4 values (16 B in FP32,
 // 32 B in FP64) so that every region can take 128-bit accesses
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) / 4 * 4; }
+
+// LDG's one-sided switch: is the own side of flux point gf (partner index
+// pt >= 0) the left side?  Conforming faces: the smaller (element, point)
+// index; mortar faces: the lower-degree side.
+template <typename real>
+__device__ __forceinline__ bool ldg_left(const KArgs<real> &a, int64_t gf, int32_t pt) {
+    return pt < a.fp_real ? gf < pt : pt < a.fp_lo_end;
+}
 
 template <int D, int N>
 struct Geo {
@@ -632,7 +646,7 @@ k_grad(const KArgs<real> a) {
         if (pt[it] >= 0) {
             // LDG: one-sided common solution, left side = smaller point index
             const int64_t gf = elem_of<real>(a.elist, e0, j) * NFP + f;
-            const real bs = a.ldg ? (gf < pt[it] ? a.ldg_beta : -a.ldg_beta) : real(0);
+            const real bs = a.ldg ? (ldg_left(a, gf, pt[it]) ? a.ldg_beta : -a.ldg_beta) : real(0);
 #pragma unroll
             for (int v = 0; v < V; ++v) {
                 uc[v] = (real(0.5) + bs) * uL[v] + (real(0.5) - bs) * uR[it][v];
@@ -817,14 +831,14 @@ k_flux(const KArgs<real> a) {
     }
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        if (pt[it] >= 0) {
+        if (pt[it] >= 0 && pt[it] < a.fp_real) {
             if (VISC) {
                 // common viscous normal flux without the LDG penalty:
                 // BR2 1/2 (own - partner); LDG (1/2 - s beta) own - (1/2 + s beta) partner
                 real fp[V];
                 ldg_v<V>(a.FV + (int64_t)pt[it] * V, fp);
                 const int64_t gf = (e0 + (tid + it * G::THREADS) / NFP) * NFP + (tid + it * G::THREADS) % NFP;
-                const real bs = a.ldg ? (gf < pt[it] ? a.ldg_beta : -a.ldg_beta) : real(0);
+                const real bs = a.ldg ? (ldg_left(a, gf, pt[it]) ? a.ldg_beta : -a.ldg_beta) : real(0);
 #pragma unroll
                 for (int v = 0; v < V; ++v) fv[it][v] = (real(0.5) - bs) * fv[it][v] - (real(0.5) + bs) * fp[v];
             }
@@ -866,17 +880,20 @@ k_flux(const KArgs<real> a) {
             for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d];
             bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, uRp, ub);
         }
+        // mortar points take the common flux formed on the mortar (k_mortar)
+        const bool mort = pt[it] >= a.fp_real;
         real Fs[V];
-        common_inviscid<D>(a.flux, uL, uRp, nr[it], a.gamma, Fs);
+        if (mort) ld_v<V>(a.MFLUX + (int64_t)(pt[it] - a.fp_real) * V, Fs);
+        else common_inviscid<D>(a.flux, uL, uRp, nr[it], a.gamma, Fs);
         if (VISC) {
             real dd[V];
             if (pt[it] >= 0) {
                 const int64_t gf = (e0 + j) * NFP + f;
-                const real bs = a.ldg ? (gf < pt[it] ? a.ldg_beta : -a.ldg_beta) : real(0);
+                const real bs = a.ldg ? (ldg_left(a, gf, pt[it]) ? a.ldg_beta : -a.ldg_beta) : real(0);
 #pragma unroll
                 for (int v = 0; v < V; ++v)
                     dd[v] = (real(0.5) + bs) * uL[v] + (real(0.5) - bs) * uRp[v] - uL[v];
-                if (a.ldg) {
+                if (a.ldg && !mort) {
                     real nn = 0;
 #pragma unroll
                     for (int d = 0; d < D; ++d) nn += nr[it][d] * nr[it][d];
@@ -888,8 +905,10 @@ k_flux(const KArgs<real> a) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) dd[v] = ub[v] - uL[v];
             }
+            if (!mort) {
 #pragma unroll
-            for (int v = 0; v < V; ++v) Fs[v] -= fv[it][v];
+                for (int v = 0; v < V; ++v) Fs[v] -= fv[it][v];
+            }
             st_v<V>(sD + (j * NFP + f) * V, dd);
         }
         st_v<V>(sC + (j * NFP + f) * V, Fs);
@@ -1107,6 +1126,7 @@ __global__ void k_probe(const KArgs<real> a) {
     const int pr = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     if (pr >= a.n_probe) return;
     const ProbeDesc &P = a.probes[pr];
+    if (P.group != a.group) return;
     double u[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) u[v] = 0.0;
@@ -1240,6 +1260,152 @@ __global__ void k_to_f64(const KArgs<real> a) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x)
         a.stage64_out[i] = (double)src[off + i];
+}
+
+// --------------------------------------------------------------------------
+// Mortar faces: faces joining elements of different degree (mortar element
+// coupling, conservative).  The mortar is the higher-degree side's set of
+// flux points.  Each side's element stores its own face trace in its outbox
+// rows (its partner index points there); one warp per face then
+//  * K_MORTAR pass 0 (after the traces are written): carries the lower
+//    side's trace to the higher side's points (T, exact evaluation of the
+//    face polynomial) and the higher side's trace to the lower side's points
+//    (P, L2 projection onto the lower degree), into each side's inbound rows;
+//  * K_MORTAR pass 1 (after the viscous normal fluxes, before k_flux): forms
+//    the common normal flux at the mortar points from the higher side's
+//    trace, the lower side's trace carried by T and, for viscous flow, both
+//    sides' own viscous normal fluxes (the lower one carried by T); the
+//    higher side takes it as it is, the lower side minus its projection P.
+//    On these faces the lower-degree side is LDG's left side.
+// --------------------------------------------------------------------------
+constexpr int kMaxGroups = 4;
+
+struct MortarFace {
+    int32_t glo, ghi;          // degree groups of the lower and higher side
+    int32_t nlo, nhi;          // flux points of the face on each side
+    int64_t lo_fp, hi_fp;      // first flux point of the face, per side (group index)
+    int64_t lo_box, hi_box;    // first outbox row of the face, per side (group index)
+    int64_t mat;               // offset of T [nhi][nlo] followed by P [nlo][nhi]
+};
+
+template <typename real>
+struct MArgs {
+    real *UF[kMaxGroups];          // face buffer of the pass, per group
+    const real *FV[kMaxGroups];    // own viscous normal flux, per group
+    const real *NRM[kMaxGroups];
+    real *MFLUX[kMaxGroups];
+    int64_t fp_real[kMaxGroups];
+    const MortarFace *faces;
+    int64_t n_faces;
+    const real *mats;
+    real gamma, ldg_beta, ldg_tau;
+    int flux, ldg, visc, pass;
+};
+
+template <int D, typename real>
+__global__ void __launch_bounds__(128) k_mortar(const MArgs<real> a) {
+    constexpr int V = D + 2;
+    __shared__ real sF[4][32 * V];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t m = (int64_t)blockIdx.x * 4 + wid;
+    if (m >= a.n_faces) return;            // per warp: the whole warp leaves
+    const MortarFace F = a.faces[m];
+    const real *T = a.mats + F.mat;
+    const real *P = T + F.nhi * F.nlo;
+    if (a.pass == 0) {
+        if (lane < F.nhi) {
+            real acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = 0;
+            for (int i = 0; i < F.nlo; ++i) {
+                const real t = T[lane * F.nlo + i];
+                const real *src = a.UF[F.glo] + (F.lo_box + i) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += t * src[v];
+            }
+            real *dst = a.UF[F.ghi] + (F.hi_fp + lane) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) dst[v] = acc[v];
+        }
+        if (lane < F.nlo) {
+            real acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] = 0;
+            for (int j = 0; j < F.nhi; ++j) {
+                const real w = P[lane * F.nhi + j];
+                const real *src = a.UF[F.ghi] + (F.hi_box + j) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) acc[v] += w * src[v];
+            }
+            real *dst = a.UF[F.glo] + (F.lo_fp + lane) * V;
+#pragma unroll
+            for (int v = 0; v < V; ++v) dst[v] = acc[v];
+        }
+        return;
+    }
+    real *sf = sF[wid];
+    if (lane < F.nhi) {
+        const int64_t hf = F.hi_fp + lane;
+        real uL[V], uR[V], nr[D], Fs[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            uL[v] = a.UF[F.ghi][(F.hi_box + lane) * V + v];   // own trace (outbox)
+            uR[v] = a.UF[F.ghi][hf * V + v];                  // lower trace carried by T
+        }
+#pragma unroll
+        for (int d = 0; d < D; ++d) nr[d] = a.NRM[F.ghi][hf * D + d];
+        common_inviscid<D>(a.flux, uL, uR, nr, a.gamma, Fs);
+        if (a.visc) {
+            real fl[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) fl[v] = 0;
+            for (int i = 0; i < F.nlo; ++i) {
+                const real t = T[lane * F.nlo + i];
+                const real *src = a.FV[F.glo] + (F.lo_fp + i) * V;
+#pragma unroll
+                for (int v = 0; v < V; ++v) fl[v] += t * src[v];
+            }
+            const real *fh = a.FV[F.ghi] + hf * V;
+            const real bs = a.ldg ? -a.ldg_beta : real(0);   // the higher side is the right side
+            if (a.ldg) {
+                real nn = 0;
+#pragma unroll
+                for (int d = 0; d < D; ++d) nn += nr[d] * nr[d];
+                const real pen = a.ldg_tau * sqrt(nn);
+#pragma unroll
+                for (int v = 0; v < V; ++v) Fs[v] += pen * (uL[v] - uR[v]);
+            }
+#pragma unroll
+            for (int v = 0; v < V; ++v) Fs[v] -= (real(0.5) - bs) * fh[v] - (real(0.5) + bs) * fl[v];
+        }
+        real *dst = a.MFLUX[F.ghi] + (F.hi_box - a.fp_real[F.ghi] + lane) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            dst[v] = Fs[v];
+            sf[lane * V + v] = Fs[v];
+        }
+    }
+    __syncwarp();
+    if (lane < F.nlo) {
+        real acc[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) acc[v] = 0;
+        for (int j = 0; j < F.nhi; ++j) {
+            const real w = P[lane * F.nhi + j];
+#pragma unroll
+            for (int v = 0; v < V; ++v) acc[v] += w * sf[j * V + v];
+        }
+        real *dst = a.MFLUX[F.glo] + (F.lo_box - a.fp_real[F.glo] + lane) * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) dst[v] = -acc[v];
+    }
+}
+
+template <int D, typename real>
+cudaError_t launch_mortar(const MArgs<real> &a, cudaStream_t st) {
+    if (a.n_faces <= 0) return cudaSuccess;
+    k_mortar<D, real><<<(unsigned)((a.n_faces + 3) / 4), 128, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 // --------------------------------------------------------------------------

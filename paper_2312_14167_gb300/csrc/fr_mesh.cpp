@@ -323,47 +323,115 @@ bool mesh_locate(const fr_mesh &m, const double *x, int64_t *elem, double *xi) {
 
 using fr::RefElem;
 
-extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_vert,
-                                    const double *xyz, int64_t n_elem, const int64_t *elem_vert,
-                                    int geo_order, const double *geo_nodes,
-                                    const int32_t *face_tag, int n_shift,
-                                    const double *periodic_shift) {
-    if (!out || !xyz || !elem_vert || !face_tag || n_elem <= 0 || n_vert <= 0 ||
-        (dim != 2 && dim != 3) || geo_order < 1 || geo_order > 7 ||
-        (n_shift > 0 && !periodic_shift) || n_shift < 0) {
-        fr::set_error("fr_mesh_create: invalid argument");
-        return FR_ERR_INVALID_ARG;
+namespace fr {
+namespace {
+
+// One connected face seen from one side: corners of (e, fc) + sh lie on those
+// of (e2, fc2).  Global element indices.
+struct Pair { int64_t e; int fc; int64_t e2; int fc2; double sh[3]; };
+
+struct MeshInput {
+    int dim;
+    int64_t n_vert, n_elem;
+    const double *xyz;
+    const int64_t *elem_vert;
+    const int32_t *face_tag;
+    int n_shift;
+    const double *periodic_shift;
+    int64_t corner(int64_t e, int fc, int c) const {
+        const int nc = 1 << dim;
+        return dim == 2 ? elem_vert[e * nc + kQuadFaces[fc][c]] : elem_vert[e * nc + kHexFaces[fc][c]];
     }
-    if (p < 1 || p > 4) {
-        fr::set_error("fr_mesh_create: polynomial degree must be 1..4");
-        return FR_ERR_UNSUPPORTED;
-    }
-    *out = nullptr;
-    fr_mesh *m = new fr_mesh();
-    m->dim = dim; m->p = p; m->n_elem = n_elem;
-    RefElem &r = m->ref;
-    fr::build_ref(r, dim, p);
-    const int nc = 1 << dim;
-    for (int64_t i = 0; i < n_elem * nc; ++i)
-        if (elem_vert[i] < 0 || elem_vert[i] >= n_vert) {
-            delete m;
-            fr::set_error("fr_mesh_create: vertex index out of range");
-            return FR_ERR_INVALID_ARG;
+    int ncf() const { return dim == 2 ? 2 : 4; }
+};
+
+// Interior faces share their corner vertices; periodic faces are matched by
+// corner coordinates (rounded on a fine lattice) after adding or subtracting
+// one of the periodic shifts.
+fr_status find_face_pairs(const MeshInput &in, std::vector<Pair> &pairs) {
+    const int dim = in.dim, ncf = in.ncf();
+    std::unordered_map<Key4, std::vector<std::pair<int64_t, int>>, Key4Hash> by_ids;
+    by_ids.reserve((size_t)in.n_elem * dim * 2);
+    for (int64_t e = 0; e < in.n_elem; ++e)
+        for (int fc = 0; fc < 2 * dim; ++fc) {
+            const int32_t tg = in.face_tag[e * 2 * dim + fc];
+            if (tg < 0 || tg > 5) {
+                set_error("fr_mesh_create: unknown face tag");
+                return FR_ERR_INVALID_ARG;
+            }
+            if (tg != FR_TAG_INTERIOR) continue;
+            Key4 k{{-1, -1, -1, -1}};
+            for (int c = 0; c < ncf; ++c) k.v[c] = in.corner(e, fc, c);
+            std::sort(k.v.begin(), k.v.begin() + ncf);
+            by_ids[k].push_back({e, fc});
         }
-    // geometry nodes
-    int q = geo_nodes ? geo_order : 1;
-    m->q = q;
-    fr::MapEval me(dim, q);
-    m->nodes.resize((size_t)n_elem * me.nn * dim);
-    if (geo_nodes) {
-        std::memcpy(m->nodes.data(), geo_nodes, m->nodes.size() * sizeof(double));
-    } else {
-        for (int64_t e = 0; e < n_elem; ++e)
-            for (int c = 0; c < nc; ++c)
-                for (int j = 0; j < dim; ++j)
-                    m->nodes[((size_t)e * nc + c) * dim + j] = xyz[elem_vert[e * nc + c] * dim + j];
+    for (auto &kv : by_ids) {
+        if (kv.second.size() != 2) {
+            set_error("fr_mesh_create: interior face without exactly one partner");
+            return FR_ERR_MESH;
+        }
+        auto a = kv.second[0], b = kv.second[1];
+        pairs.push_back({a.first, a.second, b.first, b.second, {0, 0, 0}});
+        pairs.push_back({b.first, b.second, a.first, a.second, {0, 0, 0}});
     }
-    const int nsp = r.nsp, nfp = r.nfp, nfpf = r.nfpf;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int64_t v = 0; v < in.n_vert; ++v)
+        for (int j = 0; j < dim; ++j) {
+            lo[j] = std::min(lo[j], in.xyz[v * dim + j]);
+            hi[j] = std::max(hi[j], in.xyz[v * dim + j]);
+        }
+    double span = 0;
+    for (int j = 0; j < dim; ++j) span = std::max(span, hi[j] - lo[j]);
+    const double scale = 1e6 / std::max(span, 1e-300);
+    using CKey = std::vector<int64_t>;
+    std::map<CKey, std::pair<int64_t, int>> table;
+    auto ckey = [&](int64_t e, int fc, const double *sh) {
+        std::vector<std::array<int64_t, 3>> pts(ncf);
+        for (int c = 0; c < ncf; ++c) {
+            const int64_t v = in.corner(e, fc, c);
+            for (int j = 0; j < 3; ++j)
+                pts[c][j] = j < dim ? (int64_t)std::llround((in.xyz[v * dim + j] + (sh ? sh[j] : 0.0)) * scale) : 0;
+        }
+        std::sort(pts.begin(), pts.end());
+        CKey k;
+        for (auto &pt : pts) k.insert(k.end(), pt.begin(), pt.end());
+        return k;
+    };
+    std::vector<std::pair<int64_t, int>> per;
+    for (int64_t e = 0; e < in.n_elem; ++e)
+        for (int fc = 0; fc < 2 * dim; ++fc)
+            if (in.face_tag[e * 2 * dim + fc] == FR_TAG_PERIODIC) {
+                per.push_back({e, fc});
+                table[ckey(e, fc, nullptr)] = {e, fc};
+            }
+    for (auto &pf : per) {
+        bool found = false;
+        for (int s = 0; s < in.n_shift && !found; ++s)
+            for (int sg = 1; sg >= -1 && !found; sg -= 2) {
+                double sh[3] = {0, 0, 0};
+                for (int j = 0; j < dim; ++j) sh[j] = sg * in.periodic_shift[s * dim + j];
+                auto it = table.find(ckey(pf.first, pf.second, sh));
+                if (it != table.end() && it->second != pf) {
+                    pairs.push_back({pf.first, pf.second, it->second.first, it->second.second,
+                                     {sh[0], sh[1], sh[2]}});
+                    found = true;
+                }
+            }
+        if (!found) {
+            set_error("fr_mesh_create: periodic face without partner");
+            return FR_ERR_MESH;
+        }
+    }
+    return FR_OK;
+}
+
+// Metric terms, normals and point coordinates of a uniform-degree part whose
+// ref, q, n_elem and nodes are set.
+fr_status build_geometry(fr_mesh *m) {
+    const RefElem &r = m->ref;
+    const int dim = m->dim, nsp = r.nsp, nfp = r.nfp;
+    const int64_t n_elem = m->n_elem;
+    MapEval me(dim, m->q);
     m->x_sp.resize((size_t)n_elem * nsp * dim);
     m->S.resize((size_t)n_elem * nsp * dim * dim);
     m->J.resize((size_t)n_elem * nsp);
@@ -371,7 +439,7 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
     m->x_fp.resize((size_t)n_elem * nfp * dim);
     m->partner.assign((size_t)n_elem * nfp, -1);
     m->bctag.assign((size_t)n_elem * nfp, 0);
-    const fr::MapTable tsp(me, r.sp_xi, nsp), tfp(me, r.fp_xi, nfp);
+    const MapTable tsp(me, r.sp_xi, nsp), tfp(me, r.fp_xi, nfp);
     int64_t bad_elem = -1;
     // elements are independent: one host thread per chunk of elements
 #pragma omp parallel for schedule(static)
@@ -380,7 +448,7 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
         for (int s = 0; s < nsp; ++s) {
             double x[3], A[3][3], S[3][3];
             tsp.eval(nd, s, x, A);
-            const double J = fr::adjugate(dim, A, S);
+            const double J = adjugate(dim, A, S);
             if (!(J > 0.0)) {
 #pragma omp critical
                 {
@@ -396,7 +464,7 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
         for (int f = 0; f < nfp; ++f) {
             double x[3], A[3][3], S[3][3];
             tfp.eval(nd, f, x, A);
-            fr::adjugate(dim, A, S);
+            adjugate(dim, A, S);
             const int k = r.fp_dir[f];
             const double sg = r.fp_side[f] ? 1.0 : -1.0;
             for (int j = 0; j < dim; ++j) {
@@ -406,102 +474,34 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
         }
     }
     if (bad_elem >= 0) {
-        delete m;
-        fr::set_error("fr_mesh_create: non-positive Jacobian in element " + std::to_string(bad_elem));
+        set_error("fr_mesh_create: non-positive Jacobian in element " + std::to_string(bad_elem));
         return FR_ERR_MESH;
     }
+    return FR_OK;
+}
 
-    // ---- face connectivity -------------------------------------------------
-    auto corners = [&](int64_t e, int fc, int c) -> int64_t {
-        return dim == 2 ? elem_vert[e * nc + fr::kQuadFaces[fc][c]]
-                        : elem_vert[e * nc + fr::kHexFaces[fc][c]];
-    };
-    const int ncf = dim == 2 ? 2 : 4;
-    struct Pair { int64_t e; int fc; int64_t e2; int fc2; double sh[3]; };
-    std::vector<Pair> pairs;
-    std::unordered_map<fr::Key4, std::vector<std::pair<int64_t, int>>, fr::Key4Hash> by_ids;
-    by_ids.reserve((size_t)n_elem * dim * 2);
-    for (int64_t e = 0; e < n_elem; ++e)
-        for (int fc = 0; fc < 2 * dim; ++fc) {
-            const int32_t tg = face_tag[e * 2 * dim + fc];
-            if (tg < 0 || tg > 5) {
-                delete m;
-                fr::set_error("fr_mesh_create: unknown face tag");
-                return FR_ERR_INVALID_ARG;
+double face_hmin(const MeshInput &in, int64_t e, int fc) {
+    double hmin = 1e300;
+    const int ncf = in.ncf();
+    for (int i = 0; i < ncf; ++i)
+        for (int j = i + 1; j < ncf; ++j) {
+            double q2 = 0;
+            for (int c = 0; c < in.dim; ++c) {
+                const double dd = in.xyz[in.corner(e, fc, i) * in.dim + c] - in.xyz[in.corner(e, fc, j) * in.dim + c];
+                q2 += dd * dd;
             }
-            if (tg != FR_TAG_INTERIOR) continue;
-            fr::Key4 k{{-1, -1, -1, -1}};
-            for (int c = 0; c < ncf; ++c) k.v[c] = corners(e, fc, c);
-            std::sort(k.v.begin(), k.v.begin() + ncf);
-            by_ids[k].push_back({e, fc});
+            hmin = std::min(hmin, std::sqrt(q2));
         }
-    for (auto &kv : by_ids) {
-        if (kv.second.size() != 2) {
-            delete m;
-            fr::set_error("fr_mesh_create: interior face without exactly one partner");
-            return FR_ERR_MESH;
-        }
-        auto a = kv.second[0], b = kv.second[1];
-        pairs.push_back({a.first, a.second, b.first, b.second, {0, 0, 0}});
-        pairs.push_back({b.first, b.second, a.first, a.second, {0, 0, 0}});
-    }
-    // periodic faces: corner coordinates rounded on a fine lattice
-    {
-        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-        for (int64_t v = 0; v < n_vert; ++v)
-            for (int j = 0; j < dim; ++j) {
-                lo[j] = std::min(lo[j], xyz[v * dim + j]);
-                hi[j] = std::max(hi[j], xyz[v * dim + j]);
-            }
-        double span = 0;
-        for (int j = 0; j < dim; ++j) span = std::max(span, hi[j] - lo[j]);
-        const double scale = 1e6 / std::max(span, 1e-300);
-        using CKey = std::vector<int64_t>;
-        std::map<CKey, std::pair<int64_t, int>> table;
-        auto ckey = [&](int64_t e, int fc, const double *sh) {
-            std::vector<std::array<int64_t, 3>> pts(ncf);
-            for (int c = 0; c < ncf; ++c) {
-                const int64_t v = corners(e, fc, c);
-                for (int j = 0; j < 3; ++j)
-                    pts[c][j] = j < dim ? (int64_t)std::llround((xyz[v * dim + j] + (sh ? sh[j] : 0.0)) * scale) : 0;
-            }
-            std::sort(pts.begin(), pts.end());
-            CKey k;
-            for (auto &pt : pts) k.insert(k.end(), pt.begin(), pt.end());
-            return k;
-        };
-        std::vector<std::pair<int64_t, int>> per;
-        for (int64_t e = 0; e < n_elem; ++e)
-            for (int fc = 0; fc < 2 * dim; ++fc)
-                if (face_tag[e * 2 * dim + fc] == FR_TAG_PERIODIC) {
-                    per.push_back({e, fc});
-                    table[ckey(e, fc, nullptr)] = {e, fc};
-                }
-        for (auto &pf : per) {
-            bool found = false;
-            for (int s = 0; s < n_shift && !found; ++s)
-                for (int sg = 1; sg >= -1 && !found; sg -= 2) {
-                    double sh[3] = {0, 0, 0};
-                    for (int j = 0; j < dim; ++j) sh[j] = sg * periodic_shift[s * dim + j];
-                    auto it = table.find(ckey(pf.first, pf.second, sh));
-                    if (it != table.end() && it->second != pf) {
-                        pairs.push_back({pf.first, pf.second, it->second.first, it->second.second,
-                                         {sh[0], sh[1], sh[2]}});
-                        found = true;
-                    }
-                }
-            if (!found) {
-                delete m;
-                fr::set_error("fr_mesh_create: periodic face without partner");
-                return FR_ERR_MESH;
-            }
-        }
-    }
-    // Pair flux points by physical position.  A face's points form an n x n
-    // (3-D) or n (2-D) tensor grid, so the partner's numbering is one of the
-    // 8 (3-D) or 2 (2-D) orientations of that grid: choose it on three
-    // reference points, then check every point.
-    const int nn1 = r.n;
+    return hmin;
+}
+
+// Pair the flux points of two connected faces of one part by physical
+// position.  A face's points form an n x n (3-D) or n (2-D) tensor grid, so
+// the partner's numbering is one of the 8 (3-D) or 2 (2-D) orientations of
+// that grid: choose it on three reference points, then check every point.
+fr_status pair_points(fr_mesh *m, int64_t e, int fc, int64_t e2, int fc2, const double *sh, double hmin) {
+    const RefElem &r = m->ref;
+    const int dim = m->dim, nfp = r.nfp, nfpf = r.nfpf, nn1 = r.n;
     auto orient = [&](int o, int a) -> int {
         if (dim == 2) return o ? nn1 - 1 - a : a;
         int i = a % nn1, j = a / nn1;
@@ -512,69 +512,296 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
     };
     const int n_orient = dim == 2 ? 2 : 8;
     const int refs[3] = {0, nfpf - 1, dim == 2 ? nfpf / 2 : nn1 - 1};
-    for (const Pair &pr : pairs) {
-        const double *xa = &m->x_fp[((size_t)pr.e * nfp + pr.fc * nfpf) * dim];
-        const double *xb = &m->x_fp[((size_t)pr.e2 * nfp + pr.fc2 * nfpf) * dim];
-        auto d2 = [&](int a, int b) {
+    const double *xa = &m->x_fp[((size_t)e * nfp + fc * nfpf) * dim];
+    const double *xb = &m->x_fp[((size_t)e2 * nfp + fc2 * nfpf) * dim];
+    auto d2 = [&](int a, int b) {
+        double t = 0;
+        for (int c = 0; c < dim; ++c) {
+            const double dd = xa[a * dim + c] + sh[c] - xb[b * dim + c];
+            t += dd * dd;
+        }
+        return t;
+    };
+    int best = 0;
+    double bd = 1e300;
+    for (int o = 0; o < n_orient; ++o) {
+        double t = 0;
+        for (int rr = 0; rr < 3; ++rr) t += d2(refs[rr], orient(o, refs[rr]));
+        if (t < bd) { bd = t; best = o; }
+    }
+    for (int a = 0; a < nfpf; ++a) {
+        const int b = orient(best, a);
+        if (std::sqrt(d2(a, b)) > 1e-6 * hmin) {
+            set_error("fr_mesh_create: flux points of a connected face do not coincide");
+            return FR_ERR_MESH;
+        }
+        m->partner[(size_t)e * nfp + fc * nfpf + a] = e2 * nfp + fc2 * nfpf + b;
+    }
+    return FR_OK;
+}
+
+// Physical position of face coordinates c (d-1 values in [-1, 1]) on face fc
+// of an element with nodes nd.
+void face_point(const MapEval &me, const double *nd, int fc, const double *c, double *x) {
+    const int dim = me.dim, k = fc / 2;
+    double xi[3] = {0, 0, 0};
+    int t = 0;
+    for (int a = 0; a < dim; ++a) xi[a] = (a == k) ? ((fc & 1) ? 1.0 : -1.0) : c[t++];
+    double A[3][3];
+    me.eval(nd, xi, x, A);
+}
+
+void apply_orient(int dim, int o, const double *c, double *out) {
+    if (dim == 2) { out[0] = (o & 1) ? -c[0] : c[0]; return; }
+    double a = c[0], b = c[1];
+    if (o & 4) std::swap(a, b);
+    if (o & 1) a = -a;
+    if (o & 2) b = -b;
+    out[0] = a; out[1] = b;
+}
+
+// Orientation mapping the higher face's coordinates onto the lower face's,
+// from the corners' physical positions (lower + sh lies on higher).
+fr_status mortar_orient(const MeshInput &in, const MapEval &me, const std::vector<double> &nodes,
+                        const Pair &lo_hi, double hmin, int *orient) {
+    const int dim = in.dim, ncorner = dim == 2 ? 2 : 4, n_orient = dim == 2 ? 2 : 8;
+    const double *nl = &nodes[(size_t)lo_hi.e * me.nn * dim];
+    const double *nh = &nodes[(size_t)lo_hi.e2 * me.nn * dim];
+    int best = -1;
+    double bd = 1e300;
+    for (int o = 0; o < n_orient; ++o) {
+        double worst = 0;
+        for (int c = 0; c < ncorner; ++c) {
+            const double ch[2] = {(c & 1) ? 1.0 : -1.0, (c & 2) ? 1.0 : -1.0};
+            double cl[2], xh[3], xl[3];
+            apply_orient(dim, o, ch, cl);
+            face_point(me, nh, lo_hi.fc2, ch, xh);
+            face_point(me, nl, lo_hi.fc, cl, xl);
             double t = 0;
-            for (int c = 0; c < dim; ++c) {
-                const double dd = xa[a * dim + c] + pr.sh[c] - xb[b * dim + c];
+            for (int j = 0; j < dim; ++j) {
+                const double dd = xl[j] + lo_hi.sh[j] - xh[j];
                 t += dd * dd;
             }
-            return t;
-        };
-        double hmin = 1e300;
-        for (int i = 0; i < ncf; ++i)
-            for (int j = i + 1; j < ncf; ++j) {
-                double q2 = 0;
-                for (int c = 0; c < dim; ++c) {
-                    double dd = xyz[corners(pr.e, pr.fc, i) * dim + c] - xyz[corners(pr.e, pr.fc, j) * dim + c];
-                    q2 += dd * dd;
-                }
-                hmin = std::min(hmin, std::sqrt(q2));
-            }
-        int best = 0;
-        double bd = 1e300;
-        for (int o = 0; o < n_orient; ++o) {
-            double t = 0;
-            for (int rr = 0; rr < 3; ++rr) t += d2(refs[rr], orient(o, refs[rr]));
-            if (t < bd) { bd = t; best = o; }
+            worst = std::max(worst, t);
         }
-        for (int a = 0; a < nfpf; ++a) {
-            const int b = orient(best, a);
-            if (std::sqrt(d2(a, b)) > 1e-6 * hmin) {
-                delete m;
-                fr::set_error("fr_mesh_create: flux points of a connected face do not coincide");
-                return FR_ERR_MESH;
-            }
-            m->partner[(size_t)pr.e * nfp + pr.fc * nfpf + a] = pr.e2 * nfp + pr.fc2 * nfpf + b;
+        if (worst < bd) { bd = worst; best = o; }
+    }
+    if (best < 0 || std::sqrt(bd) > 1e-6 * hmin) {
+        set_error("fr_mesh_create: corners of a face joining two degrees do not coincide");
+        return FR_ERR_MESH;
+    }
+    *orient = best;
+    return FR_OK;
+}
+
+fr_status mesh_create_impl(fr_mesh **out, int dim, int p_uniform, const int32_t *elem_p, int64_t n_vert,
+                           const double *xyz, int64_t n_elem, const int64_t *elem_vert, int geo_order,
+                           const double *geo_nodes, const int32_t *face_tag, int n_shift,
+                           const double *periodic_shift) {
+    if (!out || !xyz || !elem_vert || !face_tag || n_elem <= 0 || n_vert <= 0 ||
+        (dim != 2 && dim != 3) || geo_order < 1 || geo_order > 7 ||
+        (n_shift > 0 && !periodic_shift) || n_shift < 0) {
+        set_error("fr_mesh_create: invalid argument");
+        return FR_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    std::vector<int32_t> degree((size_t)n_elem, p_uniform);
+    if (elem_p) std::copy(elem_p, elem_p + n_elem, degree.begin());
+    bool present[kMaxN] = {};
+    for (int64_t e = 0; e < n_elem; ++e) {
+        if (degree[e] < 1 || degree[e] > 4) {
+            set_error("fr_mesh_create: polynomial degree must be 1..4");
+            return FR_ERR_UNSUPPORTED;
+        }
+        present[degree[e]] = true;
+    }
+    const int nc = 1 << dim;
+    for (int64_t i = 0; i < n_elem * nc; ++i)
+        if (elem_vert[i] < 0 || elem_vert[i] >= n_vert) {
+            set_error("fr_mesh_create: vertex index out of range");
+            return FR_ERR_INVALID_ARG;
+        }
+    const MeshInput in{dim, n_vert, n_elem, xyz, elem_vert, face_tag, n_shift, periodic_shift};
+    // geometry nodes of every element
+    const int q = geo_nodes ? geo_order : 1;
+    MapEval me(dim, q);
+    std::vector<double> nodes((size_t)n_elem * me.nn * dim);
+    if (geo_nodes) {
+        std::memcpy(nodes.data(), geo_nodes, nodes.size() * sizeof(double));
+    } else {
+        for (int64_t e = 0; e < n_elem; ++e)
+            for (int c = 0; c < nc; ++c)
+                for (int j = 0; j < dim; ++j)
+                    nodes[((size_t)e * nc + c) * dim + j] = xyz[elem_vert[e * nc + c] * dim + j];
+    }
+    std::vector<Pair> pairs;
+    fr_status st = find_face_pairs(in, pairs);
+    if (st != FR_OK) return st;
+
+    // one part per degree present, elements in their relative order
+    int part_of_degree[kMaxN] = {-1, -1, -1, -1, -1}, n_parts = 0;
+    for (int d = 1; d < kMaxN; ++d)
+        if (present[d]) part_of_degree[d] = n_parts++;
+    std::vector<int32_t> part_of((size_t)n_elem);
+    std::vector<int64_t> local((size_t)n_elem);
+    std::vector<int64_t> count(n_parts, 0);
+    for (int64_t e = 0; e < n_elem; ++e) {
+        part_of[e] = part_of_degree[degree[e]];
+        local[e] = count[part_of[e]]++;
+    }
+    std::vector<std::unique_ptr<fr_mesh>> parts(n_parts);
+    for (int d = 1; d < kMaxN; ++d) {
+        const int pi = part_of_degree[d];
+        if (pi < 0) continue;
+        auto pm = std::make_unique<fr_mesh>();
+        pm->dim = dim; pm->p = d; pm->q = q; pm->n_elem = count[pi];
+        build_ref(pm->ref, dim, d);
+        if (n_parts == 1) {
+            pm->nodes = std::move(nodes);
+        } else {
+            pm->nodes.resize((size_t)count[pi] * me.nn * dim);
+            for (int64_t e = 0; e < n_elem; ++e)
+                if (part_of[e] == pi)
+                    std::memcpy(&pm->nodes[(size_t)local[e] * me.nn * dim], &nodes[(size_t)e * me.nn * dim],
+                                (size_t)me.nn * dim * sizeof(double));
+        }
+        st = build_geometry(pm.get());
+        if (st != FR_OK) return st;
+        pm->elem_p.assign((size_t)count[pi], d);
+        pm->n_sp_total = count[pi] * pm->ref.nsp;
+        parts[pi] = std::move(pm);
+    }
+    const std::vector<double> &all_nodes = n_parts == 1 ? parts[0]->nodes : nodes;
+
+    std::vector<MortarLink> mortars;
+    for (const Pair &pr : pairs) {
+        const int pa = part_of[pr.e], pb = part_of[pr.e2];
+        fr_mesh *ma = parts[pa].get();
+        if (pa == pb) {
+            st = pair_points(ma, local[pr.e], pr.fc, local[pr.e2], pr.fc2, pr.sh, face_hmin(in, pr.e, pr.fc));
+            if (st != FR_OK) return st;
+            continue;
+        }
+        for (int a = 0; a < ma->ref.nfpf; ++a)
+            ma->bctag[(size_t)local[pr.e] * ma->ref.nfp + pr.fc * ma->ref.nfpf + a] = kTagMortar;
+        if (degree[pr.e] < degree[pr.e2]) {
+            MortarLink L;
+            L.part_lo = pa; L.part_hi = pb;
+            L.e_lo = local[pr.e]; L.e_hi = local[pr.e2];
+            L.f_lo = pr.fc; L.f_hi = pr.fc2;
+            st = mortar_orient(in, me, all_nodes, pr, face_hmin(in, pr.e, pr.fc), &L.orient);
+            if (st != FR_OK) return st;
+            mortars.push_back(L);
         }
     }
-    for (int64_t e = 0; e < n_elem; ++e)
+    for (int64_t e = 0; e < n_elem; ++e) {
+        fr_mesh *pm = parts[part_of[e]].get();
+        const int nfp = pm->ref.nfp, nfpf = pm->ref.nfpf;
         for (int fc = 0; fc < 2 * dim; ++fc) {
             const int32_t tg = face_tag[e * 2 * dim + fc];
             for (int a = 0; a < nfpf; ++a) {
-                const size_t i = (size_t)e * nfp + fc * nfpf + a;
+                const size_t i = (size_t)local[e] * nfp + fc * nfpf + a;
                 if (tg >= FR_TAG_WALL) {
-                    m->bctag[i] = tg;
-                } else if (m->partner[i] < 0) {
-                    delete m;
-                    fr::set_error("fr_mesh_create: face left unconnected");
+                    pm->bctag[i] = tg;
+                } else if (pm->partner[i] < 0 && pm->bctag[i] != kTagMortar) {
+                    set_error("fr_mesh_create: face left unconnected");
                     return FR_ERR_MESH;
                 }
             }
         }
-    *out = m;
+    }
+    if (n_parts == 1) {
+        *out = parts[0].release();
+        return FR_OK;
+    }
+    auto m = std::make_unique<fr_mesh>();
+    m->dim = dim; m->p = 0; m->q = q; m->n_elem = n_elem;
+    m->nodes = std::move(nodes);
+    m->elem_p = degree;
+    m->part_of = std::move(part_of);
+    m->local = std::move(local);
+    m->mortars = std::move(mortars);
+    for (int64_t e = 0; e < n_elem; ++e) {
+        const fr_mesh *pm = parts[m->part_of[e]].get();
+        const size_t n = (size_t)pm->ref.nsp * dim;
+        m->x_sp.insert(m->x_sp.end(), pm->x_sp.begin() + m->local[e] * n, pm->x_sp.begin() + (m->local[e] + 1) * n);
+        m->n_sp_total += pm->ref.nsp;
+    }
+    m->parts = std::move(parts);
+    *out = m.release();
     return FR_OK;
+}
+
+double lagrange_at(const RefElem &r, int j, double x) { return lagrange_1d(r.xi, r.n, j, x); }
+
+}  // namespace
+
+void mortar_matrices(const RefElem &lo, const RefElem &hi, int orient, std::vector<double> &T,
+                     std::vector<double> &P) {
+    const int dim = lo.dim, nl = lo.nfpf, nh = hi.nfpf;
+    T.assign((size_t)nh * nl, 0.0);
+    P.assign((size_t)nl * nh, 0.0);
+    auto face_w = [&](const RefElem &r, int i) { return dim == 2 ? r.w[i] : r.w[i % r.n] * r.w[i / r.n]; };
+    for (int j = 0; j < nh; ++j) {
+        const double ch[2] = {hi.xi[j % hi.n], dim == 3 ? hi.xi[j / hi.n] : 0.0};
+        double cl[2] = {0, 0};
+        apply_orient(dim, orient, ch, cl);
+        for (int i = 0; i < nl; ++i) {
+            double v = lagrange_at(lo, i % lo.n, cl[0]);
+            if (dim == 3) v *= lagrange_at(lo, i / lo.n, cl[1]);
+            T[(size_t)j * nl + i] = v;
+        }
+    }
+    for (int i = 0; i < nl; ++i)
+        for (int j = 0; j < nh; ++j)
+            P[(size_t)i * nh + j] = face_w(hi, j) * T[(size_t)j * nl + i] / face_w(lo, i);
+}
+
+}  // namespace fr
+
+extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_vert,
+                                    const double *xyz, int64_t n_elem, const int64_t *elem_vert,
+                                    int geo_order, const double *geo_nodes,
+                                    const int32_t *face_tag, int n_shift,
+                                    const double *periodic_shift) {
+    if (out && (p < 1 || p > 4)) {
+        *out = nullptr;
+        fr::set_error("fr_mesh_create: polynomial degree must be 1..4");
+        return FR_ERR_UNSUPPORTED;
+    }
+    return fr::mesh_create_impl(out, dim, p, nullptr, n_vert, xyz, n_elem, elem_vert, geo_order, geo_nodes,
+                                face_tag, n_shift, periodic_shift);
+}
+
+extern "C" fr_status fr_mesh_create_varp(fr_mesh **out, int dim, const int32_t *elem_p, int64_t n_vert,
+                                         const double *xyz, int64_t n_elem, const int64_t *elem_vert,
+                                         int geo_order, const double *geo_nodes,
+                                         const int32_t *face_tag, int n_shift,
+                                         const double *periodic_shift) {
+    if (!elem_p) {
+        if (out) *out = nullptr;
+        fr::set_error("fr_mesh_create_varp: null degree array");
+        return FR_ERR_INVALID_ARG;
+    }
+    return fr::mesh_create_impl(out, dim, 0, elem_p, n_vert, xyz, n_elem, elem_vert, geo_order, geo_nodes,
+                                face_tag, n_shift, periodic_shift);
 }
 
 extern "C" void fr_mesh_destroy(fr_mesh *mesh) { delete mesh; }
 
 extern "C" fr_status fr_mesh_info(const fr_mesh *m, int64_t *n_elem, int *nsp, int *nfp) {
     if (!m) { fr::set_error("fr_mesh_info: null mesh"); return FR_ERR_INVALID_ARG; }
+    const bool uniform = m->parts.empty();
     if (n_elem) *n_elem = m->n_elem;
-    if (nsp) *nsp = m->ref.nsp;
-    if (nfp) *nfp = m->ref.nfp;
+    if (nsp) *nsp = uniform ? m->ref.nsp : 0;
+    if (nfp) *nfp = uniform ? m->ref.nfp : 0;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_mesh_degrees(const fr_mesh *m, int32_t *elem_p, int64_t *n_sol_points) {
+    if (!m) { fr::set_error("fr_mesh_degrees: null mesh"); return FR_ERR_INVALID_ARG; }
+    if (elem_p) std::copy(m->elem_p.begin(), m->elem_p.end(), elem_p);
+    if (n_sol_points) *n_sol_points = m->n_sp_total;
     return FR_OK;
 }
 

@@ -25,7 +25,8 @@ FR_VISC_BR2, FR_VISC_LDG = 0, 1
 STATUS = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_MESH", 3: "FR_ERR_UNSUPPORTED",
           4: "FR_ERR_CUDA", 5: "FR_ERR_NONFINITE", 6: "FR_ERR_TIMEOUT", 7: "FR_ERR_WORKSPACE"}
 
-EXPORTED = ["fr_mesh_create", "fr_mesh_destroy", "fr_mesh_info", "fr_mesh_sol_coords",
+EXPORTED = ["fr_mesh_create", "fr_mesh_create_varp", "fr_mesh_degrees", "fr_mesh_destroy",
+            "fr_mesh_info", "fr_mesh_sol_coords",
             "fr_workspace_bytes", "fr_solver_create", "fr_solver_destroy", "fr_set_state",
             "fr_get_state", "fr_residual", "fr_rk_step", "fr_probe_add", "fr_probe_pressure",
             "fr_probe_history",
@@ -82,6 +83,9 @@ def lib():
     dp = C.POINTER(C.c_double)
     L.fr_mesh_create.argtypes = [C.POINTER(P), I, I, I64, dp, I64, C.POINTER(C.c_int64), I, dp,
                                  C.POINTER(C.c_int32), I, dp]
+    L.fr_mesh_create_varp.argtypes = [C.POINTER(P), I, C.POINTER(C.c_int32), I64, dp, I64,
+                                      C.POINTER(C.c_int64), I, dp, C.POINTER(C.c_int32), I, dp]
+    L.fr_mesh_degrees.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
     L.fr_mesh_destroy.argtypes = [P]
     L.fr_mesh_destroy.restype = None
     L.fr_mesh_info.argtypes = [P, C.POINTER(C.c_int64), C.POINTER(I), C.POINTER(I)]
@@ -129,31 +133,52 @@ def _dptr(a):
 
 class Mesh:
     """fr_mesh_create over a ``synth.meshes.Mesh``-like object (fields dim,
-    xyz, elem_vert, face_tag, periodic_shift, geo_order, geo_nodes)."""
+    xyz, elem_vert, face_tag, periodic_shift, geo_order, geo_nodes); ``p`` is
+    one degree or one degree per element (fr_mesh_create_varp)."""
 
-    def __init__(self, mesh, p: int):
+    def __init__(self, mesh, p):
         L = lib()
         self.dim = int(mesh.dim)
-        self.p = int(p)
+        varp = np.ndim(p) > 0
+        self.p = None if varp else int(p)
         xyz = np.ascontiguousarray(mesh.xyz, dtype=np.float64)
         ev = np.ascontiguousarray(mesh.elem_vert, dtype=np.int64)
         tags = np.ascontiguousarray(mesh.face_tag, dtype=np.int32)
         sh = np.ascontiguousarray(mesh.periodic_shift, dtype=np.float64).reshape(-1, self.dim)
         gn = None if getattr(mesh, "geo_nodes", None) is None else np.ascontiguousarray(mesh.geo_nodes, dtype=np.float64)
         h = C.c_void_p()
-        st = L.fr_mesh_create(C.byref(h), self.dim, self.p, xyz.shape[0], _dptr(xyz), ev.shape[0],
-                              ev.ctypes.data_as(C.POINTER(C.c_int64)),
-                              int(getattr(mesh, "geo_order", 1)), None if gn is None else _dptr(gn),
-                              tags.ctypes.data_as(C.POINTER(C.c_int32)), sh.shape[0],
-                              _dptr(sh) if sh.size else None)
-        _check(st, "fr_mesh_create")
+        geo = (int(getattr(mesh, "geo_order", 1)), None if gn is None else _dptr(gn),
+               tags.ctypes.data_as(C.POINTER(C.c_int32)), sh.shape[0], _dptr(sh) if sh.size else None)
+        if varp:
+            ep = np.ascontiguousarray(p, dtype=np.int32)
+            if ep.shape != (ev.shape[0],):
+                raise ValueError("one degree per element")
+            st = L.fr_mesh_create_varp(C.byref(h), self.dim, ep.ctypes.data_as(C.POINTER(C.c_int32)),
+                                       xyz.shape[0], _dptr(xyz), ev.shape[0],
+                                       ev.ctypes.data_as(C.POINTER(C.c_int64)), *geo)
+            _check(st, "fr_mesh_create_varp")
+        else:
+            st = L.fr_mesh_create(C.byref(h), self.dim, self.p, xyz.shape[0], _dptr(xyz), ev.shape[0],
+                                  ev.ctypes.data_as(C.POINTER(C.c_int64)), *geo)
+            _check(st, "fr_mesh_create")
         self.handle = h
         ne, nsp, nfp = C.c_int64(), C.c_int(), C.c_int()
         _check(L.fr_mesh_info(h, C.byref(ne), C.byref(nsp), C.byref(nfp)), "fr_mesh_info")
         self.n_elem, self.nsp, self.nfp = ne.value, nsp.value, nfp.value
+        self.elem_p = np.empty(self.n_elem, dtype=np.int32)
+        tot = C.c_int64()
+        _check(L.fr_mesh_degrees(h, self.elem_p.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(tot)),
+               "fr_mesh_degrees")
+        self.n_sp = tot.value
+
+    @property
+    def state_shape(self):
+        """Host state shape of one instance: (n_elem, nsp) for one degree,
+        (n_sp,) element after element when the degree varies."""
+        return (self.n_elem, self.nsp) if self.nsp else (self.n_sp,)
 
     def sol_coords(self):
-        out = np.empty((self.n_elem, self.nsp, self.dim))
+        out = np.empty(self.state_shape + (self.dim,))
         _check(lib().fr_mesh_sol_coords(self.handle, _dptr(out)), "fr_mesh_sol_coords")
         return out
 
@@ -203,19 +228,19 @@ class Solver:
     def set_state(self, inst, u):
         u = np.ascontiguousarray(u, dtype=np.float64)
         m = self.meshes[inst]
-        if u.shape != (m.n_elem, m.nsp, self.V):
+        if u.shape != m.state_shape + (self.V,):
             raise ValueError("state shape")
         _check(lib().fr_set_state(self.handle, inst, _dptr(u)), "fr_set_state")
 
     def get_state(self, inst):
         m = self.meshes[inst]
-        out = np.empty((m.n_elem, m.nsp, self.V))
+        out = np.empty(m.state_shape + (self.V,))
         _check(lib().fr_get_state(self.handle, inst, _dptr(out)), "fr_get_state")
         return out
 
     def residual(self, inst):
         m = self.meshes[inst]
-        out = np.empty((m.n_elem, m.nsp, self.V))
+        out = np.empty(m.state_shape + (self.V,))
         _check(lib().fr_residual(self.handle, inst, _dptr(out)), "fr_residual")
         return out
 

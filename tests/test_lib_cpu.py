@@ -94,3 +94,34 @@ def test_solver_needs_a_device_workspace(fr):
     h = C.c_void_p()
     st = fr.lib().fr_solver_create(C.byref(h), arr, 1, C.byref(cfg), None, 0, None)
     assert st == 7                                   # FR_ERR_WORKSPACE
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_variable_degree_mesh_host_processing_matches_oracle(fr, dim):
+    from oracle.fr_var import VarFRDiscretisation
+    from oracle.physics import NavierStokes
+    n = (6, 5) if dim == 2 else (3, 3, 2)
+    mesh = M.reorient(M.periodic_box(dim, n, (0.0,) * dim, (1.0,) * dim, jitter=0.2), 5)
+    ep = M.checker_degrees(mesh, (1, 2, 3, 4), seed=5)
+    lm = fr.Mesh(mesh, ep)
+    d = VarFRDiscretisation(mesh, ep, NavierStokes(dim))
+    assert lm.nsp == 0 and lm.nfp == 0 and lm.n_sp == d.n_sp
+    assert np.array_equal(lm.elem_p, ep) and lm.state_shape == (d.n_sp,)
+    assert np.abs(lm.sol_coords() - d.sol_coords()).max() < 1e-13
+    uni = fr.Mesh(mesh, 3)
+    assert uni.n_sp == mesh.n_elem * 4 ** dim and np.all(uni.elem_p == 3)
+
+
+def test_variable_degree_mesh_errors(fr):
+    mesh = M.vortex_mesh(3)
+    ep = np.full(mesh.n_elem, 2, dtype=np.int32)
+    ep[4] = 5
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(mesh, ep)
+    assert e.value.status == 3                       # FR_ERR_UNSUPPORTED
+    with pytest.raises(ValueError):
+        fr.Mesh(mesh, ep[:-1])
+    ep[4] = 0
+    with pytest.raises(fr.FRError) as e:
+        fr.Mesh(mesh, ep)
+    assert e.value.status == 3
