@@ -143,9 +143,9 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per element of one stage launch, ncu
     # --set full on the 8-airfoil case (243,854 quads; see profiles/k_flux_airfoil8_full.md),
     # scaled to a launch by the element count
-    "8604a4f7492eb257985022f891afe006f399f942de4ccb7f3b49a5d7688f7832":
-        {"flux_bytes_per_elem": (313.369344e6 + 148.510976e6) / 243854,
-         "grad_bytes_per_elem": (249.985536e6 + 45.448192e6) / 243854},
+    "81ddf6d168e5977ac35fdcef072f36cabc0e0b144934b919a8e892865c683505":
+        {"flux_bytes_per_elem": (315.162368e6 + 149.752832e6) / 243854,
+         "grad_bytes_per_elem": (249.92128e6 + 45.18784e6) / 243854},
 }
 
 
