@@ -97,10 +97,11 @@ def _tandem_draws(rank):
 
 
 def _sponge(mesh):
-    """Variable degree of the airfoil grids (Sec. 5.1): p = 3 within 4 chords
-    of the mid-chord, p = 2 out to 8 chords, p = 1 in the outer far field."""
+    """Variable degree of the airfoil grids (Sec. 5.1, a P0-P3 distribution):
+    p = 3 within 4 chords of the mid-chord, p = 2 out to 8, p = 1 out to 12,
+    p = 0 in the outer far field."""
     from synth import meshes as M
-    return M.sponge_degrees(mesh, (0.5, 0.0), (4.0, 8.0), (3, 2, 1))
+    return M.sponge_degrees(mesh, (0.5, 0.0), (4.0, 8.0, 12.0), (3, 2, 1, 0))
 
 
 def _cavity(rank, n):
@@ -119,7 +120,7 @@ WORKLOADS = {
                         "Re_c=23000, M=0.2, LSRK45, one probe per candidate", _airfoils, (1.0, 0.0)),
     "airfoil_sponge": Workload("airfoil_sponge", 2, 3, 23000.0, 0.2, 32,
                                "32 NACA 4-digit O-meshes (8k-40k curved quads, seed 2312) with a "
-                               "variable degree: p=3 within 4c, p=2 to 8c, p=1 beyond (mortar "
+                               "variable degree P0-P3: p=3 within 4c, p=2 to 8c, p=1 to 12c, p=0 beyond (mortar "
                                "coupling), NS BR2, Re_c=23000, M=0.2, LSRK45, one probe per candidate",
                                _airfoils, (1.0, 0.0), degrees=_sponge),
     "tandem": Workload("tandem", 3, 4, 1000.0, 0.2, 16,
@@ -486,7 +487,7 @@ def run_gpu(args):
     dom = max(("flux", "grad"), key=lambda k: share[k])
     kdx = kinds.index(dom)
     # one stage's launches of the dominant kind (one per degree group)
-    alg = sum(algorithmic_bytes(int(by_p[q]), 4, dom, q) for q in range(1, 5) if by_p[q])
+    alg = sum(algorithmic_bytes(int(by_p[q]), 4, dom, q) for q in range(0, 5) if by_p[q])
     stage_kernel_ms = float(kms[kdx] * kcnt[kdx]) / (n_prof * STAGES)
     achieved = alg / (stage_kernel_ms / 1e3) / 1e9
     peaks = {}
@@ -500,7 +501,7 @@ def run_gpu(args):
     rec = NCU_TRAFFIC.get(kernel_source_hash())
     if rec and W.name == rec.get("workload", "airfoil"):
         traffic = rec[f"{dom}_bytes_per_elem"] * E
-    groups = [q for q in range(1, 5) if by_p[q]]
+    groups = [q for q in range(0, 5) if by_p[q]]
     kname = (f"k_{dom}<{W.dim},{W.p + 1},float>" if len(groups) == 1 else
              f"k_{dom}<{W.dim},N,float> over the degree groups N = {[q + 1 for q in groups]}, "
              "one launch each per stage")
@@ -565,9 +566,9 @@ def run_gpu(args):
                 "config": {"workload": workload_text(),
                            "candidates_per_gpu": len(fms), "elements_per_gpu": E,
                            "sol_pts_per_gpu": NSPT, "p": W.p, "dt": dt,
-                           "elements_by_degree": {str(q): int(by_p[q]) for q in range(1, 5) if by_p[q]},
+                           "elements_by_degree": {str(q): int(by_p[q]) for q in range(0, 5) if by_p[q]},
                            "l2": "inputs larger than L2 (FP32 working set %.2f GB > 129 MB), no flush"
-                                 % (sum(sol_bytes(int(by_p[q]), q) for q in range(1, 5)) / 1e9)},
+                                 % (sum(sol_bytes(int(by_p[q]), q) for q in range(0, 5)) / 1e9)},
                 "roofline": roof,
                 "cpu_baseline": cpu_base,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,

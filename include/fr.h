@@ -43,7 +43,7 @@ typedef int fr_status;
 #define FR_OK 0
 #define FR_ERR_INVALID_ARG 1   /* null pointer, out-of-range index or size */
 #define FR_ERR_MESH 2          /* unmatched face, non-positive Jacobian, ... */
-#define FR_ERR_UNSUPPORTED 3   /* p outside 1..4, mixed dimensions in a batch */
+#define FR_ERR_UNSUPPORTED 3   /* p outside 0..4, mixed dimensions in a batch */
 #define FR_ERR_CUDA 4          /* a CUDA runtime call failed */
 #define FR_ERR_NONFINITE 5     /* NaN/Inf found in the state */
 #define FR_ERR_TIMEOUT 6       /* a bounded device wait gave up */
@@ -109,7 +109,8 @@ typedef struct fr_config {
  * the element map), outward normals scaled by the surface Jacobian and the
  * partner of every flux point.
  *  dim            2 (quads) or 3 (hexes)
- *  p              polynomial degree, 1..4
+ *  p              polynomial degree, 0..4 (0: one solution point per element,
+ *                 the first-order finite-volume limit of the scheme)
  *  xyz            n_vert * dim vertex coordinates
  *  elem_vert      n_elem * 2^dim corner vertex indices, tensor order
  *  geo_order      degree q >= 1 of the element map
@@ -129,7 +130,7 @@ void fr_mesh_destroy(fr_mesh *mesh);
 /* A mesh whose polynomial degree is chosen per element (Sec. 5.1: the
  * airfoil grids run with a variable solution degree, P0-P3 / P0-P4, lower
  * degrees in the outer zones to damp waves before the boundaries).  Same
- * arguments as fr_mesh_create with ``elem_p`` (n_elem degrees, 1..4) in place
+ * arguments as fr_mesh_create with ``elem_p`` (n_elem degrees, 0..4) in place
  * of p.  The paper does not say how a face joining two degrees is treated;
  * this library uses the conservative mortar coupling: the mortar is the
  * higher side's set of flux points, the lower side's face trace is evaluated

@@ -178,7 +178,7 @@ Plan make_plan(fr_mesh *const *meshes, int n_inst) {
     bool present[kMaxN] = {};
     for (int i = 0; i < n_inst; ++i)
         for (const fr_mesh *pm : parts_of(meshes[i])) present[pm->p] = true;
-    for (int d = 1; d < kMaxN; ++d)
+    for (int d = 0; d < kMaxN; ++d)
         if (present[d]) { P.group_of_degree[d] = P.G; P.degree[P.G] = d; ++P.G; }
     for (int i = 0; i < n_inst; ++i) {
         const fr_mesh *m = meshes[i];

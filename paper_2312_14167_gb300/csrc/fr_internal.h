@@ -11,7 +11,7 @@
 
 namespace fr {
 
-constexpr int kMaxN = 5;        // p <= 4
+constexpr int kMaxN = 5;        // p <= 4 (p = 0: one point, first-order finite volume)
 constexpr int kMaxProbes = 1024;
 // internal face tag of the flux points of a face joining an element of
 // another degree (a mortar face); never passed in by a caller

@@ -5,6 +5,7 @@ namespace frk {
 
 cudaError_t launch_3_f32(int N, int kind, bool visc, const KArgs<float> &a, int grid, cudaStream_t s) {
     switch (N) {
+    case 1: return launch_n<3, 1, float>(kind, visc, a, grid, s);
     case 2: return launch_n<3, 2, float>(kind, visc, a, grid, s);
     case 3: return launch_n<3, 3, float>(kind, visc, a, grid, s);
     case 4: return launch_n<3, 4, float>(kind, visc, a, grid, s);
@@ -26,6 +27,7 @@ static cudaError_t prepare_n(bool visc) {
 
 cudaError_t prepare_3_f32(int N, bool visc) {
     switch (N) {
+    case 1: return prepare_n<1>(visc);
     case 2: return prepare_n<2>(visc);
     case 3: return prepare_n<3>(visc);
     case 4: return prepare_n<4>(visc);

@@ -1278,7 +1278,7 @@ __global__ void k_to_f64(const KArgs<real> a) {
 //    higher side takes it as it is, the lower side minus its projection P.
 //    On these faces the lower-degree side is LDG's left side.
 // --------------------------------------------------------------------------
-constexpr int kMaxGroups = 4;
+constexpr int kMaxGroups = 5;   // degrees 0..4
 
 struct MortarFace {
     int32_t glo, ghi;          // degree groups of the lower and higher side

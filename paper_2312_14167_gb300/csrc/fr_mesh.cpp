@@ -609,8 +609,8 @@ fr_status mesh_create_impl(fr_mesh **out, int dim, int p_uniform, const int32_t 
     if (elem_p) std::copy(elem_p, elem_p + n_elem, degree.begin());
     bool present[kMaxN] = {};
     for (int64_t e = 0; e < n_elem; ++e) {
-        if (degree[e] < 1 || degree[e] > 4) {
-            set_error("fr_mesh_create: polynomial degree must be 1..4");
+        if (degree[e] < 0 || degree[e] > 4) {
+            set_error("fr_mesh_create: polynomial degree must be 0..4");
             return FR_ERR_UNSUPPORTED;
         }
         present[degree[e]] = true;
@@ -640,7 +640,7 @@ fr_status mesh_create_impl(fr_mesh **out, int dim, int p_uniform, const int32_t 
 
     // one part per degree present, elements in their relative order
     int part_of_degree[kMaxN] = {-1, -1, -1, -1, -1}, n_parts = 0;
-    for (int d = 1; d < kMaxN; ++d)
+    for (int d = 0; d < kMaxN; ++d)
         if (present[d]) part_of_degree[d] = n_parts++;
     std::vector<int32_t> part_of((size_t)n_elem);
     std::vector<int64_t> local((size_t)n_elem);
@@ -650,7 +650,7 @@ fr_status mesh_create_impl(fr_mesh **out, int dim, int p_uniform, const int32_t 
         local[e] = count[part_of[e]]++;
     }
     std::vector<std::unique_ptr<fr_mesh>> parts(n_parts);
-    for (int d = 1; d < kMaxN; ++d) {
+    for (int d = 0; d < kMaxN; ++d) {
         const int pi = part_of_degree[d];
         if (pi < 0) continue;
         auto pm = std::make_unique<fr_mesh>();
@@ -764,9 +764,9 @@ extern "C" fr_status fr_mesh_create(fr_mesh **out, int dim, int p, int64_t n_ver
                                     int geo_order, const double *geo_nodes,
                                     const int32_t *face_tag, int n_shift,
                                     const double *periodic_shift) {
-    if (out && (p < 1 || p > 4)) {
+    if (out && (p < 0 || p > 4)) {
         *out = nullptr;
-        fr::set_error("fr_mesh_create: polynomial degree must be 1..4");
+        fr::set_error("fr_mesh_create: polynomial degree must be 0..4");
         return FR_ERR_UNSUPPORTED;
     }
     return fr::mesh_create_impl(out, dim, p, nullptr, n_vert, xyz, n_elem, elem_vert, geo_order, geo_nodes,

@@ -27,10 +27,10 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _box(dim, seed=5):
+def _box(dim, seed=5, degrees=(1, 2, 3, 4)):
     n = (6, 5) if dim == 2 else (3, 3, 2)
     m = M.reorient(M.periodic_box(dim, n, (0.0,) * dim, (1.0,) * dim, jitter=0.2), seed)
-    return m, M.checker_degrees(m, (1, 2, 3, 4), seed=seed)
+    return m, M.checker_degrees(m, degrees, seed=seed)
 
 
 def _cavity():
@@ -44,7 +44,10 @@ def _airfoil():
 
 
 MESHES = {"box2d": lambda: _box(2), "box3d": lambda: _box(3), "cavity": _cavity,
-          "airfoil": _airfoil}
+          "airfoil": _airfoil,
+          # with degree-0 (one-point, finite-volume) elements
+          "box2d0": lambda: _box(2, degrees=(0, 1, 2, 3)),
+          "box3d0": lambda: _box(3, degrees=(0, 1, 2, 3))}
 
 
 # viscosity per case: the airfoil grids have 1e-3-thick wall cells, where
@@ -91,7 +94,10 @@ CASES = [("box2d", False, "br2", "rusanov"), ("box2d", True, "br2", "rusanov"),
          ("box2d", True, "ldg", "rusanov"), ("box2d", True, "br2", "roe"),
          ("box3d", False, "br2", "rusanov"), ("box3d", True, "br2", "rusanov"),
          ("box3d", True, "ldg", "roe"), ("cavity", True, "br2", "rusanov"),
-         ("cavity", True, "ldg", "rusanov"), ("airfoil", True, "br2", "rusanov")]
+         ("cavity", True, "ldg", "rusanov"), ("airfoil", True, "br2", "rusanov"),
+         ("box2d0", False, "br2", "rusanov"), ("box2d0", True, "br2", "rusanov"),
+         ("box2d0", True, "ldg", "roe"), ("box3d0", False, "br2", "rusanov"),
+         ("box3d0", True, "br2", "rusanov"), ("box3d0", True, "ldg", "rusanov")]
 
 
 @pytest.mark.parametrize("name,viscous,scheme,flux", CASES)
@@ -131,7 +137,8 @@ def test_rk4_steps_match_oracle():
     assert _rel(sol.get_state(0), ur) < 1e-12
 
 
-@pytest.mark.parametrize("name,scheme", [("box2d", "br2"), ("box3d", "ldg"), ("cavity", "br2")])
+@pytest.mark.parametrize("name,scheme", [("box2d", "br2"), ("box3d", "ldg"), ("cavity", "br2"),
+                                         ("box2d0", "ldg"), ("box3d0", "br2")])
 def test_fp32_residual_within_forward_error_bound(name, scheme):
     m, ep = MESHES[name]()
     d = VarFRDiscretisation(m, ep, _phys(m.dim, True, "rusanov"), viscous_scheme=scheme)

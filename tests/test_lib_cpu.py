@@ -121,7 +121,7 @@ def test_variable_degree_mesh_errors(fr):
     assert e.value.status == 3                       # FR_ERR_UNSUPPORTED
     with pytest.raises(ValueError):
         fr.Mesh(mesh, ep[:-1])
-    ep[4] = 0
+    ep[4] = -1
     with pytest.raises(fr.FRError) as e:
         fr.Mesh(mesh, ep)
     assert e.value.status == 3

@@ -19,10 +19,13 @@ def _phys(dim, viscous, mach=0.3, flux="rusanov", mu=0.01):
                         flux=flux)
 
 
-def _mixed_box(dim, jitter, seed=5):
+DEGREE_SETS = [(1, 2, 3, 4), (0, 1, 2, 3)]
+
+
+def _mixed_box(dim, jitter, seed=5, degrees=(1, 2, 3, 4)):
     n = (6, 5) if dim == 2 else (3, 3, 2)
     m = M.reorient(M.periodic_box(dim, n, (0.0,) * dim, (1.0,) * dim, jitter=jitter), seed)
-    return m, M.checker_degrees(m, (1, 2, 3, 4), seed=seed)
+    return m, M.checker_degrees(m, degrees, seed=seed)
 
 
 @pytest.mark.parametrize("scheme,flux", [("br2", "rusanov"), ("ldg", "rusanov"), ("br2", "roe")])
@@ -38,13 +41,14 @@ def test_uniform_degree_is_the_fr_oracle(scheme, flux):
     assert np.allclose(d1.wall_force(u.reshape(-1, 4)), d0.wall_force(u), rtol=1e-13, atol=1e-14)
 
 
+@pytest.mark.parametrize("degrees", DEGREE_SETS)
 @pytest.mark.parametrize("dim", [2, 3])
-def test_mortar_operators_are_exact_on_polynomials_in_every_orientation(dim):
+def test_mortar_operators_are_exact_on_polynomials_in_every_orientation(dim, degrees):
     """T carries a degree-p_lo polynomial of the physical coordinates from the
     lower side's points to the higher side's; P carries it back unchanged
     and keeps the face integral of any trace (affine faces, all relative
     orientations from randomly rotated element frames)."""
-    m, ep = _mixed_box(dim, jitter=0.0)
+    m, ep = _mixed_box(dim, jitter=0.0, degrees=degrees)
     d = VarFRDiscretisation(m, ep, _phys(dim, False))
     rng = np.random.default_rng(0)
     seen = {"hi": 0, "lo": 0}
@@ -75,20 +79,22 @@ def test_mortar_operators_are_exact_on_polynomials_in_every_orientation(dim):
     assert seen["hi"] > 10 and seen["lo"] > 10
 
 
+@pytest.mark.parametrize("degrees", DEGREE_SETS)
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("viscous,scheme", [(False, "br2"), (True, "br2"), (True, "ldg")])
-def test_free_stream_preserved_on_mixed_degrees(dim, viscous, scheme):
-    m, ep = _mixed_box(dim, jitter=0.2)
+def test_free_stream_preserved_on_mixed_degrees(dim, viscous, scheme, degrees):
+    m, ep = _mixed_box(dim, jitter=0.2, degrees=degrees)
     d = VarFRDiscretisation(m, ep, _phys(dim, viscous), viscous_scheme=scheme)
     u = S.free_stream((d.n_sp,), dim, 0.3, direction=(1.0, 0.4, 0.2)[:dim])
     R, mag = d.residual(u, magnitude=True)
     assert np.max(np.abs(R)) < 1e-13 * np.max(mag)
 
 
+@pytest.mark.parametrize("degrees", DEGREE_SETS)
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("scheme,flux", [("br2", "rusanov"), ("ldg", "rusanov"), ("br2", "roe")])
-def test_mixed_degree_meshes_conserve(dim, scheme, flux):
-    m, ep = _mixed_box(dim, jitter=0.2)
+def test_mixed_degree_meshes_conserve(dim, scheme, flux, degrees):
+    m, ep = _mixed_box(dim, jitter=0.2, degrees=degrees)
     d = VarFRDiscretisation(m, ep, _phys(dim, True, flux=flux), viscous_scheme=scheme)
     u = S.smooth_perturbed(d.sol_coords(), dim, 0.3, amp=0.05, seed=2)
     R = d.residual(u)
@@ -139,3 +145,31 @@ def test_mixed_degree_vortex_residual_converges_like_its_lower_degree(p):
     u32 = _vortex_residual_error(32, (p,))
     assert np.log2(e16 / e32) > p - 0.3
     assert e32 < 1.05 * u32
+
+
+@pytest.mark.parametrize("flux", ["rusanov", "roe"])
+def test_degree_zero_is_first_order_finite_volume(flux):
+    """With one solution point per element and the DG-recovery correction
+    (g_L' = -1/2, g_R' = 1/2), FR reduces to the cell-centred first-order
+    finite-volume scheme: on straight-edged (bilinear) quads
+    du/dt = -(1/area) sum over edges of F*(u, u_neighbour, n) |edge|.  The
+    right-hand side is written out here from the vertex coordinates."""
+    from oracle.geometry import face_pairs
+    m = M.periodic_box(2, (7, 6), (0.0, 0.0), (1.4, 1.0), jitter=0.25)
+    ph = _phys(2, False, flux=flux)
+    d = VarFRDiscretisation(m, np.zeros(m.n_elem, dtype=np.int64), ph)
+    u = S.smooth_perturbed(d.sol_coords(), 2, 0.3, amp=0.1, seed=6)
+    X = m.xyz[m.elem_vert]                                   # corners, tensor order
+    ring = [0, 1, 3, 2]                                      # counter-clockwise
+    P = X[:, ring]
+    area = 0.5 * np.sum(P[:, :, 0] * np.roll(P[:, :, 1], -1, 1) - np.roll(P[:, :, 0], -1, 1) * P[:, :, 1], 1)
+    edge = {0: (2, 0), 1: (1, 3), 2: (0, 1), 3: (3, 2)}      # face -> corners, counter-clockwise
+    nb = {(e, f): e2 for (e, f, e2, f2, sh) in face_pairs(m)}
+    R = np.zeros_like(u)
+    for e in range(m.n_elem):
+        for f, (a, b) in edge.items():
+            t = X[e, b] - X[e, a]
+            n = np.array([t[1], -t[0]])                      # outward, |n| = edge length
+            R[e] -= ph.common_inviscid(u[e][None], u[nb[(e, f)]][None], n[None])[0]
+        R[e] /= area[e]
+    assert np.abs(d.residual(u) - R).max() < 1e-12 * np.abs(R).max()
