@@ -311,6 +311,8 @@ void fill_args(const fr_solver *s, int g, frk::KArgs<real> &a) {
         a.opGL[i] = r.dgL[i];
         a.opGR[i] = r.dgR[i];
         a.opW[i] = r.w[i];
+        for (int mm = 0; mm < G.N; ++mm)
+            a.opDT[i * frk::kMaxN + mm] = r.D1[i][mm] - r.dgR[i] * r.lend[1][mm] - r.dgL[i] * r.lend[0][mm];
     }
 }
 

@@ -117,6 +117,9 @@ struct KArgs {
     double opD1[kMaxN * kMaxN];   // D1[i][m] = l_m'(xi_i)
     double opL[2 * kMaxN];        // l_m(-1), l_m(+1)
     double opGL[kMaxN], opGR[kMaxN];  // g_L'(xi_i), g_R'(xi_i)
+    // divergence operator with the correction of the discontinuous flux folded
+    // in: DT[i][m] = D1[i][m] - g_R'(xi_i) l_m(+1) - g_L'(xi_i) l_m(-1)
+    double opDT[kMaxN * kMaxN];
     double opW[kMaxN];            // Gauss weights
 };
 
@@ -126,6 +129,8 @@ struct KArgs {
 // shared-memory regions are padded to multiples of 4 values (16 B in FP32,
 // 32 B in FP64) so that every region can take 128-bit accesses
 __host__ __device__ constexpr int pad4(int n) { return (n + 3) / 4 * 4; }
+// shared-memory slots of the 1-D operators (load_ops)
+__host__ __device__ constexpr int ops_slots(int N) { return pad4(2 * N * N + 4 * N); }
 
 // LDG's one-sided switch: is the own side of flux point gf (partner index
 // pt >= 0) the left side?  Conforming faces: the smaller (element, point)
@@ -417,8 +422,11 @@ __device__ __forceinline__ void bc_states(int tag, const real *uL, const real *n
 // --------------------------------------------------------------------------
 template <typename real>
 __device__ __forceinline__ void load_ops(const KArgs<real> &a, real *sOp, int N) {
-    // layout: D1[N*N] | L[2N] | GL[N] | GR[N]
-    for (int i = threadIdx.x; i < N * N; i += blockDim.x) sOp[i] = (real)a.opD1[(i / N) * kMaxN + (i % N)];
+    // layout: D1[N*N] | L[2N] | GL[N] | GR[N] | DT[N*N]
+    for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+        sOp[i] = (real)a.opD1[(i / N) * kMaxN + (i % N)];
+        sOp[N * N + 4 * N + i] = (real)a.opDT[(i / N) * kMaxN + (i % N)];
+    }
     for (int i = threadIdx.x; i < 2 * N; i += blockDim.x) sOp[N * N + i] = (real)a.opL[(i / N) * kMaxN + (i % N)];
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         sOp[N * N + 2 * N + i] = (real)a.opGL[i];
@@ -599,7 +607,7 @@ k_grad(const KArgs<real> a) {
     constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
-    real *sU = sOp + pad4(N * N + 4 * N);
+    real *sU = sOp + ops_slots(N);
     real *sM = sU + pad4(NE * G::PROWS * V);
     real *sD = sM + pad4(NE * NSP * MS);
     real *sB = sD + pad4(NE * NFP * V);
@@ -796,12 +804,12 @@ k_flux(const KArgs<real> a) {
     constexpr int ITS = (NE * NSP + G::THREADS - 1) / G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
-    real *sU = sOp + pad4(N * N + 4 * N);
+    real *sU = sOp + ops_slots(N);
     real *sM = sU + pad4(NE * NSP * V);
     real *sC = sM + pad4(NE * NSP * MS);
     real *sD = sC + pad4(NE * NFP * V);
     real *sF = sD + (VISC ? pad4(NE * NFP * V) : 0);   // [j][k][s][v]
-    const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N;
+    const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N, *DT = GR + N;
 
     const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
     const int64_t e_end = a.elem0 + a.n_elem;
@@ -977,10 +985,11 @@ k_flux(const KArgs<real> a) {
     }
     __syncthreads();
 
-    // 3) divergence + correction, residual, RK update.  Along each line the
-    // same loaded values give the derivative and the flux polynomial at both
-    // ends; jump = common normal flux - discontinuous normal flux, where the
-    // - face's outward normal flux is minus the polynomial's value there.
+    // 3) divergence + correction, residual, RK update.  The correction
+    // g_R' (F*_+ - f(+1)) - g_L' (F*_- + f(-1)) (the - face's outward normal
+    // flux is minus the flux polynomial's value there) is linear in the line's
+    // flux values, so the polynomial's end values are folded into the
+    // derivative operator (DT) and only the common fluxes are added here.
 #pragma unroll
     for (int it = 0; it < ITS; ++it) {
         const int w = tid + it * G::THREADS;
@@ -993,28 +1002,21 @@ k_flux(const KArgs<real> a) {
 #pragma unroll
         for (int k = 0; k < D; ++k) {
             const int ik = G::digit(s, k), st = G::stride(k);
-            const real *row = D1 + ik * N;
+            const real *row = DT + ik * N;
             const int q0 = (j * D + k) * NSP + s - ik * st;
-            real fm[V], fp[V];
-#pragma unroll
-            for (int v = 0; v < V; ++v) { fm[v] = 0; fp[v] = 0; }
 #pragma unroll
             for (int m = 0; m < N; ++m) {
                 real x[V];
                 ld_v<V>(sF + G::template slot<false>(q0 + m * st) * V, x);
-                const real c = row[m], cm = Lm[m], cp = Lp[m];
+                const real c = row[m];
 #pragma unroll
-                for (int v = 0; v < V; ++v) {
-                    div[v] += c * x[v];
-                    fm[v] += cm * x[v];
-                    fp[v] += cp * x[v];
-                }
+                for (int v = 0; v < V; ++v) div[v] += c * x[v];
             }
             real jm[V], jp[V];
             ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 0)) * V, jm);
             ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 1)) * V, jp);
 #pragma unroll
-            for (int v = 0; v < V; ++v) div[v] += GR[ik] * (jp[v] - fp[v]) - GL[ik] * (jm[v] + fm[v]);
+            for (int v = 0; v < V; ++v) div[v] += GR[ik] * jp[v] - GL[ik] * jm[v];
         }
         const real iJ = sM[(j * NSP + s) * MS + D * D];
         const int64_t g = (e * NSP + s) * V;
@@ -1088,7 +1090,7 @@ k_interp(const KArgs<real> a) {
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, NE = G::NE;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
-    real *sU = sOp + pad4(N * N + 4 * N);
+    real *sU = sOp + ops_slots(N);
     const real *Lm = sOp + N * N, *Lp = Lm + N;
     const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
     const int64_t e_end = a.elem0 + a.n_elem;
@@ -1415,7 +1417,7 @@ template <int D, int N, typename real>
 size_t smem_bytes(int kind, bool visc) {
     using G = Geo<D, N>;
     constexpr int NE = G::NE, NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS;
-    size_t n = pad4(N * N + 4 * N);
+    size_t n = ops_slots(N);
     constexpr int PR = G::PROWS;   // k_grad uses the row-padded layout
     if (kind == K_FLUX) {
         n += pad4(NE * NSP * V) + pad4(NE * NSP * MS) + pad4(NE * NFP * V) * (visc ? 2 : 1) +
