@@ -144,9 +144,9 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per element of one stage launch, ncu
     # --set full on the 8-airfoil case (243,854 quads; see profiles/k_flux_airfoil8_full.md),
     # scaled to a launch by the element count
-    "81ddf6d168e5977ac35fdcef072f36cabc0e0b144934b919a8e892865c683505":
-        {"flux_bytes_per_elem": (315.162368e6 + 149.752832e6) / 243854,
-         "grad_bytes_per_elem": (249.92128e6 + 45.18784e6) / 243854},
+    "5a2588fd0811ddda537a7bffe000f9711664409e38d275cd289ee158c20f8d5b":
+        {"flux_bytes_per_elem": (315.155456e6 + 150.039552e6) / 243854,
+         "grad_bytes_per_elem": (249.938176e6 + 45.37472e6) / 243854},
 }
 
 

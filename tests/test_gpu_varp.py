@@ -43,17 +43,26 @@ def _airfoil():
     return m, M.sponge_degrees(m, (0.5, 0.0), (2.0, 6.0), (4, 3, 2))
 
 
+def _tandem():
+    """Curved (q = 2) tandem-cylinder hexes: O-rings and the Cartesian
+    background meet in non-trivial face orientations; 564 faces join two
+    degrees."""
+    m = M.tandem_cylinders(2.5, 0.8, 900, 3)
+    return m, M.sponge_degrees(m, (1.25, 0.0), (2.5, 5.0), (3, 2, 1))
+
+
 MESHES = {"box2d": lambda: _box(2), "box3d": lambda: _box(3), "cavity": _cavity,
           "airfoil": _airfoil,
           # with degree-0 (one-point, finite-volume) elements
           "box2d0": lambda: _box(2, degrees=(0, 1, 2, 3)),
-          "box3d0": lambda: _box(3, degrees=(0, 1, 2, 3))}
+          "box3d0": lambda: _box(3, degrees=(0, 1, 2, 3)),
+          "tandem": _tandem}
 
 
 # viscosity per case: the airfoil grids have 1e-3-thick wall cells, where
 # mu = 0.01 would put the explicit viscous step limit far below the CFL step;
 # they run at the airfoil workload's Re_c = 23000
-MU_CASE = {"airfoil": 1.0 / 23000.0}
+MU_CASE = {"airfoil": 1.0 / 23000.0, "tandem": 1.0e-3}
 
 
 def _phys(dim, viscous, flux, mu=MU):
@@ -97,7 +106,8 @@ CASES = [("box2d", False, "br2", "rusanov"), ("box2d", True, "br2", "rusanov"),
          ("cavity", True, "ldg", "rusanov"), ("airfoil", True, "br2", "rusanov"),
          ("box2d0", False, "br2", "rusanov"), ("box2d0", True, "br2", "rusanov"),
          ("box2d0", True, "ldg", "roe"), ("box3d0", False, "br2", "rusanov"),
-         ("box3d0", True, "br2", "rusanov"), ("box3d0", True, "ldg", "rusanov")]
+         ("box3d0", True, "br2", "rusanov"), ("box3d0", True, "ldg", "rusanov"),
+         ("tandem", True, "br2", "rusanov"), ("tandem", True, "ldg", "roe")]
 
 
 @pytest.mark.parametrize("name,viscous,scheme,flux", CASES)
@@ -138,12 +148,13 @@ def test_rk4_steps_match_oracle():
 
 
 @pytest.mark.parametrize("name,scheme", [("box2d", "br2"), ("box3d", "ldg"), ("cavity", "br2"),
-                                         ("box2d0", "ldg"), ("box3d0", "br2")])
+                                         ("box2d0", "ldg"), ("box3d0", "br2"), ("tandem", "br2")])
 def test_fp32_residual_within_forward_error_bound(name, scheme):
     m, ep = MESHES[name]()
-    d = VarFRDiscretisation(m, ep, _phys(m.dim, True, "rusanov"), viscous_scheme=scheme)
-    sol = _solver([(m, ep)], True, scheme, "rusanov", "fp32")
-    u = _state(sol.meshes[0].sol_coords(), m.dim)
+    mu = MU_CASE.get(name, MU)
+    d = VarFRDiscretisation(m, ep, _phys(m.dim, True, "rusanov", mu), viscous_scheme=scheme)
+    sol = _solver([(m, ep)], True, scheme, "rusanov", "fp32", mu=mu)
+    u = _state(sol.meshes[0].sol_coords(), m.dim, mesh=m)
     sol.set_state(0, u)
     u32 = u.astype(np.float32).astype(np.float64)
     R, mag = d.residual(u32, magnitude=True)
