@@ -144,9 +144,9 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per element of one stage launch, ncu
     # --set full on the 8-airfoil case (243,854 quads; see profiles/k_flux_airfoil8_full.md),
     # scaled to a launch by the element count
-    "5a2588fd0811ddda537a7bffe000f9711664409e38d275cd289ee158c20f8d5b":
-        {"flux_bytes_per_elem": (315.155456e6 + 150.039552e6) / 243854,
-         "grad_bytes_per_elem": (249.938176e6 + 45.37472e6) / 243854},
+    "175c2c4449899d311e15f5af07aa5d44cf3210159064cba998be789c04534ed5":
+        {"flux_bytes_per_elem": (315.179776e6 + 149.26464e6) / 243854,
+         "grad_bytes_per_elem": (250.00448e6 + 45.308672e6) / 243854},
 }
 
 

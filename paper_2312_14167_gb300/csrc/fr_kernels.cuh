@@ -161,6 +161,13 @@ struct Geo {
     __host__ __device__ __forceinline__ static constexpr int slot(int i) { return PAD ? i + i / N : i; }
     template <bool PAD>
     static constexpr int slots() { return PAD ? PROWS : NSP; }
+    // Row padding per kernel.  2-D states are read as 128-bit vectors and the
+    // gradient kernel pads every row (flux kernel: no pad).  3-D states are
+    // read one scalar at a time, so a warp whose lanes step row by row (flux
+    // points on a face normal to xi step N points) is conflict-free when that
+    // step, in words, is odd: pad a row (one V-slot) only when N is even.
+    static constexpr bool GRAD_PAD = (D == 2) || (N % 2 == 0);
+    static constexpr bool FLUX_PAD = (D == 3) && (N % 2 == 0);
     __device__ __forceinline__ static int digit(int s, int k) { return (s / stride(k)) % N; }
     // flux point at the end (side 0: -1, 1: +1) of the k-line through s
     __device__ __forceinline__ static int fp_of(int s, int k, int side) {
@@ -608,10 +615,11 @@ k_grad(const KArgs<real> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
     real *sU = sOp + ops_slots(N);
-    real *sM = sU + pad4(NE * G::PROWS * V);
+    constexpr bool PAD = G::GRAD_PAD;
+    real *sM = sU + pad4(NE * G::template slots<PAD>() * V);
     real *sD = sM + pad4(NE * NSP * MS);
     real *sB = sD + pad4(NE * NFP * V);
-    real *sGD = sB + pad4(NE * NFP * V);      // [j][s][jd][v], V pad floats per row
+    real *sGD = sB + pad4(NE * NFP * V);      // [j][s][jd][v], V pad floats per row if PAD
     const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N;
 
     const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
@@ -638,7 +646,7 @@ k_grad(const KArgs<real> a) {
         }
     }
     load_ops(a, sOp, N);
-    load_state_rows<N, V, true>(sU, a.U, a.elist, e0, ne, NSP);
+    load_state_rows<N, V, PAD>(sU, a.U, a.elist, e0, ne, NSP);
     load_tile(sM, a.MET, a.elist, e0, ne, NSP * MS);
     __syncthreads();
 
@@ -649,7 +657,7 @@ k_grad(const KArgs<real> a) {
         if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         real uL[V];
-        interp_line<D, N, V, true>(sU, j, f, Lm, Lp, uL);
+        interp_line<D, N, V, PAD>(sU, j, f, Lm, Lp, uL);
         real uc[V], ub[V];
         if (pt[it] >= 0) {
             // LDG: one-sided common solution, left side = smaller point index
@@ -700,13 +708,13 @@ k_grad(const KArgs<real> a) {
 #pragma unroll
             for (int m = 0; m < N; ++m) {
                 real x[V];
-                ld_v<V>(sU + G::prow(q0 + m * st) * V, x);
+                ld_v<V>(sU + G::template slot<PAD>(q0 + m * st) * V, x);
                 const real c = row[m];
 #pragma unroll
                 for (int v = 0; v < V; ++v) Gk[k][v] += c * x[v];
             }
         }
-        real *dst = sGD + (j * NSP + s) * D * V + ((j * NSP + s) / N) * V;
+        real *dst = sGD + (j * NSP + s) * D * V + (PAD ? ((j * NSP + s) / N) * V : 0);
 #pragma unroll
         for (int jd = 0; jd < D; ++jd) {
             real g[V];
@@ -744,7 +752,7 @@ k_grad(const KArgs<real> a) {
         for (int m = 0; m < N; ++m) {
             const int sp = base + m * st;
             const real c = L[m];
-            const real *gd = sGD + (j * NSP + sp) * D * V + ((j * NSP + sp) / N) * V;
+            const real *gd = sGD + (j * NSP + sp) * D * V + (PAD ? ((j * NSP + sp) / N) * V : 0);
             const real *M = sM + (j * NSP + sp) * MS;
             const real cg = c * Gs[m] * M[D * D];
 #pragma unroll
@@ -805,7 +813,8 @@ k_flux(const KArgs<real> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
     real *sU = sOp + ops_slots(N);
-    real *sM = sU + pad4(NE * NSP * V);
+    constexpr bool PAD = G::FLUX_PAD;
+    real *sM = sU + pad4(NE * G::template slots<PAD>() * V);
     real *sC = sM + pad4(NE * NSP * MS);
     real *sD = sC + pad4(NE * NFP * V);
     real *sF = sD + (VISC ? pad4(NE * NFP * V) : 0);   // [j][k][s][v]
@@ -866,7 +875,7 @@ k_flux(const KArgs<real> a) {
         }
     }
     load_ops(a, sOp, N);
-    load_state_rows<N, V, false>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
+    load_state_rows<N, V, PAD>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
     __syncthreads();
 
@@ -877,7 +886,7 @@ k_flux(const KArgs<real> a) {
         if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         real uL[V];
-        interp_line<D, N, V, false>(sU, j, f, Lm, Lp, uL);
+        interp_line<D, N, V, PAD>(sU, j, f, Lm, Lp, uL);
         real ub[V], uRp[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) uRp[v] = uR[it][v];
@@ -928,7 +937,7 @@ k_flux(const KArgs<real> a) {
         const int j = w / NSP, s = w % NSP;
         const real *M = sM + (j * NSP + s) * MS;
         real uu[V];
-        ld_v<V>(sU + G::template slot<false>(j * NSP + s) * V, uu);
+        ld_v<V>(sU + G::template slot<PAD>(j * NSP + s) * V, uu);
         real F[D][V];
         flux_inv<D>(uu, a.gamma - real(1), F);
         if (VISC) {
@@ -947,7 +956,7 @@ k_flux(const KArgs<real> a) {
 #pragma unroll
                 for (int m = 0; m < N; ++m) {
                     real x[V];
-                    ld_v<V>(sU + G::template slot<false>(q0 + m * st) * V, x);
+                    ld_v<V>(sU + G::template slot<PAD>(q0 + m * st) * V, x);
                     const real c = row[m];
 #pragma unroll
                     for (int v = 0; v < V; ++v) Gk[k][v] += c * x[v];
@@ -1020,7 +1029,7 @@ k_flux(const KArgs<real> a) {
         }
         const real iJ = sM[(j * NSP + s) * MS + D * D];
         const int64_t g = (e * NSP + s) * V;
-        real *su = sU + G::template slot<false>(j * NSP + s) * V;
+        real *su = sU + G::template slot<PAD>(j * NSP + s) * V;
         real u0[V], un[V], R[V];
         ld_v<V>(su, u0);
 #pragma unroll
@@ -1075,7 +1084,7 @@ k_flux(const KArgs<real> a) {
         if (w >= ne * NFP || pt[it] < 0) continue;
         const int j = w / NFP, f = w % NFP;
         real uf[V];
-        interp_line<D, N, V, false>(sU, j, f, Lm, Lp, uf);
+        interp_line<D, N, V, PAD>(sU, j, f, Lm, Lp, uf);
         st_v<V>(a.UFout + (int64_t)pt[it] * V, uf);
     }
 }
@@ -1418,13 +1427,13 @@ size_t smem_bytes(int kind, bool visc) {
     using G = Geo<D, N>;
     constexpr int NE = G::NE, NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS;
     size_t n = ops_slots(N);
-    constexpr int PR = G::PROWS;   // k_grad uses the row-padded layout
+    constexpr bool GP = G::GRAD_PAD, FP = G::FLUX_PAD;
     if (kind == K_FLUX) {
-        n += pad4(NE * NSP * V) + pad4(NE * NSP * MS) + pad4(NE * NFP * V) * (visc ? 2 : 1) +
-             pad4(NE * D * NSP * V);
+        n += pad4(NE * G::template slots<FP>() * V) + pad4(NE * NSP * MS) +
+             pad4(NE * NFP * V) * (visc ? 2 : 1) + pad4(NE * D * NSP * V);
     } else if (kind == K_GRAD) {
-        n += pad4(NE * PR * V) + pad4(NE * NSP * MS) + 2 * pad4(NE * NFP * V) +
-             pad4(NE * NSP * D * V + NE * (NSP / N) * V);
+        n += pad4(NE * G::template slots<GP>() * V) + pad4(NE * NSP * MS) + 2 * pad4(NE * NFP * V) +
+             pad4(NE * NSP * D * V + (GP ? NE * (NSP / N) * V : 0));
     } else if (kind == K_INTERP) {
         n += pad4(NE * NSP * V);
     }
