@@ -144,9 +144,9 @@ NCU_TRAFFIC = {
     # dram__bytes_read.sum + dram__bytes_write.sum per element of one stage launch, ncu
     # --set full on the 8-airfoil case (243,854 quads; see profiles/k_flux_airfoil8_full.md),
     # scaled to a launch by the element count
-    "175c2c4449899d311e15f5af07aa5d44cf3210159064cba998be789c04534ed5":
-        {"flux_bytes_per_elem": (315.179776e6 + 149.26464e6) / 243854,
-         "grad_bytes_per_elem": (250.00448e6 + 45.308672e6) / 243854},
+    "27cb25267663f2302c003941030f01c1edb87b8d534c2a1fdbedf362bd20cbd4":
+        {"flux_bytes_per_elem": (315.181568e6 + 149.768192e6) / 243854,
+         "grad_bytes_per_elem": (249.938432e6 + 45.308928e6) / 243854},
 }
 
 

@@ -580,20 +580,22 @@ __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const 
 #define FR_MINB_GRAD_2D_F32 8
 #endif
 // 3-D FP32 (TGV p=3, tandem cylinders p=4): flux kernel best at 3 CTAs for
-// p <= 3 and 4 for p = 4, gradient kernel at 4.
+// p <= 3 and 4 for p = 4; gradient kernel at 5 for p >= 3 (with the
+// parity-padded shared layout), 4 below.
 #ifndef FR_MINB_FLUX_3D_F32
 #define FR_MINB_FLUX_3D_F32 0
 #endif
 #ifndef FR_MINB_GRAD_3D_F32
-#define FR_MINB_GRAD_3D_F32 4
+#define FR_MINB_GRAD_3D_F32 0
 #endif
 template <int D, typename real, bool GRAD = false, int N = 4>
 struct MinBlocks {
     static constexpr int flux3 = FR_MINB_FLUX_3D_F32 > 0 ? FR_MINB_FLUX_3D_F32 : (N >= 5 ? 4 : 3);
+    static constexpr int grad3 = FR_MINB_GRAD_3D_F32 > 0 ? FR_MINB_GRAD_3D_F32 : (N >= 4 ? 5 : 4);
     static constexpr int value =
         sizeof(real) == 8 ? 1
         : (D == 2 ? (GRAD ? FR_MINB_GRAD_2D_F32 : FR_MINB_FLUX_2D_F32)
-                  : (GRAD ? FR_MINB_GRAD_3D_F32 : flux3));
+                  : (GRAD ? grad3 : flux3));
 };
 
 // --------------------------------------------------------------------------
