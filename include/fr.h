@@ -220,7 +220,7 @@ fr_status fr_forces(fr_solver *solver, int inst, double *mean_force);
  * w_i J_i R_i per variable (zero to round-off on periodic meshes). */
 fr_status fr_conservation(fr_solver *solver, int inst, double *sums);
 /* Integral of the conserved variables over the instance (FP64), and the
- * number of non-finite state values (all instances) in *n_nonfinite. */
+ * number of non-finite state values of that instance in *n_nonfinite. */
 fr_status fr_integral(fr_solver *solver, int inst, double *sums, int64_t *n_nonfinite);
 
 /* Allocation-free variant of fr_integral (the paper has no counterpart: it is
