@@ -154,3 +154,36 @@ def test_tandem_candidate_full_size_sampled_parity():
     sols["fp32"].rk_step(3)
     _, bad = sols["fp32"].integral(0)
     assert bad == 0
+
+
+def test_airfoil_sponge_candidate_full_size_parity():
+    """The smallest candidate of the variable-degree airfoil poll (about 8k
+    curved quads; p = 3 within 4 chords, 2 to 8, 1 to 12, 0 beyond): the
+    whole residual against the variable-degree oracle, FP64 and FP32."""
+    from oracle.fr_var import VarFRDiscretisation
+    from oracle.physics import NavierStokes
+    from paper_2312_14167_gb300 import fr
+    meshes = M.airfoil_batch(32, seed=2312)
+    m = min(meshes, key=lambda mm: mm.n_elem)
+    ep = M.sponge_degrees(m, (0.5, 0.0), (4.0, 8.0, 12.0), (3, 2, 1, 0))
+    assert set(np.unique(ep)) == {0, 1, 2, 3}
+    case = FC.Case("airfoil", [m], 3, True, 1.0 / 23000.0, 0.2, dt=FC.cfl_dt([m], 0.2, 3))
+    ph = NavierStokes(2, gamma=FC.GAMMA, mu=case.mu, prandtl=FC.PR, viscous=True, rho_inf=1.0,
+                      v_inf=case.v_inf, p_inf=case.p_inf)
+    d = VarFRDiscretisation(m, ep, ph)
+    u = FC.initial_state(case, d.sol_coords())
+    R, mag = d.residual(u, magnitude=True)
+    s64 = fr.Solver([fr.Mesh(m, ep)], FC.lib_config(case, "fp64"))
+    s64.set_state(0, u)
+    tol = max(1e-12, 16 * EPS64 * np.linalg.norm(mag) / np.linalg.norm(R))
+    err = FC.rel_l2(s64.residual(0), R)
+    print(f"sponge candidate fp64: {err:.3e} (tol {tol:.3e})")
+    assert err < tol
+    s32 = fr.Solver([fr.Mesh(m, ep)], FC.lib_config(case, "fp32"))
+    s32.set_state(0, u)
+    u32 = u.astype(np.float32).astype(np.float64)
+    R32, mag32 = d.residual(u32, magnitude=True)
+    err32 = FC.rel_l2(s32.residual(0), R32)
+    bound = 16 * EPS32 * np.linalg.norm(mag32) / np.linalg.norm(R32)
+    print(f"sponge candidate fp32: {err32:.3e} (bound {bound:.3e})")
+    assert err32 < bound
