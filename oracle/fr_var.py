@@ -132,7 +132,7 @@ def projection_matrix(mesh, refs, e, face, e2, face2, shift, nq=8):
 
 class VarFRDiscretisation:
     """FR residual du/dt on a mesh whose element e has degree elem_p[e]
-    (1..4 here; the operators are defined for any degree >= 0)."""
+    (0..4 in the tests; the operators are defined for any degree >= 0)."""
 
     def __init__(self, mesh, elem_p, phys, br2_eta=None, viscous_scheme="br2", ldg_beta=0.5,
                  ldg_tau=0.1):

@@ -205,7 +205,9 @@ class BatchedPollEvaluator:
     force, design) -> float`` turns the observer level and the mean wall force
     into the objective.  Each call runs ``n_transient`` steps, resets the
     observers, runs ``n_average`` steps and reads the OASPL (running-mean
-    reading of Eqs. 11-12) and the time-mean wall force of every candidate."""
+    reading of Eqs. 11-12) and the time-mean wall force of every candidate.
+    ``p`` is one degree for every element, or a callable mesh -> degree per
+    element (the far-field sponge zones of Sec. 5.1)."""
 
     def __init__(self, make_mesh, p: int, config, n_transient: int, n_average: int, start,
                  objective, p_ref: float = 2e-5, p_scale: float = 1.0, mean_mode: int = 0):
@@ -220,7 +222,7 @@ class BatchedPollEvaluator:
         if not designs:
             return []
         meshes = [self.make_mesh(d) for d in designs]
-        fms = [fr.Mesh(m, self.p) for m in meshes]
+        fms = [fr.Mesh(m, self.p(m) if callable(self.p) else self.p) for m in meshes]
         sol = fr.Solver(fms, self.cfg)
         ids = []
         for i, (m, fm) in enumerate(zip(meshes, fms)):

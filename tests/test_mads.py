@@ -133,3 +133,8 @@ def test_batched_poll_evaluator_runs_a_poll_on_the_gpu():
                                    p_scale=101325 * 1.4 * 0.04)
     vals = ev([np.array([0.02, 0.12]), np.array([0.03, 0.10]), np.array([0.01, 0.14])])
     assert len(vals) == 3 and all(np.isfinite(vals))
+    # the same poll on grids with a lower-degree far field (a degree per element)
+    ev2 = mads.BatchedPollEvaluator(make_mesh, lambda m: M.sponge_degrees(m, (0.5, 0.0), (2.0, 6.0), (3, 2, 1)),
+                                    cfg, 5, 20, start, objective, p_scale=101325 * 1.4 * 0.04)
+    vals2 = ev2([np.array([0.02, 0.12]), np.array([0.03, 0.10])])
+    assert len(vals2) == 2 and all(np.isfinite(vals2))
