@@ -532,7 +532,7 @@ def run_gpu(args):
             sol.set_state(i, u)
         sol.rk_step(1)
         for i in range(len(fms)):
-            outs[i][...] = sol.get_state(i)
+            sol.get_state(i, out=outs[i])
     sol.synchronize()
     e2e_sec = time.perf_counter() - t0
     e2e_val = NSPT * STAGES * n_e2e / e2e_sec * (NSPT_all / NSPT)
@@ -574,7 +574,8 @@ def run_gpu(args):
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes,
                         "how": "per step: fr_set_state of every candidate from pinned FP64 host "
-                               "arrays, fr_rk_step(1), fr_get_state of every candidate"},
+                               "arrays, fr_rk_step(1), fr_get_state of every candidate into pinned "
+                               "FP64 host arrays"},
                 "gpu_launches": int(launches),
                 "clocks": clocks,
                 "fp64_single_instance": {"value": fp64_val, "unit": UNIT,

@@ -232,15 +232,24 @@ class Solver:
             raise ValueError("state shape")
         _check(lib().fr_set_state(self.handle, inst, _dptr(u)), "fr_set_state")
 
-    def get_state(self, inst):
-        m = self.meshes[inst]
-        out = np.empty(m.state_shape + (self.V,))
+    def _out(self, inst, out):
+        shape = self.meshes[inst].state_shape + (self.V,)
+        if out is None:
+            return np.empty(shape)
+        if (not isinstance(out, np.ndarray) or out.dtype != np.float64 or out.shape != shape
+                or not out.flags.c_contiguous or not out.flags.writeable):
+            raise ValueError(f"out must be a writeable C-contiguous float64 array of shape {shape}")
+        return out
+
+    def get_state(self, inst, out=None):
+        """FP64 state of one instance; ``out`` (optional) is written in place,
+        e.g. a pinned host buffer so that the copy runs at full link speed."""
+        out = self._out(inst, out)
         _check(lib().fr_get_state(self.handle, inst, _dptr(out)), "fr_get_state")
         return out
 
-    def residual(self, inst):
-        m = self.meshes[inst]
-        out = np.empty(m.state_shape + (self.V,))
+    def residual(self, inst, out=None):
+        out = self._out(inst, out)
         _check(lib().fr_residual(self.handle, inst, _dptr(out)), "fr_residual")
         return out
 

@@ -75,6 +75,10 @@ def test_no_op_and_argument_errors():
     sol.set_state(0, u)
     sol.rk_step(0)                                   # no steps: state unchanged
     assert np.array_equal(sol.get_state(0), u)
+    buf = np.empty_like(u)                           # caller-provided output, written in place
+    assert sol.get_state(0, out=buf) is buf and np.array_equal(buf, u)
+    with pytest.raises(ValueError):
+        sol.get_state(0, out=np.empty(u.shape, dtype=np.float32))
     # no instance 1: the binding's list index refuses it, and so does the C ABI
     with pytest.raises(IndexError):
         sol.set_state(1, u)
