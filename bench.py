@@ -517,22 +517,20 @@ def run_gpu(args):
     # end to end through the C ABI: every step uploads the FP64 state of all
     # candidates from pinned host memory, advances one step and reads the state back
     sol = fr.Solver(fms, cfg32)
-    pinned = [torch.empty(u.shape, dtype=torch.float64, pin_memory=True).numpy() for u in states]
-    outs = [torch.empty(u.shape, dtype=torch.float64, pin_memory=True).numpy() for u in states]
-    for p_, u in zip(pinned, states):
-        p_[...] = u
+    n_all = sum(u.size for u in states)
+    pinned = torch.empty(n_all, dtype=torch.float64, pin_memory=True).numpy()
+    outs = torch.empty(n_all, dtype=torch.float64, pin_memory=True).numpy()
+    pinned[...] = np.concatenate([u.reshape(-1) for u in states])
     n_e2e = max(3, min(args.steps, 10))
-    for i, u in enumerate(pinned):
-        sol.set_state(i, u)
+    sol.set_states(pinned)
     sol.rk_step(1)
+    sol.get_states(out=outs)
     sol.synchronize()
     t0 = time.perf_counter()
     for _ in range(n_e2e):
-        for i, u in enumerate(pinned):
-            sol.set_state(i, u)
+        sol.set_states(pinned)
         sol.rk_step(1)
-        for i in range(len(fms)):
-            sol.get_state(i, out=outs[i])
+        sol.get_states(out=outs)
     sol.synchronize()
     e2e_sec = time.perf_counter() - t0
     e2e_val = NSPT * STAGES * n_e2e / e2e_sec * (NSPT_all / NSPT)
@@ -573,9 +571,9 @@ def run_gpu(args):
                 "cpu_baseline": cpu_base,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": state_bytes,
                         "d2h_bytes_per_step": state_bytes,
-                        "how": "per step: fr_set_state of every candidate from pinned FP64 host "
-                               "arrays, fr_rk_step(1), fr_get_state of every candidate into pinned "
-                               "FP64 host arrays"},
+                        "how": "per step: fr_set_states (every candidate, from one pinned FP64 "
+                               "host array), fr_rk_step(1), fr_get_states into one pinned FP64 "
+                               "host array"},
                 "gpu_launches": int(launches),
                 "clocks": clocks,
                 "fp64_single_instance": {"value": fp64_val, "unit": UNIT,

@@ -170,9 +170,20 @@ fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, int n_inst,
                            void *stream);
 void fr_solver_destroy(fr_solver *solver);
 
-/* Copy one instance's state (host FP64 [elem][sp][var]) in / out. */
+/* Copy one instance's state (host FP64 [elem][sp][var]) in / out.  Both
+ * synchronise the solver's stream. */
 fr_status fr_set_state(fr_solver *solver, int inst, const double *u);
 fr_status fr_get_state(fr_solver *solver, int inst, double *u);
+/* The states of all instances at once: u holds instance 0's state, then
+ * instance 1's, ... (each in the layout of fr_set_state), sum over instances
+ * of n_sol_points * V doubles.  The copies and conversions of all instances
+ * are queued back to back and the stream is synchronised once, which is what
+ * a poll evaluator that moves every candidate each step wants; with pinned
+ * host memory the copies run at the host link's speed.  Same results as one
+ * fr_set_state / fr_get_state per instance.  Errors: FR_ERR_INVALID_ARG
+ * (null pointer), FR_ERR_CUDA. */
+fr_status fr_set_states(fr_solver *solver, const double *u);
+fr_status fr_get_states(fr_solver *solver, double *u);
 
 /* du/dt of the current state of instance ``inst`` at its solution points
  * (host FP64 [elem][sp][var]): the FR residual of Sec. 2.3 applied to

@@ -887,26 +887,28 @@ extern "C" void fr_solver_destroy(fr_solver *s) {
     delete s;
 }
 
-extern "C" fr_status fr_set_state(fr_solver *s, int inst, const double *u) {
-    fr_status st = check_inst(s, inst);
-    if (st != FR_OK) return st;
-    if (!u) { set_error("null state"); return FR_ERR_INVALID_ARG; }
+namespace {
+
+// Enqueue the upload of one instance's FP64 host state (the ABI's element
+// order) and the derivation of its face values; no synchronisation.  An
+// instance spread over several degree groups is reordered on the host into
+// `tmp`, which must stay alive until the stream has been synchronised.
+fr_status enqueue_upload(fr_solver *s, int inst, const double *u, std::vector<double> &tmp) {
     const int V = s->V;
     const size_t n = (size_t)s->inst_nsp[inst] * V;
     if (!spread(s, inst)) {
         FR_CK(cudaMemcpyAsync(s->stage64, u, n * 8, cudaMemcpyHostToDevice, s->stream));
     } else {
         // host reorder: element order -> group blocks
-        std::vector<double> h(n);
+        tmp.resize(n);
         std::vector<int64_t> blk(s->grp.size());
         for (size_t g = 0; g < s->grp.size(); ++g) blk[g] = stage_block(s, inst, (int)g);
         for (size_t e = 0; e < s->egroup[inst].size(); ++e) {
             const int g = s->egroup[inst][e];
             const size_t cnt = (size_t)s->grp[g].nsp * V;
-            std::memcpy(&h[blk[g] + s->elocal[inst][e] * cnt], u + s->esp[inst][e] * V, cnt * 8);
+            std::memcpy(&tmp[blk[g] + s->elocal[inst][e] * cnt], u + s->esp[inst][e] * V, cnt * 8);
         }
-        FR_CK(cudaMemcpyAsync(s->stage64, h.data(), n * 8, cudaMemcpyHostToDevice, s->stream));
-        FR_CK(cudaStreamSynchronize(s->stream));   // h leaves scope
+        FR_CK(cudaMemcpyAsync(s->stage64, tmp.data(), n * 8, cudaMemcpyHostToDevice, s->stream));
     }
     for (size_t g = 0; g < s->grp.size(); ++g) {
         const Group &G = s->grp[g];
@@ -928,11 +930,14 @@ extern "C" fr_status fr_set_state(fr_solver *s, int inst, const double *u) {
         FR_CK(launch(s, in));
     }
     FR_CK(mortar(s, 0, s->parity, s->moff[inst], s->mcnt[inst]));
-    FR_CK(cudaStreamSynchronize(s->stream));
     return FR_OK;
 }
 
-static fr_status copy_out(fr_solver *s, int inst, int src, double *u) {
+// Enqueue the FP64 conversion of one instance's state (src 0) or residual
+// (src 1) and its download to u; no synchronisation.  An instance spread over
+// several degree groups lands in `tmp` and is put in element order by
+// finish_download once the stream has been synchronised.
+fr_status enqueue_download(fr_solver *s, int inst, int src, double *u, std::vector<double> &tmp) {
     const int V = s->V;
     const size_t n = (size_t)s->inst_nsp[inst] * V;
     for (size_t g = 0; g < s->grp.size(); ++g) {
@@ -950,19 +955,77 @@ static fr_status copy_out(fr_solver *s, int inst, int src, double *u) {
     }
     if (!spread(s, inst)) {
         FR_CK(cudaMemcpyAsync(u, s->stage64, n * 8, cudaMemcpyDeviceToHost, s->stream));
-        FR_CK(cudaStreamSynchronize(s->stream));
-        return FR_OK;
+    } else {
+        tmp.resize(n);
+        FR_CK(cudaMemcpyAsync(tmp.data(), s->stage64, n * 8, cudaMemcpyDeviceToHost, s->stream));
     }
-    std::vector<double> h(n);
-    FR_CK(cudaMemcpyAsync(h.data(), s->stage64, n * 8, cudaMemcpyDeviceToHost, s->stream));
-    FR_CK(cudaStreamSynchronize(s->stream));
+    return FR_OK;
+}
+
+void finish_download(const fr_solver *s, int inst, const std::vector<double> &tmp, double *u) {
+    if (!spread(s, inst)) return;
+    const int V = s->V;
     std::vector<int64_t> blk(s->grp.size());
     for (size_t g = 0; g < s->grp.size(); ++g) blk[g] = stage_block(s, inst, (int)g);
     for (size_t e = 0; e < s->egroup[inst].size(); ++e) {
         const int g = s->egroup[inst][e];
         const size_t cnt = (size_t)s->grp[g].nsp * V;
-        std::memcpy(u + s->esp[inst][e] * V, &h[blk[g] + s->elocal[inst][e] * cnt], cnt * 8);
+        std::memcpy(u + s->esp[inst][e] * V, &tmp[blk[g] + s->elocal[inst][e] * cnt], cnt * 8);
     }
+}
+
+}  // namespace
+
+extern "C" fr_status fr_set_state(fr_solver *s, int inst, const double *u) {
+    fr_status st = check_inst(s, inst);
+    if (st != FR_OK) return st;
+    if (!u) { set_error("null state"); return FR_ERR_INVALID_ARG; }
+    std::vector<double> tmp;
+    st = enqueue_upload(s, inst, u, tmp);
+    if (st != FR_OK) return st;
+    FR_CK(cudaStreamSynchronize(s->stream));
+    return FR_OK;
+}
+
+static fr_status copy_out(fr_solver *s, int inst, int src, double *u) {
+    std::vector<double> tmp;
+    fr_status st = enqueue_download(s, inst, src, u, tmp);
+    if (st != FR_OK) return st;
+    FR_CK(cudaStreamSynchronize(s->stream));
+    finish_download(s, inst, tmp, u);
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_states(fr_solver *s, const double *u) {
+    if (!s || !u) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
+    std::vector<std::vector<double>> tmp(s->n_inst);
+    size_t off = 0;
+    for (int i = 0; i < s->n_inst; ++i) {
+        fr_status st = enqueue_upload(s, i, u + off, tmp[i]);
+        if (st != FR_OK) {
+            cudaStreamSynchronize(s->stream);   // the host buffers above must outlive the copies
+            return st;
+        }
+        off += (size_t)s->inst_nsp[i] * s->V;
+    }
+    FR_CK(cudaStreamSynchronize(s->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_get_states(fr_solver *s, double *u) {
+    if (!s || !u) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
+    std::vector<std::vector<double>> tmp(s->n_inst);
+    std::vector<size_t> off(s->n_inst + 1, 0);
+    for (int i = 0; i < s->n_inst; ++i) off[i + 1] = off[i] + (size_t)s->inst_nsp[i] * s->V;
+    for (int i = 0; i < s->n_inst; ++i) {
+        fr_status st = enqueue_download(s, i, 0, u + off[i], tmp[i]);
+        if (st != FR_OK) {
+            cudaStreamSynchronize(s->stream);
+            return st;
+        }
+    }
+    FR_CK(cudaStreamSynchronize(s->stream));
+    for (int i = 0; i < s->n_inst; ++i) finish_download(s, i, tmp[i], u + off[i]);
     return FR_OK;
 }
 

@@ -28,6 +28,7 @@ STATUS = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_MESH", 3: "FR_ERR_UNSU
 EXPORTED = ["fr_mesh_create", "fr_mesh_create_varp", "fr_mesh_degrees", "fr_mesh_destroy",
             "fr_mesh_info", "fr_mesh_sol_coords",
             "fr_workspace_bytes", "fr_solver_create", "fr_solver_destroy", "fr_set_state",
+            "fr_set_states", "fr_get_states",
             "fr_get_state", "fr_residual", "fr_rk_step", "fr_probe_add", "fr_probe_pressure",
             "fr_probe_history",
             "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
@@ -97,6 +98,8 @@ def lib():
     L.fr_solver_destroy.restype = None
     L.fr_set_state.argtypes = [P, I, dp]
     L.fr_get_state.argtypes = [P, I, dp]
+    L.fr_set_states.argtypes = [P, dp]
+    L.fr_get_states.argtypes = [P, dp]
     L.fr_residual.argtypes = [P, I, dp]
     L.fr_rk_step.argtypes = [P, I]
     L.fr_probe_add.argtypes = [P, I, dp, C.POINTER(I)]
@@ -246,6 +249,30 @@ class Solver:
         e.g. a pinned host buffer so that the copy runs at full link speed."""
         out = self._out(inst, out)
         _check(lib().fr_get_state(self.handle, inst, _dptr(out)), "fr_get_state")
+        return out
+
+    def state_sizes(self):
+        """Number of FP64 values of each instance's state."""
+        return [int(np.prod(m.state_shape)) * self.V for m in self.meshes]
+
+    def set_states(self, u):
+        """All instances at once from one flat FP64 array (instance after
+        instance), one synchronisation (fr_set_states)."""
+        u = np.ascontiguousarray(u, dtype=np.float64).reshape(-1)
+        if u.size != sum(self.state_sizes()):
+            raise ValueError("state size")
+        _check(lib().fr_set_states(self.handle, _dptr(u)), "fr_set_states")
+
+    def get_states(self, out=None):
+        """All instances' states into one flat FP64 array (``out`` written in
+        place when given, e.g. pinned host memory); returns it."""
+        n = sum(self.state_sizes())
+        if out is None:
+            out = np.empty(n)
+        elif (not isinstance(out, np.ndarray) or out.dtype != np.float64 or out.size != n
+              or not out.flags.c_contiguous or not out.flags.writeable):
+            raise ValueError(f"out must be a writeable C-contiguous float64 array of {n} values")
+        _check(lib().fr_get_states(self.handle, _dptr(out)), "fr_get_states")
         return out
 
     def residual(self, inst, out=None):

@@ -230,3 +230,16 @@ def test_batch_of_variable_and_uniform_meshes_of_several_degrees():
         for _ in range(2):
             ur = T.lsrk45_step(d.residual, ur, 1e-4)
         assert _rel(sol.get_state(i).reshape(-1, 4), ur) < 1e-12
+    # all instances in one call each way: the same values as one call per instance
+    flat = sol.get_states()
+    assert np.array_equal(flat, np.concatenate([sol.get_state(i).reshape(-1) for i in range(3)]))
+    new = np.concatenate([(u * 1.01).reshape(-1) for u in us])
+    sol.set_states(new)
+    off = 0
+    for i, u in enumerate(us):
+        assert np.array_equal(sol.get_state(i).reshape(-1), new[off:off + u.size])
+        off += u.size
+    sol.set_state(1, us[1].reshape(sol.meshes[1].state_shape + (4,)))
+    assert np.array_equal(sol.get_states()[us[0].size:us[0].size + us[1].size], us[1].reshape(-1))
+    with pytest.raises(ValueError):
+        sol.set_states(new[:-1])
