@@ -548,7 +548,10 @@ fr_status residual_into_res(fr_solver *s, int inst, int mode) {
 
 fr_status reduce_integral(fr_solver *s, int inst, int src, double *out_sums, double *out_bad) {
     const int G = (int)s->grp.size();
-    FR_CK(cudaMemsetAsync(s->partials, 0, (size_t)G * kPartialBlocks * (2 * s->V + 1) * 8, s->stream));
+    // the partial-sum blocks are shared out among the degree groups, so the
+    // ordered reduction reads kPartialBlocks slots whatever the number of groups
+    const int per = std::max(1, kPartialBlocks / G);
+    FR_CK(cudaMemsetAsync(s->partials, 0, (size_t)G * per * (2 * s->V + 1) * 8, s->stream));
     for (int g = 0; g < G; ++g) {
         if (s->grp[g].ne[inst] <= 0) continue;
         Launch in;
@@ -557,13 +560,13 @@ fr_status reduce_integral(fr_solver *s, int inst, int src, double *out_sums, dou
         in.elem0 = s->grp[g].off[inst];
         in.n_elem = s->grp[g].ne[inst];
         in.integral_src = src;
-        in.partial_slot = (int64_t)g * kPartialBlocks;
-        in.grid = kPartialBlocks;
+        in.partial_slot = (int64_t)g * per;
+        in.grid = per;
         FR_CK(launch(s, in));
     }
     Launch rd;
     rd.kind = frk::K_REDUCE;
-    rd.n_partials = (int64_t)G * kPartialBlocks;
+    rd.n_partials = (int64_t)G * per;
     FR_CK(launch(s, rd));
     std::vector<double> h(s->V + 1);
     FR_CK(cudaMemcpyAsync(h.data(), s->reduce_out, h.size() * 8, cudaMemcpyDeviceToHost, s->stream));
