@@ -243,3 +243,13 @@ def test_batch_of_variable_and_uniform_meshes_of_several_degrees():
     assert np.array_equal(sol.get_states()[us[0].size:us[0].size + us[1].size], us[1].reshape(-1))
     with pytest.raises(ValueError):
         sol.set_states(new[:-1])
+    # determinism: a candidate advanced inside the batch (degree groups and
+    # mortar passes shared with the others) is bitwise the candidate alone
+    solo = _solver([(b, eb)], True, "br2", "rusanov", "fp64")
+    u1 = us[1].reshape(sol.meshes[1].state_shape + (4,))
+    solo.set_state(0, u1)
+    sol.set_states(np.concatenate([u.reshape(-1) for u in us]))
+    solo.rk_step(2)
+    sol.rk_step(2)
+    assert np.array_equal(solo.get_state(0), sol.get_state(1))
+    assert np.array_equal(solo.residual(0), sol.residual(1))
