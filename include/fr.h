@@ -207,6 +207,20 @@ fr_status fr_probe_pressure(fr_solver *solver, int probe_id, double *p_latest);
  * *n_out (the device keeps a 4096-sample ring per probe), for spectra of the
  * observer signal (Welch PSD, Secs. 3.2, 4.2, 5.2 figures).  Synchronises. */
 fr_status fr_probe_history(fr_solver *solver, int probe_id, double *out, int max_n, int *n_out);
+/* Checkpoint of everything a step accumulates besides the flow state (which
+ * fr_get_state / fr_set_state save): the number of steps in the current
+ * averaging window, the wall-force sums of every instance, and every probe's
+ * FP64 accumulators and sample ring.  fr_accumulators_size is the number of
+ * doubles (-1 for a null solver).  fr_set_accumulators wants a solver with the
+ * same instances and the same probes added in the same order
+ * (FR_ERR_INVALID_ARG if the probe count differs).  States and accumulators
+ * restored, the following steps, OASPL and probe histories are bitwise those
+ * of an uninterrupted run; the wall-force sums agree to rounding (they are
+ * accumulated with atomic additions, whose order varies from run to run).
+ * Both synchronise. */
+int64_t fr_accumulators_size(const fr_solver *solver);
+fr_status fr_get_accumulators(fr_solver *solver, double *out);
+fr_status fr_set_accumulators(fr_solver *solver, const double *in);
 /* Start a new averaging window: zero all probe and force accumulators. */
 fr_status fr_probe_reset(fr_solver *solver);
 /* OASPL in dB (Sec. 3.1.2, Eqs. 9-12) over the samples since the last reset:

@@ -8,6 +8,7 @@
 // Faces joining two degrees (meshes built by fr_mesh_create_varp) are
 // coupled by the mortar kernels between the group kernels of each stage.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -41,6 +42,14 @@ namespace fr {
 
 thread_local std::string g_last_error;
 void set_error(const std::string &msg) { g_last_error = msg; }
+
+// NVTX range around a public call (visible to nsys / ncu; free without a tool)
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 namespace {
 
@@ -612,6 +621,7 @@ void to_real(std::vector<char> &dst, const std::vector<double> &src) {
 extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, int n_inst,
                                       const fr_config *cfg, void *workspace, size_t ws_bytes,
                                       void *stream) {
+    fr::Range nvtx_range("fr_solver_create");
     if (!out) { set_error("null output pointer"); return FR_ERR_INVALID_ARG; }
     *out = nullptr;
     fr_status st = check_batch(meshes, n_inst, cfg);
@@ -980,6 +990,7 @@ void finish_download(const fr_solver *s, int inst, const std::vector<double> &tm
 }  // namespace
 
 extern "C" fr_status fr_set_state(fr_solver *s, int inst, const double *u) {
+    fr::Range nvtx_range("fr_set_state");
     fr_status st = check_inst(s, inst);
     if (st != FR_OK) return st;
     if (!u) { set_error("null state"); return FR_ERR_INVALID_ARG; }
@@ -1000,6 +1011,7 @@ static fr_status copy_out(fr_solver *s, int inst, int src, double *u) {
 }
 
 extern "C" fr_status fr_set_states(fr_solver *s, const double *u) {
+    fr::Range nvtx_range("fr_set_states");
     if (!s || !u) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
     std::vector<std::vector<double>> tmp(s->n_inst);
     size_t off = 0;
@@ -1016,6 +1028,7 @@ extern "C" fr_status fr_set_states(fr_solver *s, const double *u) {
 }
 
 extern "C" fr_status fr_get_states(fr_solver *s, double *u) {
+    fr::Range nvtx_range("fr_get_states");
     if (!s || !u) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
     std::vector<std::vector<double>> tmp(s->n_inst);
     std::vector<size_t> off(s->n_inst + 1, 0);
@@ -1033,6 +1046,7 @@ extern "C" fr_status fr_get_states(fr_solver *s, double *u) {
 }
 
 extern "C" fr_status fr_get_state(fr_solver *s, int inst, double *u) {
+    fr::Range nvtx_range("fr_get_state");
     fr_status st = check_inst(s, inst);
     if (st != FR_OK) return st;
     if (!u) { set_error("null output"); return FR_ERR_INVALID_ARG; }
@@ -1040,6 +1054,7 @@ extern "C" fr_status fr_get_state(fr_solver *s, int inst, double *u) {
 }
 
 extern "C" fr_status fr_residual(fr_solver *s, int inst, double *r) {
+    fr::Range nvtx_range("fr_residual");
     fr_status st = check_inst(s, inst);
     if (st != FR_OK) return st;
     if (!r) { set_error("null output"); return FR_ERR_INVALID_ARG; }
@@ -1049,6 +1064,7 @@ extern "C" fr_status fr_residual(fr_solver *s, int inst, double *r) {
 }
 
 extern "C" fr_status fr_rk_step(fr_solver *s, int n_steps) {
+    fr::Range nvtx_range("fr_rk_step");
     if (!s || n_steps < 0) { set_error("invalid fr_rk_step arguments"); return FR_ERR_INVALID_ARG; }
     const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
     int64_t total = 0;
@@ -1086,6 +1102,7 @@ extern "C" fr_status fr_rk_step(fr_solver *s, int n_steps) {
 extern "C" int64_t fr_last_launch_count(const fr_solver *s) { return s ? s->last_launches : -1; }
 
 extern "C" fr_status fr_profile_steps(fr_solver *s, int n_steps, double *ms, int64_t *count) {
+    fr::Range nvtx_range("fr_profile_steps");
     if (!s || n_steps <= 0 || !ms || !count) { set_error("invalid fr_profile_steps arguments"); return FR_ERR_INVALID_ARG; }
     const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
     s->prof.clear();
@@ -1200,6 +1217,52 @@ extern "C" fr_status fr_probe_history(fr_solver *s, int probe_id, double *out, i
     return FR_OK;
 }
 
+// Accumulator checkpoint: [steps in the window, number of probes, wall-force
+// sums n_inst x 3, probe accumulators n_probe x 16, sample rings n_probe x kHistLen]
+extern "C" int64_t fr_accumulators_size(const fr_solver *s) {
+    if (!s) return -1;
+    return 2 + (int64_t)s->n_inst * 3 + (int64_t)s->n_probe * (int64_t)(sizeof(frk::ProbeAcc) / 8) +
+           (int64_t)s->n_probe * frk::kHistLen;
+}
+
+extern "C" fr_status fr_get_accumulators(fr_solver *s, double *out) {
+    if (!s || !out) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
+    const size_t na = sizeof(frk::ProbeAcc) / 8;
+    out[0] = (double)s->steps_since_reset;
+    out[1] = (double)s->n_probe;
+    double *f = out + 2, *pa = f + (size_t)s->n_inst * 3, *ph = pa + (size_t)s->n_probe * na;
+    FR_CK(cudaMemcpyAsync(f, s->force_acc, (size_t)s->n_inst * 3 * 8, cudaMemcpyDeviceToHost, s->stream));
+    if (s->n_probe > 0) {
+        FR_CK(cudaMemcpyAsync(pa, s->pacc, (size_t)s->n_probe * sizeof(frk::ProbeAcc), cudaMemcpyDeviceToHost,
+                              s->stream));
+        FR_CK(cudaMemcpyAsync(ph, s->phist, (size_t)s->n_probe * frk::kHistLen * 8, cudaMemcpyDeviceToHost,
+                              s->stream));
+    }
+    FR_CK(cudaStreamSynchronize(s->stream));
+    return FR_OK;
+}
+
+extern "C" fr_status fr_set_accumulators(fr_solver *s, const double *in) {
+    if (!s || !in) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
+    if (in[1] != (double)s->n_probe || !(in[0] >= 0.0)) {
+        set_error("accumulator checkpoint is for " + std::to_string((int64_t)in[1]) + " probes, the solver has " +
+                  std::to_string(s->n_probe));
+        return FR_ERR_INVALID_ARG;
+    }
+    const size_t na = sizeof(frk::ProbeAcc) / 8;
+    const double *f = in + 2, *pa = f + (size_t)s->n_inst * 3, *ph = pa + (size_t)s->n_probe * na;
+    FR_CK(cudaMemcpyAsync(s->force_acc, f, (size_t)s->n_inst * 3 * 8, cudaMemcpyHostToDevice, s->stream));
+    if (s->n_probe > 0) {
+        FR_CK(cudaMemcpyAsync(s->pacc, pa, (size_t)s->n_probe * sizeof(frk::ProbeAcc), cudaMemcpyHostToDevice,
+                              s->stream));
+        FR_CK(cudaMemcpyAsync(s->phist, ph, (size_t)s->n_probe * frk::kHistLen * 8, cudaMemcpyHostToDevice,
+                              s->stream));
+    }
+    FR_CK(cudaStreamSynchronize(s->stream));
+    s->steps_since_reset = (int64_t)in[0];
+    return FR_OK;
+}
+
 extern "C" fr_status fr_probe_reset(fr_solver *s) {
     if (!s) { set_error("null solver"); return FR_ERR_INVALID_ARG; }
     FR_CK(cudaMemsetAsync(s->pacc, 0, sizeof(frk::ProbeAcc) * kMaxProbes, s->stream));
@@ -1241,6 +1304,7 @@ extern "C" fr_status fr_forces(fr_solver *s, int inst, double *mean_force) {
 }
 
 extern "C" fr_status fr_conservation(fr_solver *s, int inst, double *sums) {
+    fr::Range nvtx_range("fr_conservation");
     fr_status st = check_inst(s, inst);
     if (st != FR_OK) return st;
     if (!sums) { set_error("null output"); return FR_ERR_INVALID_ARG; }
@@ -1250,6 +1314,7 @@ extern "C" fr_status fr_conservation(fr_solver *s, int inst, double *sums) {
 }
 
 extern "C" fr_status fr_integral(fr_solver *s, int inst, double *sums, int64_t *n_nonfinite) {
+    fr::Range nvtx_range("fr_integral");
     fr_status st = check_inst(s, inst);
     if (st != FR_OK) return st;
     if (!sums) { set_error("null output"); return FR_ERR_INVALID_ARG; }

@@ -28,7 +28,8 @@ STATUS = {0: "FR_OK", 1: "FR_ERR_INVALID_ARG", 2: "FR_ERR_MESH", 3: "FR_ERR_UNSU
 EXPORTED = ["fr_mesh_create", "fr_mesh_create_varp", "fr_mesh_degrees", "fr_mesh_destroy",
             "fr_mesh_info", "fr_mesh_sol_coords",
             "fr_workspace_bytes", "fr_solver_create", "fr_solver_destroy", "fr_set_state",
-            "fr_set_states", "fr_get_states",
+            "fr_set_states", "fr_get_states", "fr_accumulators_size", "fr_get_accumulators",
+            "fr_set_accumulators",
             "fr_get_state", "fr_residual", "fr_rk_step", "fr_probe_add", "fr_probe_pressure",
             "fr_probe_history",
             "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
@@ -99,6 +100,10 @@ def lib():
     L.fr_set_state.argtypes = [P, I, dp]
     L.fr_get_state.argtypes = [P, I, dp]
     L.fr_set_states.argtypes = [P, dp]
+    L.fr_accumulators_size.argtypes = [P]
+    L.fr_accumulators_size.restype = C.c_int64
+    L.fr_get_accumulators.argtypes = [P, dp]
+    L.fr_set_accumulators.argtypes = [P, dp]
     L.fr_get_states.argtypes = [P, dp]
     L.fr_residual.argtypes = [P, I, dp]
     L.fr_rk_step.argtypes = [P, I]
@@ -119,7 +124,7 @@ def lib():
     L.fr_last_error.restype = C.c_char_p
     for name in EXPORTED:
         if name not in ("fr_mesh_destroy", "fr_solver_destroy", "fr_workspace_bytes",
-                        "fr_last_launch_count", "fr_last_error"):
+                        "fr_last_launch_count", "fr_last_error", "fr_accumulators_size"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -274,6 +279,18 @@ class Solver:
             raise ValueError(f"out must be a writeable C-contiguous float64 array of {n} values")
         _check(lib().fr_get_states(self.handle, _dptr(out)), "fr_get_states")
         return out
+
+    def get_accumulators(self):
+        """Checkpoint of the observers and wall-force sums (fr_get_accumulators)."""
+        out = np.empty(int(lib().fr_accumulators_size(self.handle)))
+        _check(lib().fr_get_accumulators(self.handle, _dptr(out)), "fr_get_accumulators")
+        return out
+
+    def set_accumulators(self, acc):
+        acc = np.ascontiguousarray(acc, dtype=np.float64)
+        if acc.size != int(lib().fr_accumulators_size(self.handle)):
+            raise ValueError("accumulator checkpoint size")
+        _check(lib().fr_set_accumulators(self.handle, _dptr(acc)), "fr_set_accumulators")
 
     def residual(self, inst, out=None):
         out = self._out(inst, out)

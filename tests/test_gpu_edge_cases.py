@@ -136,3 +136,45 @@ def test_checkpoint_resume_is_bitwise_equal(rk):
     resumed.rk_step(3)
     for i in range(2):
         assert np.array_equal(resumed.get_state(i), full.get_state(i))
+
+
+def test_checkpoint_resume_with_observers_is_bitwise_equal():
+    """States (fr_get_state) and accumulators (fr_get_accumulators) saved
+    mid-window and restored into a fresh solver with the same probes: the
+    state, OASPL and probe history after the remaining steps are bitwise
+    those of the uninterrupted run; the mean wall force agrees to rounding
+    (its sums use atomic additions, whose order varies between runs)."""
+    from paper_2312_14167_gb300 import fr
+    case = FC.airfoil_case(n_inst=2)
+    us = [FC.initial_state(case, FC.oracle_disc(case, i).sol_coords(), i) for i in range(2)]
+
+    def fresh():
+        sol = FC.lib_solver(case, "fp32")
+        for i in range(2):
+            sol.set_state(i, us[i])
+        ids = [sol.probe_add(i, np.asarray(case.meshes[i].info["probe"], float)) for i in range(2)]
+        sol.probe_reset()
+        return sol, ids
+
+    full, ids = fresh()
+    full.rk_step(6)
+    first, ids1 = fresh()
+    first.rk_step(3)
+    states = [first.get_state(i) for i in range(2)]
+    acc = first.get_accumulators()
+    assert acc.size == fr.lib().fr_accumulators_size(first.handle) and acc[0] == 3 and acc[1] == 2
+    resumed = FC.lib_solver(case, "fp32")
+    ids2 = [resumed.probe_add(i, np.asarray(case.meshes[i].info["probe"], float)) for i in range(2)]
+    for i in range(2):
+        resumed.set_state(i, states[i])
+    resumed.set_accumulators(acc)
+    resumed.rk_step(3)
+    assert resumed.oaspl(ids2) == full.oaspl(ids)
+    for i in range(2):
+        assert np.array_equal(resumed.get_state(i), full.get_state(i))
+        assert np.allclose(resumed.forces(i), full.forces(i), rtol=1e-12, atol=0.0)
+        assert np.array_equal(resumed.probe_history(ids2[i]), full.probe_history(ids[i]))
+    lone = FC.lib_solver(case, "fp32")                 # no probes: the checkpoint does not fit
+    assert fr.lib().fr_set_accumulators(lone.handle, fr._dptr(acc)) == 1
+    with pytest.raises(ValueError):
+        lone.set_accumulators(acc)

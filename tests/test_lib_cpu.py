@@ -94,6 +94,10 @@ def test_solver_needs_a_device_workspace(fr):
     h = C.c_void_p()
     st = fr.lib().fr_solver_create(C.byref(h), arr, 1, C.byref(cfg), None, 0, None)
     assert st == 7                                   # FR_ERR_WORKSPACE
+    # an aligned pointer with too few bytes is refused by size, also before any device access
+    need = fr.lib().fr_workspace_bytes(arr, 1, C.byref(cfg))
+    st = fr.lib().fr_solver_create(C.byref(h), arr, 1, C.byref(cfg), C.c_void_p(256), need - 1, None)
+    assert st == 7 and b"too small" in fr.lib().fr_last_error()
 
 
 @pytest.mark.parametrize("dim", [2, 3])
