@@ -154,6 +154,28 @@ def vortex_mesh(n: int = 16, jitter: float = 0.0, seed: int = 2312) -> Mesh:
     return periodic_box(2, (n, n), (-5.0, -5.0), (5.0, 5.0), jitter, seed)
 
 
+def curved_periodic_box(n: int, q: int, amp: float = 0.15) -> Mesh:
+    """Periodic (2 pi)^3 box of n^3 hexes, every element curved in all three
+    directions: the map X -> X + amp (sin Y sin Z, sin Z sin X, sin X sin Y)
+    (periodic, so periodic faces still match) sampled at the degree-q node
+    lattice of each element."""
+    b = periodic_box(3, (n, n, n), (0, 0, 0), (2 * np.pi,) * 3)
+
+    def warp(X):
+        s = np.sin(X)
+        return X + amp * np.stack([s[..., 1] * s[..., 2], s[..., 2] * s[..., 0],
+                                   s[..., 0] * s[..., 1]], -1)
+
+    h = 2 * np.pi / n
+    x0 = b.xyz[b.elem_vert].min(axis=1)
+    t = np.linspace(0.0, 1.0, q + 1)
+    lat = np.array([[i, j, k] for k in t for j in t for i in t])      # xi fastest
+    nodes = warp(x0[:, None, :] + h * lat[None])
+    return Mesh(dim=3, xyz=warp(b.xyz), elem_vert=b.elem_vert, face_tag=b.face_tag,
+                periodic_shift=b.periodic_shift, geo_order=q, geo_nodes=nodes,
+                info={"kind": "curved_box"})
+
+
 def tgv_mesh(n: int = 16) -> Mesh:
     """Taylor-Green box [0, 2 pi]^3 with n^3 hexes."""
     two_pi = 2.0 * np.pi
