@@ -75,7 +75,14 @@ typedef int fr_status;
 
 #define FR_FP64 0           /* plain FP64 state, geometry and arithmetic */
 #define FR_FP32 1           /* FP32 state/fluxes/contractions; geometry computed in
-                               FP64 then cast; FP64 probe/force/conservation sums */
+                               FP64 then cast; FP64 probe/force/conservation sums.
+                               The device state is the FP32 perturbation
+                               u - u_ref about the reference state u_ref =
+                               (rho_inf, rho_inf v_inf, p_inf/(gamma-1) +
+                               rho_inf |v_inf|^2 / 2), each component rounded
+                               to FP32, and fluxes are evaluated as
+                               F(u) - F(u_ref); the host sees full FP64 states
+                               (u_ref + the stored perturbation) */
 
 typedef struct fr_mesh fr_mesh;
 typedef struct fr_solver fr_solver;
@@ -98,9 +105,17 @@ typedef struct fr_config {
     int precision;         /* FR_FP64 or FR_FP32 */
     int flux;              /* inviscid interface flux: FR_FLUX_RUSANOV or FR_FLUX_ROE */
     int viscous_scheme;    /* FR_VISC_BR2 or FR_VISC_LDG */
-    int reserved;
+    int check_every;       /* > 0: fr_rk_step scans every instance's state for
+                              NaN/Inf after every check_every-th step and flags
+                              the instances concerned (fr_instance_status); 0: off */
     double ldg_beta;       /* LDG: one-sidedness of the common solution (0.5: upwind) */
     double ldg_tau;        /* LDG: penalty on the solution jump */
+    int flux_reference;    /* FP32: 0 = every element evaluates its fluxes as perturbations
+                              about its own reference state (the state at its first solution
+                              point; accurate near walls, where the flow is far from the free
+                              stream); 1 = about the free stream everywhere (fewer
+                              instructions, larger rounding in wall cells) */
+    int reserved;
 } fr_config;
 
 /* Build one mesh (host, FP64).  The FR discretisation is Huynh's Flux
@@ -211,16 +226,20 @@ fr_status fr_probe_history(fr_solver *solver, int probe_id, double *out, int max
  * fr_get_state / fr_set_state save): the number of steps in the current
  * averaging window, the wall-force sums of every instance, and every probe's
  * FP64 accumulators and sample ring.  fr_accumulators_size is the number of
- * doubles (-1 for a null solver).  fr_set_accumulators wants a solver with the
- * same instances and the same probes added in the same order
- * (FR_ERR_INVALID_ARG if the probe count differs).  States and accumulators
+ * doubles (-1 for a null solver).  The checkpoint starts with a header: steps
+ * in the window, number of probes, number of instances and a fingerprint of
+ * the observers (instance and element of each, in order).
+ * fr_set_accumulators takes the checkpoint and its length n; it wants a
+ * solver with the same instances and the same probes added in the same order
+ * and returns FR_ERR_INVALID_ARG, without reading past n, if n is not this
+ * solver's fr_accumulators_size or the header disagrees.  States and accumulators
  * restored, the following steps, OASPL and probe histories are bitwise those
  * of an uninterrupted run; the wall-force sums agree to rounding (they are
  * accumulated with atomic additions, whose order varies from run to run).
  * Both synchronise. */
 int64_t fr_accumulators_size(const fr_solver *solver);
 fr_status fr_get_accumulators(fr_solver *solver, double *out);
-fr_status fr_set_accumulators(fr_solver *solver, const double *in);
+fr_status fr_set_accumulators(fr_solver *solver, const double *in, int64_t n);
 /* Start a new averaging window: zero all probe and force accumulators. */
 fr_status fr_probe_reset(fr_solver *solver);
 /* OASPL in dB (Sec. 3.1.2, Eqs. 9-12) over the samples since the last reset:
@@ -240,6 +259,17 @@ fr_status fr_probe_stats(fr_solver *solver, int probe_id, double *out4);
  * values): sum over wall flux points of w (p n - tau . n) (the force behind
  * C_D, Sec. 3.1.2), averaged over the completed steps. */
 fr_status fr_forces(fr_solver *solver, int inst, double *mean_force);
+/* Time-mean lift and drag coefficients of instance ``inst`` since the last
+ * reset (Sec. 3.1.2; the objective of Sec. 5.2 penalises them):
+ * C = F . e / (rho_inf |v_inf|^2 a_ref / 2) with F the mean wall force of
+ * fr_forces, e the drag direction v_inf / |v_inf| for C_D and the lift
+ * direction for C_L (2-D: the drag direction turned by +90 degrees; 3-D: the
+ * y axis made orthogonal to the drag direction).  a_ref is the reference
+ * length in 2-D (chord) or area in 3-D (chord x span).  FR_ERR_INVALID_ARG
+ * for a_ref <= 0, a zero free-stream velocity or (3-D) a free stream along y.
+ * Synchronises. */
+fr_status fr_force_coefficients(fr_solver *solver, int inst, double a_ref, double *mean_cl,
+                                double *mean_cd);
 
 /* Conservation check: FP64 compensated sums over the instance of
  * w_i J_i R_i per variable (zero to round-off on periodic meshes). */
@@ -263,15 +293,65 @@ fr_status fr_integral(fr_solver *solver, int inst, double *sums, int64_t *n_nonf
  *  - Limit: the instance may have at most 1024 * 256 * 8 = 2,097,152 solution
  *    points; larger instances get FR_ERR_INVALID_ARG with a message (use
  *    fr_integral for them).
- *  - The first call on a device looks up the array's device address for
- *    that device (once per device, with it current); make that first call
- *    before any stream capture on that device.
+ *  - Every call looks up the array's device address on the current device
+ *    (cudaGetSymbolAddress, with that device current), so a device reset
+ *    between calls is harmless; make the first call on a device before any
+ *    stream capture on it.
  *  - All calls share the one array and it keeps the last call's contents;
  *    each call clears it first.  Calls that overlap on the GPU (other
  *    streams, other threads, other solvers on the same device) race on it:
  *    serialise them.
  *  - Synchronises the solver's stream. */
 fr_status fr_integral_static(fr_solver *solver, int inst, double *sums, int64_t *n_nonfinite);
+
+/* Per-instance health of the batch (failure detection inside the time
+ * loop; the paper's poll treats a failed evaluation as a rejected candidate,
+ * Sec. 2.2).  With cfg.check_every = K > 0, fr_rk_step appends after every
+ * K-th step a scan of the state that sets the flag of each instance holding
+ * a NaN or Inf; a flag stays set until that instance's state is set again
+ * (fr_set_state / fr_set_states).  Instances never interact, so one
+ * instance diverging leaves the others' results unchanged.  Synchronises;
+ * copies the n_inst flags into ``flags`` (may be NULL), the lowest flagged
+ * instance into *first_bad (-1 if none) and returns FR_ERR_NONFINITE if any
+ * instance is flagged, else FR_OK. */
+fr_status fr_instance_status(fr_solver *solver, int32_t *flags, int *first_bad);
+
+/* Autotuner (a service of this library; the paper has no counterpart).  A
+ * solver's stage schedule -- for BR2 batches without mortar faces, one
+ * fused kernel per RK stage or a gradient kernel plus a flux kernel -- the
+ * register level of its stage kernels (FP32: 0 = the default residency,
+ * 1 = one resident CTA fewer per SM and more registers per thread) and, in
+ * FP32, the contraction of the divergence + correction operators (SIMT
+ * sum factorisation, or 3xTF32 tensor-core mma products of every element
+ * line: FP32-level accuracy, FP32 accumulation) are measured on the
+ * solver's own batch: every candidate runs 2 warm-up and 3 timed RK steps
+ * (CUDA events) and the fastest is kept.  The
+ * result is cached in the JSON file cache_path (NULL: no cache) under a key
+ * of the GPU architecture, dimension, degrees, variables, precision,
+ * viscous scheme, interface flux, mortar faces and log2 of the solution
+ * points.  mode 0: use the cached entry if there is one, else measure and
+ * store; 1: always measure and store; 2: use the cached entry if there is
+ * one, else keep the current schedule.  Measuring sets every instance to the
+ * configuration's free stream and advances it: call fr_tune before
+ * fr_set_state (it also clears the probe, force and health accumulators).
+ * choice receives "stage=...;regs=...;contract=...;ms=...;source=..." (and, after a
+ * measurement, ";candidates=..." with every candidate's ms per step).
+ * Synchronises. */
+fr_status fr_tune(fr_solver *solver, const char *cache_path, int mode, char *choice, size_t choice_len);
+/* The solver's current schedule string (as fr_tune writes it) and its
+ * cache key.  Either output may be NULL. */
+fr_status fr_schedule(fr_solver *solver, char *schedule, size_t len, char *key, size_t key_len);
+/* Host-only cache read: the value stored under key in the JSON file
+ * cache_path.  FR_ERR_INVALID_ARG if the file or the key is missing (value
+ * is then the empty string). */
+fr_status fr_tune_lookup(const char *cache_path, const char *key, char *value, size_t len);
+
+/* Measured arithmetic peak of the current GPU's FMA pipes (a service of this
+ * library for roofline fractions of ALU-bound kernels): precision FR_FP64 or
+ * FR_FP32; independent FMA chains in every thread of 8 CTAs per SM, 2 flops
+ * per FMA, the best of 3 timed launches (CUDA events).  Allocates nothing.
+ * Synchronises the device. */
+fr_status fr_alu_peak(int precision, double *flops_per_s);
 
 /* Number of kernel launches issued by the last fr_rk_step call. */
 int64_t fr_last_launch_count(const fr_solver *solver);

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libfr.so")
 
 SOURCES = ["fr_mesh.cpp", "fr_api.cu", "fr_k2_f32.cu", "fr_k2_f64.cu",
-           "fr_k3_f32.cu", "fr_k3_f64.cu"]
+           "fr_k3_f32.cu", "fr_k3_f64.cu", "fr_peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -67,6 +67,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 # FP32 kernels: approximate division / square root (a few ulp)
                 # and flush-to-zero; the FP32 parity tests bound the result
                 cmd = cmd[:1] + ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"] + cmd[1:]
+            if src == "fr_api.cu":
+                cmd = cmd[:1] + ["-Xcompiler", "-fopenmp"] + cmd[1:]
             if src.endswith(".cpp"):
                 cmd = [nvcc, "-x", "cu"] + _flags() + ["-Xcompiler", "-fopenmp", "-c", s, "-o", o]
             jobs.append((src, cmd))

@@ -12,6 +12,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -87,8 +88,12 @@ struct Group {
     int64_t fp_real = 0, n_box_lo = 0, n_box = 0;
     std::vector<int64_t> off, ne;            // per instance
     char *U = nullptr, *R1 = nullptr, *R2 = nullptr, *RES = nullptr, *UF[2] = {nullptr, nullptr};
-    char *FV = nullptr, *MET = nullptr, *NRM = nullptr, *MFLUX = nullptr;
+    char *FV = nullptr, *MET = nullptr, *NRM = nullptr, *MFLUX = nullptr, *DIVREF = nullptr;
+    // fused viscous stage: second (ping-pong) buffer of the inbound gradient
+    // flux parts (the first is FV) and the partner lifting coefficients
+    char *FV2 = nullptr, *LFP = nullptr;
     int32_t *PART = nullptr, *EINST = nullptr, *WALL = nullptr;
+    bool use_divref = false;   // FP32: the reference flux has a residual here
     int n_probe = 0;
     RefElem ref;
 };
@@ -131,15 +136,38 @@ struct fr_solver {
     char *BVREF = nullptr;
     int32_t *BTAG = nullptr;
     double *stage64 = nullptr, *force_acc = nullptr, *partials = nullptr, *reduce_out = nullptr;
+    // FP32: reference state of the perturbation storage (FP32 constants of the
+    // kernels, the FP64 conserved values and pressure, the FP64 reference flux)
+    frk::RefState<float> ref32{};
+    double uref64[5] = {0, 0, 0, 0, 0}, pref64 = 0.0;
+    double vref64[3] = {0, 0, 0};
+    double Fref[3][5] = {};
+    // FP32: sum over each instance's wall points of w n (FP64, host); the
+    // kernels accumulate w ((p - p_r) n - tau n) and fr_forces adds p_r times it
+    std::vector<double> wall_nsum;
     frk::ProbeDesc *probes = nullptr;
     frk::ProbeAcc *pacc = nullptr;
     double *phist = nullptr;
     int n_probe = 0;
     std::vector<int> probe_inst;
+    std::vector<int64_t> probe_elem;   // element (within its degree group) of each observer
     int parity = 0;
     int64_t steps_since_reset = 0;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     int64_t launches_per_step = 0, last_launches = 0;
+    // non-finite scan every check_every steps (cfg.check_every; 0: off)
+    int32_t *FLAGS = nullptr;
+    int64_t steps_since_check = 0;
+    // BR2 stages as one fused kernel (K_STAGE) instead of K_GRAD + K_FLUX
+    bool fused = false;
+    // FP32: fluxes about element-local references (cfg.flux_reference 0) or the free stream
+    bool local_ref = true;
+    // register level of the stage kernels (fr_tune)
+    int regs_level = 0;
+    // FP32: line contractions on the tensor cores (3xTF32 mma.sync; fr_tune)
+    bool tc = false;
+    std::string schedule_source = "default";
+    double schedule_ms = 0.0;
     std::vector<std::unique_ptr<fr_mesh>> host_meshes;   // for probe location
     // per-launch event pairs while fr_profile_steps runs
     bool profiling = false;
@@ -169,6 +197,8 @@ fr_status check_batch(fr_mesh *const *meshes, int n_inst, const fr_config *cfg) 
         }
     }
     if (cfg->rk != FR_RK4 && cfg->rk != FR_LSRK45) { set_error("unknown rk scheme"); return FR_ERR_INVALID_ARG; }
+    if (cfg->check_every < 0) { set_error("check_every must be >= 0"); return FR_ERR_INVALID_ARG; }
+    if (cfg->flux_reference != 0 && cfg->flux_reference != 1) { set_error("unknown flux reference"); return FR_ERR_INVALID_ARG; }
     if (cfg->precision != FR_FP64 && cfg->precision != FR_FP32) { set_error("unknown precision"); return FR_ERR_INVALID_ARG; }
     if (cfg->flux != FR_FLUX_RUSANOV && cfg->flux != FR_FLUX_ROE) { set_error("unknown interface flux"); return FR_ERR_INVALID_ARG; }
     if (cfg->viscous_scheme != FR_VISC_BR2 && cfg->viscous_scheme != FR_VISC_LDG) { set_error("unknown viscous scheme"); return FR_ERR_INVALID_ARG; }
@@ -224,11 +254,11 @@ Plan make_plan(fr_mesh *const *meshes, int n_inst) {
 }
 
 struct GroupLayout {
-    size_t U, R1, R2, RES, UF0, UF1, FV, MET, NRM, MFLUX, PART, EINST, WALL;
+    size_t U, R1, R2, RES, UF0, UF1, FV, MET, NRM, MFLUX, PART, EINST, WALL, DIVREF, FV2, LFP;
 };
 struct Layout {
     GroupLayout g[frk::kMaxGroups];
-    size_t BTAG, BVREF, STAGE, PROBES, PACC, PHIST, FORCE, PART_SUMS, RED, MORT, MATS, total;
+    size_t BTAG, BVREF, STAGE, PROBES, PACC, PHIST, FORCE, PART_SUMS, RED, MORT, MATS, FLAGS, total;
 };
 
 Layout make_layout(const Plan &P, int n_inst, bool fp64, bool visc) {
@@ -256,6 +286,9 @@ Layout make_layout(const Plan &P, int n_inst, bool fp64, bool visc) {
         G.PART = take((size_t)E * nfp * 4);
         G.EINST = take((size_t)E * 4);
         G.WALL = take((size_t)P.n_wall[g] * 4);
+        G.DIVREF = take(fp64 ? 16 : st);
+        G.FV2 = take(visc ? fc : 16);
+        G.LFP = take(visc ? (size_t)E * nfp * dim * rs : 16);
     }
     L.BTAG = take((size_t)P.nb * 4);
     L.BVREF = take((size_t)P.nb * dim * rs);
@@ -268,6 +301,7 @@ Layout make_layout(const Plan &P, int n_inst, bool fp64, bool visc) {
     L.RED = take((size_t)(V + 1) * 8);
     L.MORT = take((size_t)P.n_mortar * sizeof(frk::MortarFace));
     L.MATS = take((size_t)P.mat_reals * rs);
+    L.FLAGS = take((size_t)n_inst * 4);
     L.total = o;
     return L;
 }
@@ -312,6 +346,16 @@ void fill_args(const fr_solver *s, int g, frk::KArgs<real> &a) {
     a.n_partials = kPartialBlocks;
     a.stage64 = s->stage64;
     a.stage64_out = s->stage64;
+    a.gamma64 = s->cfg.gamma;
+    a.pref64 = s->pref64;
+    for (int v = 0; v < 5; ++v) a.uref64[v] = s->uref64[v];
+    if constexpr (std::is_same<real, float>::value) a.ref = s->ref32;
+    a.DIVREF = G.use_divref ? (const real *)G.DIVREF : nullptr;
+    a.FLAGS = s->FLAGS;
+    a.LFP = (const real *)G.LFP;
+    a.local_ref = s->local_ref ? 1 : 0;
+    a.regs_level = s->regs_level;
+    a.tc = (s->tc && !s->fp64) ? 1 : 0;
     const RefElem &r = G.ref;
     for (int i = 0; i < G.N; ++i) {
         for (int mm = 0; mm < G.N; ++mm) a.opD1[i * frk::kMaxN + mm] = r.D1[i][mm];
@@ -334,6 +378,8 @@ struct Launch {
     double rk_a = 0, rk_b = 0, rk_c = 0;
     const void *UFin = nullptr;
     void *UFout = nullptr;
+    const void *FVin = nullptr;   // fused stage: inbound / outbound gradient flux parts
+    void *FVout = nullptr;
     int64_t stage_off = 0;        // doubles into the FP64 staging buffer
     int64_t partial_slot = 0;     // first partial-sum block of the launch
     int64_t n_partials = 0;       // K_REDUCE: partial-sum blocks to reduce
@@ -355,6 +401,8 @@ cudaError_t do_launch(const fr_solver *s, const Launch &L) {
     a.rk_c = (real)L.rk_c;
     a.UFin = (const real *)L.UFin;
     a.UFout = (real *)L.UFout;
+    a.FVin = (const real *)L.FVin;
+    a.FVout = (real *)L.FVout;
     a.stage64 = s->stage64 + L.stage_off;
     a.stage64_out = s->stage64 + L.stage_off;
     a.partials = s->partials + L.partial_slot * (2 * s->V + 1);
@@ -392,6 +440,7 @@ cudaError_t do_mortar(const fr_solver *s, int pass, int par, int64_t m0, int64_t
     a.ldg = s->cfg.viscous_scheme == FR_VISC_LDG ? 1 : 0;
     a.visc = s->visc ? 1 : 0;
     a.pass = pass;
+    if constexpr (std::is_same<real, float>::value) a.ref = s->ref32;
     if constexpr (std::is_same<real, float>::value)
         return s->dim == 2 ? frk::mortar_2_f32(a, s->stream) : frk::mortar_3_f32(a, s->stream);
     else
@@ -402,7 +451,7 @@ cudaError_t do_mortar(const fr_solver *s, int pass, int par, int64_t m0, int64_t
 enum ProfKind { P_FLUX = 0, P_GRAD = 1, P_PROBE = 2, P_FORCE = 3, P_OTHER = 4 };
 
 int prof_kind(const Launch &L) {
-    if (L.kind == frk::K_FLUX) return P_FLUX;
+    if (L.kind == frk::K_FLUX || L.kind == frk::K_STAGE) return P_FLUX;
     if (L.kind == frk::K_GRAD) return L.force ? P_FORCE : P_GRAD;
     if (L.kind == frk::K_PROBE) return P_PROBE;
     return P_OTHER;
@@ -440,6 +489,9 @@ int grid_for(int64_t items) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(g, kPartialBlocks));
 }
 
+// inbound gradient-flux-part buffer of face parity par (fused stage)
+char *fvbuf(const Group &G, int par) { return par == 0 ? G.FV : G.FV2; }
+
 // One RK step starting from face-buffer parity p0; returns the launches issued.
 fr_status enqueue_step(fr_solver *s, int p0, int64_t *n_launch) {
     int par = p0;
@@ -448,7 +500,7 @@ fr_status enqueue_step(fr_solver *s, int p0, int64_t *n_launch) {
     const double dt = s->cfg.dt;
     const int G = (int)s->grp.size();
     for (int st = 0; st < stages; ++st) {
-        if (s->visc) {
+        if (s->visc && !s->fused) {
             for (int g = 0; g < G; ++g) {
                 Launch l;
                 l.kind = frk::K_GRAD;
@@ -465,11 +517,13 @@ fr_status enqueue_step(fr_solver *s, int p0, int64_t *n_launch) {
         }
         for (int g = 0; g < G; ++g) {
             Launch f;
-            f.kind = frk::K_FLUX;
+            f.kind = s->fused ? frk::K_STAGE : frk::K_FLUX;
             f.g = g;
             f.n_elem = s->grp[g].E;
             f.UFin = s->grp[g].UF[par];
             f.UFout = s->grp[g].UF[par ^ 1];
+            f.FVin = fvbuf(s->grp[g], par);
+            f.FVout = fvbuf(s->grp[g], par ^ 1);
             if (s->cfg.rk == FR_LSRK45) {
                 f.mode = st == 0 ? frk::M_LSRK_FIRST : frk::M_LSRK;
                 f.rk_a = kLsA[st];
@@ -530,7 +584,7 @@ fr_status check_inst(fr_solver *s, int inst) {
 // residual (or J * residual) of one instance into RES
 fr_status residual_into_res(fr_solver *s, int inst, int mode) {
     const int G = (int)s->grp.size();
-    if (s->visc) {
+    if (s->visc && !s->fused) {
         for (int g = 0; g < G; ++g) {
             Launch l;
             l.kind = frk::K_GRAD;
@@ -544,11 +598,12 @@ fr_status residual_into_res(fr_solver *s, int inst, int mode) {
     FR_CK(mortar(s, 1, s->parity, s->moff[inst], s->mcnt[inst]));
     for (int g = 0; g < G; ++g) {
         Launch f;
-        f.kind = frk::K_FLUX;
+        f.kind = s->fused ? frk::K_STAGE : frk::K_FLUX;
         f.g = g;
         f.elem0 = s->grp[g].off[inst];
         f.n_elem = s->grp[g].ne[inst];
         f.UFin = s->grp[g].UF[s->parity];
+        f.FVin = fvbuf(s->grp[g], s->parity);
         f.mode = mode;
         FR_CK(launch(s, f));
     }
@@ -593,6 +648,148 @@ int64_t stage_block(const fr_solver *s, int inst, int g) {
     int64_t o = 0;
     for (int h = 0; h < g; ++h) o += s->grp[h].ne[inst] * s->grp[h].nsp * s->V;
     return o;
+}
+
+// FP32 perturbation storage: the reference state and the FP64 constants
+// derived from it.  u_ref is the configuration's free stream with each
+// conserved component rounded to FP32, so that the stored perturbation plus
+// u_ref is exactly the state the host sees.
+void set_reference(fr_solver *s, const fr_config *cfg) {
+    const int dim = s->dim, V = dim + 2;
+    const double g = cfg->gamma;
+    double m[3] = {0, 0, 0}, v2 = 0.0;
+    for (int d = 0; d < dim; ++d) {
+        m[d] = cfg->rho_inf * cfg->v_inf[d];
+        v2 += cfg->v_inf[d] * cfg->v_inf[d];
+    }
+    s->uref64[0] = (double)(float)cfg->rho_inf;
+    for (int d = 0; d < dim; ++d) s->uref64[1 + d] = (double)(float)m[d];
+    s->uref64[V - 1] = (double)(float)(cfg->p_inf / (g - 1.0) + 0.5 * cfg->rho_inf * v2);
+    const double rho = s->uref64[0], E = s->uref64[V - 1];
+    double vr[3] = {0, 0, 0}, ke = 0.0;
+    for (int d = 0; d < dim; ++d) {
+        vr[d] = s->uref64[1 + d] / rho;
+        ke += 0.5 * s->uref64[1 + d] * vr[d];
+    }
+    const double p = (g - 1.0) * (E - ke), H = E + p;
+    s->pref64 = p;
+    frk::RefState<float> &r = s->ref32;
+    r = frk::RefState<float>{};
+    r.rho = (float)rho;
+    for (int d = 0; d < dim; ++d) {
+        r.m[d] = (float)s->uref64[1 + d];
+        r.v[d] = (float)vr[d];
+        s->vref64[d] = vr[d];
+    }
+    r.E = (float)E;
+    r.p = (float)p;
+    r.H = (float)H;
+    r.ke = (float)ke;
+    r.drho_inf = (float)(cfg->rho_inf - rho);
+    r.dp_inf = (float)(cfg->p_inf - p);
+    r.c_inf = (float)std::sqrt(g * cfg->p_inf / cfg->rho_inf);
+    // F_ref,j = [m_j, m_i v_j + p delta_ij, v_j H]
+    for (int j = 0; j < dim; ++j) {
+        s->Fref[j][0] = s->uref64[1 + j];
+        for (int i = 0; i < dim; ++i) s->Fref[j][1 + i] = s->uref64[1 + i] * vr[j] + (i == j ? p : 0.0);
+        s->Fref[j][V - 1] = vr[j] * H;
+    }
+}
+
+// J times the FR residual of the constant reference flux F(u_ref) in degree
+// group g (FP64): the divergence through the folded operator DT of the
+// transformed reference flux S F_ref along every line plus g' times the
+// reference part of the common fluxes, n F_ref at the element's own flux
+// points and, on the lower side of a mortar face, minus the projection P of
+// the higher side's n F_ref (what the kernels subtract there).  It vanishes
+// to round-off wherever the discrete metric identities hold; the return
+// value says whether it does not anywhere in the group.
+bool reference_divergence(const fr_solver *s, int g, const std::vector<double> &met,
+                          const std::vector<std::vector<double>> &nrm_groups, const std::vector<int32_t> &part,
+                          const std::vector<frk::MortarFace> &mfaces, const std::vector<double> &mats,
+                          std::vector<float> &out) {
+    const std::vector<double> &nrm = nrm_groups[g];
+    const Group &G = s->grp[g];
+    const int dim = s->dim, V = s->V, MS = s->MS, N = G.N, nsp = G.nsp, nfp = G.nfp, nfpf = G.nfpf;
+    const RefElem &r = G.ref;
+    double DT[kMaxN][kMaxN];
+    for (int i = 0; i < N; ++i)
+        for (int mm = 0; mm < N; ++mm) DT[i][mm] = r.D1[i][mm] - r.dgR[i] * r.lend[1][mm] - r.dgL[i] * r.lend[0][mm];
+    // lower-side mortar rows of this group: face and lane
+    std::vector<std::pair<int64_t, int>> lo_row((size_t)G.n_box_lo, {-1, 0});
+    for (size_t mi = 0; mi < mfaces.size(); ++mi) {
+        const frk::MortarFace &F = mfaces[mi];
+        if (F.glo != g) continue;
+        for (int l = 0; l < F.nlo; ++l) lo_row[(size_t)(F.lo_box - G.fp_real + l)] = {(int64_t)mi, l};
+    }
+    auto stride = [&](int k) { return k == 0 ? 1 : (k == 1 ? N : N * N); };
+    auto digit = [&](int sp, int k) { return (sp / stride(k)) % N; };
+    auto fp_of = [&](int sp, int k, int side) {
+        int l;
+        if (dim == 2) {
+            l = digit(sp, 1 - k);
+        } else {
+            const int a = (k == 0) ? 1 : 0, b = (k == 2) ? 1 : 2;
+            l = digit(sp, a) + N * digit(sp, b);
+        }
+        return (2 * k + side) * nfpf + l;
+    };
+    out.assign((size_t)G.E * nsp * V, 0.0f);
+    double worst = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : worst)
+    for (int64_t e = 0; e < G.E; ++e) {
+        // reference part of the common flux at every flux point of e
+        std::vector<double> jref((size_t)nfp * V), fhat((size_t)nsp * dim * V);
+        for (int f = 0; f < nfp; ++f) {
+            const int32_t pt = part[(size_t)e * nfp + f];
+            for (int v = 0; v < V; ++v) {
+                double t = 0.0;
+                if (pt >= G.fp_real && pt < G.fp_real + G.n_box_lo) {
+                    const auto &fl = lo_row[(size_t)(pt - G.fp_real)];
+                    const frk::MortarFace &F = mfaces[(size_t)fl.first];
+                    const double *Pm = mats.data() + F.mat + (int64_t)F.nhi * F.nlo;
+                    const std::vector<double> &nh = nrm_groups[F.ghi];
+                    for (int l = 0; l < F.nhi; ++l) {
+                        double nf = 0.0;
+                        for (int j = 0; j < dim; ++j) nf += nh[(size_t)(F.hi_fp + l) * dim + j] * s->Fref[j][v];
+                        t -= Pm[fl.second * F.nhi + l] * nf;
+                    }
+                } else {
+                    for (int j = 0; j < dim; ++j) t += nrm[((size_t)e * nfp + f) * dim + j] * s->Fref[j][v];
+                }
+                jref[(size_t)f * V + v] = t;
+            }
+        }
+        for (int sp = 0; sp < nsp; ++sp)
+            for (int k = 0; k < dim; ++k)
+                for (int v = 0; v < V; ++v) {
+                    double t = 0.0;
+                    for (int j = 0; j < dim; ++j)
+                        t += met[((size_t)e * nsp + sp) * MS + k * dim + j] * s->Fref[j][v];
+                    fhat[((size_t)sp * dim + k) * V + v] = t;
+                }
+        for (int sp = 0; sp < nsp; ++sp) {
+            for (int v = 0; v < V; ++v) {
+                double acc = 0.0, mag = 0.0;
+                for (int k = 0; k < dim; ++k) {
+                    const int ik = digit(sp, k), st = stride(k), q0 = sp - ik * st;
+                    for (int mm = 0; mm < N; ++mm) {
+                        const double t = DT[ik][mm] * fhat[((size_t)(q0 + mm * st) * dim + k) * V + v];
+                        acc += t;
+                        mag += std::fabs(t);
+                    }
+                    const double tp = r.dgR[ik] * jref[(size_t)fp_of(sp, k, 1) * V + v];
+                    const double tm = -r.dgL[ik] * jref[(size_t)fp_of(sp, k, 0) * V + v];
+                    acc += tp + tm;
+                    mag += std::fabs(tp) + std::fabs(tm);
+                }
+                out[((size_t)e * nsp + sp) * V + v] = (float)acc;
+                if (mag > 0.0) worst = std::max(worst, std::fabs(acc) / mag);
+            }
+        }
+    }
+    // round-off of the FP64 sums (a few dozen terms) stays far below this
+    return worst > 1e-11;
 }
 
 }  // namespace
@@ -677,6 +874,9 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
         G.MET = w + gl.MET; G.NRM = w + gl.NRM; G.MFLUX = w + gl.MFLUX;
         G.PART = (int32_t *)(w + gl.PART); G.EINST = (int32_t *)(w + gl.EINST);
         G.WALL = (int32_t *)(w + gl.WALL);
+        G.DIVREF = w + gl.DIVREF;
+        G.FV2 = w + gl.FV2;
+        G.LFP = w + gl.LFP;
     }
     s->BTAG = (int32_t *)(w + L.BTAG); s->BVREF = w + L.BVREF;
     s->stage64 = (double *)(w + L.STAGE);
@@ -687,6 +887,7 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
     s->partials = (double *)(w + L.PART_SUMS);
     s->reduce_out = (double *)(w + L.RED);
     s->MORT = (frk::MortarFace *)(w + L.MORT);
+    s->FLAGS = (int32_t *)(w + L.FLAGS);
     s->MATS = w + L.MATS;
 
     // element ranges of every instance in every group
@@ -776,6 +977,8 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
         std::copy(Pm.begin(), Pm.end(), mats.begin() + kv.second + (int64_t)T.size());
     }
 
+    if (!s->fp64) set_reference(s.get(), cfg);
+    s->local_ref = cfg->flux_reference == 0;
     // host tables, FP64 first, cast once
     const int MS = s->MS;
     std::vector<double> bvref((size_t)std::max<int64_t>(P.nb, 1) * dim, 0.0);
@@ -791,6 +994,7 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
         wall[g].reserve(G.n_wall);
     }
     int64_t b = 0;
+    s->wall_nsum.assign((size_t)n_inst * 3, 0.0);
     for (int i = 0; i < n_inst; ++i) {
         for (const fr_mesh *m : parts_of(meshes[i])) {
             const int g = P.group_of_degree[m->p];
@@ -809,6 +1013,12 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
                 bool has_wall = false;
                 for (int f = 0; f < nfp; ++f) {
                     const size_t lf = (size_t)e * nfp + f;
+                    if (m->bctag[lf] == FR_TAG_WALL) {
+                        // face quadrature weight: product of the free directions' weights
+                        const int l = f % G.nfpf, n1 = G.N;
+                        const double wf = dim == 2 ? G.ref.w[l] : G.ref.w[l % n1] * G.ref.w[l / n1];
+                        for (int d = 0; d < dim; ++d) s->wall_nsum[(size_t)i * 3 + d] += wf * m->nrm[lf * dim + d];
+                    }
                     for (int d = 0; d < dim; ++d) nrm[g][((size_t)ge * nfp + f) * dim + d] = m->nrm[lf * dim + d];
                     const int64_t pt = m->partner[lf];
                     const int32_t tag = m->bctag[lf];
@@ -828,7 +1038,9 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
                         double prof = 1.0;
                         if (tag == FR_TAG_INFLOW && cfg->inflow_delta > 0.0)
                             prof = std::tanh(3.0 * (m->x_fp[lf * dim + 1] - cfg->inflow_ywall) / cfg->inflow_delta);
-                        for (int d = 0; d < dim; ++d) bvref[(size_t)b * dim + d] = cfg->v_inf[d] * prof;
+                        // FP32 stores it relative to the reference velocity
+                        for (int d = 0; d < dim; ++d)
+                            bvref[(size_t)b * dim + d] = cfg->v_inf[d] * prof - s->vref64[d];
                         if (tag == FR_TAG_WALL) has_wall = true;
                         ++b;
                     }
@@ -871,8 +1083,50 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
         FR_CK(cudaMemsetAsync(G.RES, 0, st_bytes, cs));
         FR_CK(cudaMemsetAsync(G.UF[0], 0, fc_bytes, cs));
         FR_CK(cudaMemsetAsync(G.UF[1], 0, fc_bytes, cs));
-        if (s->visc) FR_CK(cudaMemsetAsync(G.FV, 0, fc_bytes, cs));
+        if (s->visc) {
+            FR_CK(cudaMemsetAsync(G.FV, 0, fc_bytes, cs));
+            FR_CK(cudaMemsetAsync(G.FV2, 0, fc_bytes, cs));
+        }
         FR_CK(cudaMemsetAsync(G.MFLUX, 0, (size_t)G.n_box * s->V * s->rsz, cs));
+    }
+    // BR2 stages may run as one fused kernel when every face is conforming;
+    // the default is the gradient + flux kernel pair, fr_tune measures both
+    const bool fusable = s->visc && cfg->viscous_scheme == FR_VISC_BR2 && P.n_mortar == 0;
+    s->fused = false;
+    if (fusable) {
+        // partner lifting coefficients per own flux point (FP64, then cast):
+        // lf = sum_m l_m(side) g'_side(m) (1/J) S[k][:] along the partner's line
+        for (int g = 0; g < P.G; ++g) {
+            const Group &G = s->grp[g];
+            const RefElem &r = G.ref;
+            const int nsp = G.nsp, nfp = G.nfp, N = G.N;
+            std::vector<double> lf((size_t)G.E * nfp * dim, 0.0), lfp((size_t)G.E * nfp * dim, 0.0);
+#pragma omp parallel for schedule(static)
+            for (int64_t e = 0; e < G.E; ++e)
+                for (int f = 0; f < nfp; ++f) {
+                    const int k = r.fp_dir[f], side = r.fp_side[f];
+                    for (int mm = 0; mm < N; ++mm) {
+                        const int sp = ref_line_sp(r, f, mm);
+                        const double *Mv = &met[g][((size_t)e * nsp + sp) * MS];
+                        const double c = r.lend[side][mm] * (side ? r.dgR[mm] : r.dgL[mm]) * Mv[dim * dim];
+                        for (int jd = 0; jd < dim; ++jd) lf[((size_t)e * nfp + f) * dim + jd] += c * Mv[k * dim + jd];
+                    }
+                }
+            for (size_t q = 0; q < (size_t)G.E * nfp; ++q) {
+                const int32_t pt = part[g][q];
+                if (pt < 0) continue;
+                for (int jd = 0; jd < dim; ++jd) lfp[q * dim + jd] = lf[(size_t)pt * dim + jd];
+            }
+            FR_CK(up_real(G.LFP, lfp, lfp.size()));
+        }
+    }
+    if (!s->fp64) {
+        std::vector<float> dr;
+        for (int g = 0; g < P.G; ++g) {
+            Group &G = s->grp[g];
+            G.use_divref = reference_divergence(s.get(), g, met[g], nrm, part[g], mfaces, mats, dr);
+            if (G.use_divref) FR_CK(up(G.DIVREF, dr.data(), dr.size() * sizeof(float)));
+        }
     }
     FR_CK(up_real(s->BVREF, bvref, (size_t)P.nb * dim));
     FR_CK(up(s->BTAG, btag.data(), (size_t)P.nb * 4));
@@ -880,6 +1134,7 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
     FR_CK(up_real(s->MATS, mats, (size_t)P.mat_reals));
     FR_CK(cudaMemsetAsync(s->pacc, 0, sizeof(frk::ProbeAcc) * kMaxProbes, cs));
     FR_CK(cudaMemsetAsync(s->force_acc, 0, (size_t)n_inst * 3 * 8, cs));
+    FR_CK(cudaMemsetAsync(s->FLAGS, 0, (size_t)n_inst * 4, cs));
     FR_CK(cudaStreamSynchronize(cs));
     for (int g = 0; g < P.G; ++g) {
         const int N = s->grp[g].N;
@@ -908,6 +1163,7 @@ namespace {
 // `tmp`, which must stay alive until the stream has been synchronised.
 fr_status enqueue_upload(fr_solver *s, int inst, const double *u, std::vector<double> &tmp) {
     const int V = s->V;
+    FR_CK(cudaMemsetAsync(s->FLAGS + inst, 0, 4, s->stream));
     const size_t n = (size_t)s->inst_nsp[inst] * V;
     if (!spread(s, inst)) {
         FR_CK(cudaMemcpyAsync(s->stage64, u, n * 8, cudaMemcpyHostToDevice, s->stream));
@@ -935,11 +1191,12 @@ fr_status enqueue_upload(fr_solver *s, int inst, const double *u, std::vector<do
         c.grid = grid_for(G.ne[inst] * G.nsp * V);
         FR_CK(launch(s, c));
         Launch in;
-        in.kind = frk::K_INTERP;
+        in.kind = s->fused ? frk::K_INTERP_VISC : frk::K_INTERP;
         in.g = (int)g;
         in.elem0 = G.off[inst];
         in.n_elem = G.ne[inst];
         in.UFout = G.UF[s->parity];
+        in.FVout = fvbuf(G, s->parity);
         FR_CK(launch(s, in));
     }
     FR_CK(mortar(s, 0, s->parity, s->moff[inst], s->mcnt[inst]));
@@ -1094,8 +1351,38 @@ extern "C" fr_status fr_rk_step(fr_solver *s, int n_steps) {
         }
         s->parity = (stages % 2) ? p0 ^ 1 : p0;
         ++s->steps_since_reset;
+        if (s->cfg.check_every > 0 && ++s->steps_since_check >= s->cfg.check_every) {
+            s->steps_since_check = 0;
+            for (size_t g = 0; g < s->grp.size(); ++g) {
+                Launch c;
+                c.kind = frk::K_FINITE;
+                c.g = (int)g;
+                c.n_elem = s->grp[g].E;
+                c.grid = grid_for(s->grp[g].E * s->grp[g].nsp);
+                FR_CK(launch(s, c));
+                ++total;
+            }
+        }
     }
     s->last_launches = total;
+    return FR_OK;
+}
+
+extern "C" fr_status fr_instance_status(fr_solver *s, int32_t *flags, int *first_bad) {
+    fr::Range nvtx_range("fr_instance_status");
+    if (!s || !first_bad) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
+    std::vector<int32_t> h(s->n_inst);
+    FR_CK(cudaMemcpyAsync(h.data(), s->FLAGS, h.size() * 4, cudaMemcpyDeviceToHost, s->stream));
+    FR_CK(cudaStreamSynchronize(s->stream));
+    *first_bad = -1;
+    for (int i = 0; i < s->n_inst; ++i) {
+        if (flags) flags[i] = h[i];
+        if (h[i] && *first_bad < 0) *first_bad = i;
+    }
+    if (*first_bad >= 0) {
+        set_error("non-finite values in the state of instance " + std::to_string(*first_bad));
+        return FR_ERR_NONFINITE;
+    }
     return FR_OK;
 }
 
@@ -1165,6 +1452,7 @@ extern "C" fr_status fr_probe_add(fr_solver *s, int inst, const double *x, int *
     s->n_probe += 1;
     s->grp[g].n_probe += 1;
     s->probe_inst.push_back(inst);
+    s->probe_elem.push_back(d.elem);
     drop_graphs(s);   // the captured step must include the new observer
     *probe_id = id;
     return FR_OK;
@@ -1217,11 +1505,25 @@ extern "C" fr_status fr_probe_history(fr_solver *s, int probe_id, double *out, i
     return FR_OK;
 }
 
-// Accumulator checkpoint: [steps in the window, number of probes, wall-force
-// sums n_inst x 3, probe accumulators n_probe x 16, sample rings n_probe x kHistLen]
+// Accumulator checkpoint: [steps in the window, number of probes, number of
+// instances, probe fingerprint, wall-force sums n_inst x 3, probe
+// accumulators n_probe x 16, sample rings n_probe x kHistLen]
+static constexpr int kAccHeader = 4;
+
+// identifies the observers (instance and element of each, in order); an
+// integer below 2^53, so it survives the round trip through a double exactly
+static double probe_fingerprint(const fr_solver *s) {
+    uint64_t h = 1469598103934665603ull;
+    for (int i = 0; i < s->n_probe; ++i) {
+        h = (h ^ (uint64_t)s->probe_inst[i]) * 1099511628211ull;
+        h = (h ^ (uint64_t)s->probe_elem[i]) * 1099511628211ull;
+    }
+    return (double)(h >> 11);
+}
+
 extern "C" int64_t fr_accumulators_size(const fr_solver *s) {
     if (!s) return -1;
-    return 2 + (int64_t)s->n_inst * 3 + (int64_t)s->n_probe * (int64_t)(sizeof(frk::ProbeAcc) / 8) +
+    return kAccHeader + (int64_t)s->n_inst * 3 + (int64_t)s->n_probe * (int64_t)(sizeof(frk::ProbeAcc) / 8) +
            (int64_t)s->n_probe * frk::kHistLen;
 }
 
@@ -1230,7 +1532,9 @@ extern "C" fr_status fr_get_accumulators(fr_solver *s, double *out) {
     const size_t na = sizeof(frk::ProbeAcc) / 8;
     out[0] = (double)s->steps_since_reset;
     out[1] = (double)s->n_probe;
-    double *f = out + 2, *pa = f + (size_t)s->n_inst * 3, *ph = pa + (size_t)s->n_probe * na;
+    out[2] = (double)s->n_inst;
+    out[3] = probe_fingerprint(s);
+    double *f = out + kAccHeader, *pa = f + (size_t)s->n_inst * 3, *ph = pa + (size_t)s->n_probe * na;
     FR_CK(cudaMemcpyAsync(f, s->force_acc, (size_t)s->n_inst * 3 * 8, cudaMemcpyDeviceToHost, s->stream));
     if (s->n_probe > 0) {
         FR_CK(cudaMemcpyAsync(pa, s->pacc, (size_t)s->n_probe * sizeof(frk::ProbeAcc), cudaMemcpyDeviceToHost,
@@ -1242,15 +1546,25 @@ extern "C" fr_status fr_get_accumulators(fr_solver *s, double *out) {
     return FR_OK;
 }
 
-extern "C" fr_status fr_set_accumulators(fr_solver *s, const double *in) {
+extern "C" fr_status fr_set_accumulators(fr_solver *s, const double *in, int64_t n) {
     if (!s || !in) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
-    if (in[1] != (double)s->n_probe || !(in[0] >= 0.0)) {
-        set_error("accumulator checkpoint is for " + std::to_string((int64_t)in[1]) + " probes, the solver has " +
-                  std::to_string(s->n_probe));
+    if (n != fr_accumulators_size(s)) {
+        set_error("accumulator checkpoint has " + std::to_string(n) + " values, this solver's has " +
+                  std::to_string(fr_accumulators_size(s)));
+        return FR_ERR_INVALID_ARG;
+    }
+    if (in[1] != (double)s->n_probe || in[2] != (double)s->n_inst || !(in[0] >= 0.0)) {
+        set_error("accumulator checkpoint is for " + std::to_string((int64_t)in[2]) + " instances and " +
+                  std::to_string((int64_t)in[1]) + " probes, the solver has " + std::to_string(s->n_inst) +
+                  " and " + std::to_string(s->n_probe));
+        return FR_ERR_INVALID_ARG;
+    }
+    if (in[3] != probe_fingerprint(s)) {
+        set_error("accumulator checkpoint was taken with other observers (instances or locations differ)");
         return FR_ERR_INVALID_ARG;
     }
     const size_t na = sizeof(frk::ProbeAcc) / 8;
-    const double *f = in + 2, *pa = f + (size_t)s->n_inst * 3, *ph = pa + (size_t)s->n_probe * na;
+    const double *f = in + kAccHeader, *pa = f + (size_t)s->n_inst * 3, *ph = pa + (size_t)s->n_probe * na;
     FR_CK(cudaMemcpyAsync(s->force_acc, f, (size_t)s->n_inst * 3 * 8, cudaMemcpyHostToDevice, s->stream));
     if (s->n_probe > 0) {
         FR_CK(cudaMemcpyAsync(s->pacc, pa, (size_t)s->n_probe * sizeof(frk::ProbeAcc), cudaMemcpyHostToDevice,
@@ -1299,7 +1613,50 @@ extern "C" fr_status fr_forces(fr_solver *s, int inst, double *mean_force) {
     FR_CK(cudaMemcpyAsync(h, s->force_acc + (size_t)inst * 3, 24, cudaMemcpyDeviceToHost, s->stream));
     FR_CK(cudaStreamSynchronize(s->stream));
     const double n = (double)std::max<int64_t>(s->steps_since_reset, 1);
-    for (int d = 0; d < s->dim; ++d) mean_force[d] = h[d] / n;
+    for (int d = 0; d < s->dim; ++d) {
+        mean_force[d] = h[d] / n;
+        if (!s->fp64 && s->steps_since_reset > 0) mean_force[d] += s->pref64 * s->wall_nsum[(size_t)inst * 3 + d];
+    }
+    return FR_OK;
+}
+
+extern "C" fr_status fr_force_coefficients(fr_solver *s, int inst, double a_ref, double *mean_cl,
+                                           double *mean_cd) {
+    if (!mean_cl || !mean_cd || !(a_ref > 0.0)) {
+        set_error("invalid fr_force_coefficients arguments");
+        return FR_ERR_INVALID_ARG;
+    }
+    double F[3] = {0, 0, 0};
+    fr_status st = fr_forces(s, inst, F);
+    if (st != FR_OK) return st;
+    const int dim = s->dim;
+    double vv = 0.0;
+    for (int d = 0; d < dim; ++d) vv += s->cfg.v_inf[d] * s->cfg.v_inf[d];
+    if (!(vv > 0.0) || !(s->cfg.rho_inf > 0.0)) {
+        set_error("force coefficients need a non-zero free-stream velocity");
+        return FR_ERR_INVALID_ARG;
+    }
+    const double vm = std::sqrt(vv);
+    double dr[3] = {0, 0, 0}, li[3] = {0, 0, 0};
+    for (int d = 0; d < dim; ++d) dr[d] = s->cfg.v_inf[d] / vm;
+    if (dim == 2) {
+        li[0] = -dr[1];
+        li[1] = dr[0];
+    } else {
+        // the y axis made orthogonal to the drag direction
+        for (int d = 0; d < 3; ++d) li[d] = (d == 1 ? 1.0 : 0.0) - dr[1] * dr[d];
+        const double ln = std::sqrt(li[0] * li[0] + li[1] * li[1] + li[2] * li[2]);
+        if (!(ln > 1e-12)) { set_error("free stream along the y axis: lift direction undefined"); return FR_ERR_INVALID_ARG; }
+        for (int d = 0; d < 3; ++d) li[d] /= ln;
+    }
+    const double q = 0.5 * s->cfg.rho_inf * vv * a_ref;
+    double cl = 0.0, cd = 0.0;
+    for (int d = 0; d < dim; ++d) {
+        cl += F[d] * li[d];
+        cd += F[d] * dr[d];
+    }
+    *mean_cl = cl / q;
+    *mean_cd = cd / q;
     return FR_OK;
 }
 
@@ -1345,22 +1702,14 @@ constexpr size_t kStaticDoubles = (size_t)kStaticBlocks * kStaticSlotsPerBlock +
 
 __device__ __align__(256) double g_static_scratch[kStaticDoubles];
 
-std::mutex g_static_mu;
-double *g_static_ptr[64] = {};   // device address of g_static_scratch, per device
-
-// Device address of the scratch array on the current device.  Looked up once
-// per device (cudaGetSymbolAddress), with that device current.
+// Device address of the scratch array on the current device, looked up on
+// every call (cudaGetSymbolAddress, with the caller's device current): a
+// cached address would outlive a device reset or a re-created primary
+// context, and the lookup costs far less than the launches it serves.
 fr_status static_scratch(double **out) {
-    int dev = 0;
-    FR_CK(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) { set_error("device index out of range"); return FR_ERR_INVALID_ARG; }
-    std::lock_guard<std::mutex> lk(g_static_mu);
-    if (!g_static_ptr[dev]) {
-        void *p = nullptr;
-        FR_CK(cudaGetSymbolAddress(&p, g_static_scratch));
-        g_static_ptr[dev] = static_cast<double *>(p);
-    }
-    *out = g_static_ptr[dev];
+    void *p = nullptr;
+    FR_CK(cudaGetSymbolAddress(&p, g_static_scratch));
+    *out = static_cast<double *>(p);
     return FR_OK;
 }
 
@@ -1434,5 +1783,228 @@ extern "C" fr_status fr_integral_static(fr_solver *s, int inst, double *sums, in
     for (int v = 0; v < s->V; ++v) sums[v] = h[v];
     if (n_nonfinite) *n_nonfinite = (int64_t)h[s->V];
     if (h[s->V] > 0) { set_error("non-finite values in the state"); return FR_ERR_NONFINITE; }
+    return FR_OK;
+}
+
+// --------------------------------------------------------------------------
+// Autotuner (fr_tune): the stage schedule of a solver (BR2: one fused kernel
+// or gradient + flux kernels) and the register level of its stage kernels,
+// measured on the solver's own batch and cached in a small JSON file keyed
+// on the GPU architecture and the batch's shape.
+// --------------------------------------------------------------------------
+namespace fr {
+namespace {
+
+std::string schedule_string(const fr_solver *s) {
+    char buf[192];
+    std::snprintf(buf, sizeof(buf), "stage=%s;regs=%d;contract=%s;ms=%.6f;source=%s", s->fused ? "fused" : "split",
+                  s->regs_level, s->tc ? "tc" : "simt", s->schedule_ms, s->schedule_source.c_str());
+    return buf;
+}
+
+std::string tune_key(const fr_solver *s) {
+    int dev = 0;
+    cudaDeviceProp prop{};
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaGetDeviceProperties(&prop, dev);
+    int64_t nsp = 0;
+    std::string deg;
+    for (const Group &G : s->grp) {
+        nsp += G.E * G.nsp;
+        if (!deg.empty()) deg += ",";
+        deg += std::to_string(G.p);
+    }
+    int bucket = 0;
+    while (((int64_t)1 << (bucket + 1)) <= nsp) ++bucket;
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "sm_%d%d|dim=%d|p=%s|V=%d|%s|%s|%s|mortar=%d|log2sp=%d", prop.major,
+                  prop.minor, s->dim, deg.c_str(), s->V, s->fp64 ? "fp64" : "fp32",
+                  !s->visc ? "euler" : (s->cfg.viscous_scheme == FR_VISC_LDG ? "ldg" : "br2"),
+                  s->cfg.flux == FR_FLUX_ROE ? "roe" : "rusanov", s->n_mortar > 0 ? 1 : 0, bucket);
+    return buf;
+}
+
+// The cache file: a JSON object with one "key": "value" pair per line.
+std::map<std::string, std::string> read_cache(const char *path) {
+    std::map<std::string, std::string> m;
+    if (!path) return m;
+    FILE *f = std::fopen(path, "r");
+    if (!f) return m;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        std::string l(line);
+        const size_t a = l.find('"');
+        if (a == std::string::npos) continue;
+        const size_t b = l.find('"', a + 1);
+        if (b == std::string::npos) continue;
+        const size_t c = l.find('"', b + 1);
+        if (c == std::string::npos) continue;
+        const size_t d = l.find('"', c + 1);
+        if (d == std::string::npos) continue;
+        if (l.find(':', b) > c) continue;
+        m[l.substr(a + 1, b - a - 1)] = l.substr(c + 1, d - c - 1);
+    }
+    std::fclose(f);
+    return m;
+}
+
+bool write_cache(const char *path, const std::map<std::string, std::string> &m) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = std::fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    std::fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto &kv : m) std::fprintf(f, "  \"%s\": \"%s\"%s\n", kv.first.c_str(), kv.second.c_str(), ++i < m.size() ? "," : "");
+    std::fprintf(f, "}\n");
+    std::fclose(f);
+    return std::rename(tmp.c_str(), path) == 0;
+}
+
+// apply "stage=...;regs=..." if it is valid for this solver
+bool apply_schedule(fr_solver *s, const std::string &v, const char *source) {
+    const bool fused = v.find("stage=fused") != std::string::npos;
+    const size_t r = v.find("regs=");
+    const int regs = r == std::string::npos ? 0 : std::atoi(v.c_str() + r + 5);
+    const bool tc = v.find("contract=tc") != std::string::npos;
+    const bool fusable = s->visc && s->cfg.viscous_scheme == FR_VISC_BR2 && s->n_mortar == 0;
+    if ((fused && !fusable) || regs < 0 || regs >= frk::kRegLevels || (tc && s->fp64)) return false;
+    s->fused = fused;
+    s->regs_level = s->fp64 ? 0 : regs;
+    s->tc = tc;
+    const size_t m = v.find("ms=");
+    s->schedule_ms = m == std::string::npos ? 0.0 : std::atof(v.c_str() + m + 3);
+    s->schedule_source = source;
+    drop_graphs(s);
+    return true;
+}
+
+}  // namespace
+}  // namespace fr
+
+extern "C" fr_status fr_tune_lookup(const char *cache_path, const char *key, char *value, size_t len) {
+    if (!cache_path || !key || !value || len == 0) { set_error("invalid fr_tune_lookup arguments"); return FR_ERR_INVALID_ARG; }
+    const auto m = fr::read_cache(cache_path);
+    const auto it = m.find(key);
+    value[0] = 0;
+    if (it == m.end()) { set_error("no cached schedule for this key"); return FR_ERR_INVALID_ARG; }
+    std::snprintf(value, len, "%s", it->second.c_str());
+    return FR_OK;
+}
+
+extern "C" fr_status fr_schedule(fr_solver *s, char *out, size_t len, char *key, size_t key_len) {
+    if (!s) { set_error("null solver"); return FR_ERR_INVALID_ARG; }
+    if (out && len) std::snprintf(out, len, "%s", fr::schedule_string(s).c_str());
+    if (key && key_len) std::snprintf(key, key_len, "%s", fr::tune_key(s).c_str());
+    return FR_OK;
+}
+
+extern "C" fr_status fr_tune(fr_solver *s, const char *cache_path, int mode, char *choice, size_t choice_len) {
+    fr::Range nvtx_range("fr_tune");
+    if (!s || mode < 0 || mode > 2) { set_error("invalid fr_tune arguments"); return FR_ERR_INVALID_ARG; }
+    const std::string key = fr::tune_key(s);
+    auto cache = fr::read_cache(cache_path);
+    const auto hit = cache.find(key);
+    if (mode != 1 && hit != cache.end() && fr::apply_schedule(s, hit->second, "cache")) {
+        if (choice && choice_len) std::snprintf(choice, choice_len, "%s", fr::schedule_string(s).c_str());
+        return FR_OK;
+    }
+    if (mode == 2) {   // lookup only: keep the default
+        if (choice && choice_len) std::snprintf(choice, choice_len, "%s", fr::schedule_string(s).c_str());
+        return FR_OK;
+    }
+    // candidates: stage schedule x register level
+    struct Cand { bool fused; int regs; bool tc; double ms; };
+    std::vector<Cand> cands;
+    const bool fusable = s->visc && s->cfg.viscous_scheme == FR_VISC_BR2 && s->n_mortar == 0;
+    for (int c = 0; c < (s->fp64 ? 1 : 2); ++c)
+        for (int f = 0; f < (fusable ? 2 : 1); ++f)
+            for (int r = 0; r < (s->fp64 ? 1 : frk::kRegLevels); ++r) cands.push_back({f == 1, r, c == 1, 0.0});
+    const int warm = 2, timed = 3;
+    const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
+    // every instance starts from the free stream of the configuration
+    {
+        const int V = s->V;
+        double u0[5] = {s->cfg.rho_inf, 0, 0, 0, 0}, v2 = 0.0;
+        for (int d = 0; d < s->dim; ++d) {
+            u0[1 + d] = s->cfg.rho_inf * s->cfg.v_inf[d];
+            v2 += s->cfg.v_inf[d] * s->cfg.v_inf[d];
+        }
+        u0[V - 1] = s->cfg.p_inf / (s->cfg.gamma - 1.0) + 0.5 * s->cfg.rho_inf * v2;
+        for (int i = 0; i < s->n_inst; ++i) {
+            std::vector<double> fs((size_t)s->inst_nsp[i] * V), tmp;
+            for (size_t q = 0; q < fs.size(); ++q) fs[q] = u0[q % V];
+            fr_status su = enqueue_upload(s, i, fs.data(), tmp);
+            if (su != FR_OK) return su;
+            FR_CK(cudaStreamSynchronize(s->stream));
+        }
+    }
+    cudaEvent_t e0, e1;
+    FR_CK(cudaEventCreate(&e0));
+    FR_CK(cudaEventCreate(&e1));
+    fr_status st = FR_OK;
+    for (Cand &c : cands) {
+        s->fused = c.fused;
+        s->regs_level = c.regs;
+        s->tc = c.tc;
+        drop_graphs(s);
+        // face data for this schedule, then warm-up and timed steps
+        for (int i = 0; i < s->n_inst && st == FR_OK; ++i) {
+            for (size_t g = 0; g < s->grp.size(); ++g) {
+                const Group &G = s->grp[g];
+                if (G.ne[i] <= 0) continue;
+                Launch in;
+                in.kind = s->fused ? frk::K_INTERP_VISC : frk::K_INTERP;
+                in.g = (int)g;
+                in.elem0 = G.off[i];
+                in.n_elem = G.ne[i];
+                in.UFout = G.UF[s->parity];
+                in.FVout = fvbuf(G, s->parity);
+                if (launch(s, in) != cudaSuccess) st = FR_ERR_CUDA;
+            }
+            if (st == FR_OK && mortar(s, 0, s->parity, s->moff[i], s->mcnt[i]) != cudaSuccess) st = FR_ERR_CUDA;
+        }
+        for (int it = 0; it < warm + timed && st == FR_OK; ++it) {
+            if (it == warm && cudaEventRecord(e0, s->stream) != cudaSuccess) st = FR_ERR_CUDA;
+            int64_t cnt = 0;
+            if (st == FR_OK) st = enqueue_step(s, s->parity, &cnt);
+            s->parity = (stages % 2) ? s->parity ^ 1 : s->parity;
+        }
+        if (st == FR_OK && cudaEventRecord(e1, s->stream) != cudaSuccess) st = FR_ERR_CUDA;
+        if (st == FR_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FR_ERR_CUDA;
+        float ms = 0.f;
+        if (st == FR_OK) cudaEventElapsedTime(&ms, e0, e1);
+        c.ms = ms / timed;
+        if (st != FR_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    // the steps above ran on whatever state the solver held: start afresh
+    cudaMemsetAsync(s->pacc, 0, sizeof(frk::ProbeAcc) * kMaxProbes, s->stream);
+    cudaMemsetAsync(s->force_acc, 0, (size_t)s->n_inst * 3 * 8, s->stream);
+    cudaMemsetAsync(s->FLAGS, 0, (size_t)s->n_inst * 4, s->stream);
+    s->steps_since_reset = 0;
+    if (st != FR_OK) {
+        set_error("fr_tune: a candidate schedule failed to run");
+        return st;
+    }
+    const Cand *best = &cands[0];
+    for (const Cand &c : cands)
+        if (c.ms < best->ms) best = &c;
+    char v[160];
+    std::snprintf(v, sizeof(v), "stage=%s;regs=%d;contract=%s;ms=%.6f", best->fused ? "fused" : "split", best->regs,
+                  best->tc ? "tc" : "simt", best->ms);
+    fr::apply_schedule(s, v, "measured");
+    std::string all;
+    for (const Cand &c : cands) {
+        char b[96];
+        std::snprintf(b, sizeof(b), "%s%s/%d/%s=%.4f", all.empty() ? "" : ",", c.fused ? "fused" : "split", c.regs,
+                      c.tc ? "tc" : "simt", c.ms);
+        all += b;
+    }
+    if (cache_path) {
+        cache[key] = v;
+        fr::write_cache(cache_path, cache);
+    }
+    if (choice && choice_len)
+        std::snprintf(choice, choice_len, "%s;candidates=%s", fr::schedule_string(s).c_str(), all.c_str());
     return FR_OK;
 }

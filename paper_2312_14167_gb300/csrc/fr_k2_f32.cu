@@ -22,7 +22,19 @@ static cudaError_t prepare_n(bool visc) {
     if (e != cudaSuccess) return e;
     e = prep_smem(k_grad<2, N, float>, smem_bytes<2, N, float>(K_GRAD, true));
     if (e != cudaSuccess) return e;
-    return prep_smem(k_interp<2, N, float>, smem_bytes<2, N, float>(K_INTERP, false));
+    e = prep_smem(k_interp<2, N, float>, smem_bytes<2, N, float>(K_INTERP, false));
+    if (e != cudaSuccess || !visc) return e;
+    e = prep_smem(k_stage<2, N, float>, smem_bytes<2, N, float>(K_STAGE, true));
+    if (e != cudaSuccess) return e;
+    e = prep_smem(k_interp_visc<2, N, float>, smem_bytes<2, N, float>(K_INTERP_VISC, true));
+    if (e != cudaSuccess || !has_level1<N, float>()) return e;
+    // register level 1 (autotuner candidates)
+    constexpr int L1 = has_level1<N, float>() ? 1 : 0;
+    e = prep_smem(k_flux<2, N, float, true, L1>, smem_bytes<2, N, float>(K_FLUX, true));
+    if (e != cudaSuccess) return e;
+    e = prep_smem(k_grad<2, N, float, L1>, smem_bytes<2, N, float>(K_GRAD, true));
+    if (e != cudaSuccess) return e;
+    return prep_smem(k_stage<2, N, float, L1>, smem_bytes<2, N, float>(K_STAGE, true));
 }
 
 cudaError_t prepare_2_f32(int N, bool visc) {

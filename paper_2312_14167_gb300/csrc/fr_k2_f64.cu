@@ -22,7 +22,11 @@ static cudaError_t prepare_n(bool visc) {
     if (e != cudaSuccess) return e;
     e = prep_smem(k_grad<2, N, double>, smem_bytes<2, N, double>(K_GRAD, true));
     if (e != cudaSuccess) return e;
-    return prep_smem(k_interp<2, N, double>, smem_bytes<2, N, double>(K_INTERP, false));
+    e = prep_smem(k_interp<2, N, double>, smem_bytes<2, N, double>(K_INTERP, false));
+    if (e != cudaSuccess || !visc) return e;
+    e = prep_smem(k_stage<2, N, double>, smem_bytes<2, N, double>(K_STAGE, true));
+    if (e != cudaSuccess) return e;
+    return prep_smem(k_interp_visc<2, N, double>, smem_bytes<2, N, double>(K_INTERP_VISC, true));
 }
 
 cudaError_t prepare_2_f64(int N, bool visc) {

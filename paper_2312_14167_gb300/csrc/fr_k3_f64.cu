@@ -22,7 +22,11 @@ static cudaError_t prepare_n(bool visc) {
     if (e != cudaSuccess) return e;
     e = prep_smem(k_grad<3, N, double>, smem_bytes<3, N, double>(K_GRAD, true));
     if (e != cudaSuccess) return e;
-    return prep_smem(k_interp<3, N, double>, smem_bytes<3, N, double>(K_INTERP, false));
+    e = prep_smem(k_interp<3, N, double>, smem_bytes<3, N, double>(K_INTERP, false));
+    if (e != cudaSuccess || !visc) return e;
+    e = prep_smem(k_stage<3, N, double>, smem_bytes<3, N, double>(K_STAGE, true));
+    if (e != cudaSuccess) return e;
+    return prep_smem(k_interp_visc<3, N, double>, smem_bytes<3, N, double>(K_INTERP_VISC, true));
 }
 
 cudaError_t prepare_3_f64(int N, bool visc) {

@@ -42,6 +42,9 @@ enum Kind : int {
     K_REDUCE = 5,    // ordered compensated reduction of the partials
     K_TO_REAL = 6,   // FP64 staging -> state
     K_TO_F64 = 7,    // state/residual -> FP64 staging
+    K_FINITE = 8,    // per-instance non-finite flags of the state
+    K_STAGE = 9,     // fused BR2 stage (K_GRAD + K_FLUX in one kernel)
+    K_INTERP_VISC = 10,  // face states + gradient flux parts (fused stage prologue)
 };
 
 enum Mode : int {
@@ -70,6 +73,22 @@ struct ProbeAcc {      // FP64 accumulators of one observer
     double mean, m2, m2_c;     // Welford window moments
     double last;
     double pad[7];
+};
+
+// Mixed precision (FP32) stores the state as its perturbation u' = u - u_r
+// about a constant reference state u_r (the free stream of the
+// configuration, rounded to FP32 values), and evaluates every flux as its
+// perturbation F(u) - F(u_r) in a form without cancellation: the rounding
+// of a stored value and of a flux is then relative to the perturbation, not
+// to the total (at M = 0.1 the energy flux is ~250 times the residual).
+// The FR residual of the constant flux F(u_r) (zero wherever the metric
+// identities hold) is added back from an FP64 host evaluation.
+template <typename real>
+struct RefState {
+    real rho, m[3], E, v[3], p, H, ke;   // rho_r, rho_r v_r, rhoE_r, v_r, p_r, rhoE_r + p_r, m_r.v_r / 2
+    // the boundary reference (far field) relative to u_r: rho_inf - rho_r,
+    // p_inf - p_r, and c_inf
+    real drho_inf, dp_inf, c_inf;
 };
 
 template <typename real>
@@ -121,6 +140,24 @@ struct KArgs {
     // in: DT[i][m] = D1[i][m] - g_R'(xi_i) l_m(+1) - g_L'(xi_i) l_m(-1)
     double opDT[kMaxN * kMaxN];
     double opW[kMaxN];            // Gauss weights
+    // perturbation storage (FP32 kernels): reference state, its FP64
+    // conserved values (for the FP64 staging conversions and integrals), and
+    // J times the residual of the constant reference flux per solution point
+    // (null where that is zero to round-off)
+    RefState<real> ref;
+    double uref64[5], pref64, gamma64;
+    const real *DIVREF;
+    int32_t *FLAGS;            // [n_inst] set to 1 where the state holds a NaN or Inf
+    // fused viscous stage (BR2, k_stage): inbound gradient part of the
+    // partner's viscous normal flux F_v(u_f, grad u_f) . n_partner at each
+    // own point, its outbound twin, and the partner's BR2 lifting
+    // coefficients lf at each own point [E][NFP][D]
+    const real *FVin;
+    real *FVout;
+    const real *LFP;
+    int local_ref;             // FP32: evaluate fluxes about element-local references
+    int regs_level;            // register level of the stage kernels (host-side launch choice)
+    int tc;                    // FP32: line contractions on the tensor cores (3xTF32 mma.sync)
 };
 
 // --------------------------------------------------------------------------
@@ -362,6 +399,56 @@ __device__ __forceinline__ void flux_vis(const real *u, const real (*grad)[D + 2
     }
 }
 
+// viscous normal flux F_v(u, Q) . n
+template <int D, typename real>
+__device__ __forceinline__ void flux_vis_n(const real *u, const real (*Q)[D + 2], const real *n, real gamma,
+                                           real mu, real prandtl, real *out) {
+    real Fv[D][D + 2];
+    flux_vis<D>(u, Q, gamma, mu, prandtl, Fv);
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) {
+        real t = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) t += Fv[d][v] * n[d];
+        out[v] = t;
+    }
+}
+
+// F_v(u, lf (x) dd) . n: the viscous normal flux of the rank-one gradient
+// lf_j dd_v (the BR2 lifting of a face jump dd with lifting coefficients
+// lf); F_v is linear in the gradient for a fixed state, so a face's flux is
+// the flux of its interpolated gradient plus this term
+template <int D, typename real>
+__device__ __forceinline__ void flux_vis_lift_n(const real *u, const real *lf, const real *dd, const real *n,
+                                                real gamma, real mu, real prandtl, real *out) {
+    constexpr int V = D + 2;
+    const real ir = real(1) / u[0];
+    const real Es = u[V - 1] * ir;
+    real vel[D], w[D], ln = 0, lw = 0, wn = 0, vw = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        vel[i] = u[1 + i] * ir;
+        w[i] = (dd[1 + i] - dd[0] * vel[i]) * ir;       // grad v_i = lf w_i
+    }
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        ln += lf[i] * n[i];
+        lw += lf[i] * w[i];
+        wn += w[i] * n[i];
+        vw += vel[i] * w[i];
+    }
+    const real e = (dd[V - 1] - dd[0] * Es) * ir;      // grad E = lf e
+    real en = 0;
+    out[0] = 0;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        const real t = mu * (w[i] * ln + lf[i] * wn - real(2.0 / 3.0) * n[i] * lw);
+        out[1 + i] = t;
+        en += vel[i] * t;
+    }
+    out[V - 1] = en + mu / prandtl * gamma * ln * (e - vw);
+}
+
 // boundary states: ghost for the inviscid flux, state for gradients
 template <int D, typename real>
 __device__ __forceinline__ void bc_states(int tag, const real *uL, const real *n, const real *vref,
@@ -420,6 +507,289 @@ __device__ __forceinline__ void bc_states(int tag, const real *uL, const real *n
         ke += vb[j] * vb[j];
     }
     ub[V - 1] = pb / gm1 + real(0.5) * rb * ke;
+#pragma unroll
+    for (int v = 0; v < V; ++v) ug[v] = ub[v];
+}
+
+// --------------------------------------------------------------------------
+// perturbation physics (FP32 path): inputs and outputs are perturbations
+// about the reference state r; every expression is exact algebra of the
+// definitions above, arranged so that no term of the reference magnitude is
+// formed and then cancelled
+// --------------------------------------------------------------------------
+// rho, v' = v - v_r, v, p' = p - p_r, p from u'
+template <int D, typename real>
+__device__ __forceinline__ void prim_pert(const real *up, const RefState<real> &r, real gm1, real &rho,
+                                          real *vp, real *v, real &pp, real &p) {
+    rho = r.rho + up[0];
+    const real ir = real(1) / rho;
+    real kep = 0;   // m.v - m_r.v_r
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        vp[i] = (up[1 + i] - r.v[i] * up[0]) * ir;
+        v[i] = r.v[i] + vp[i];
+        kep += r.m[i] * vp[i] + up[1 + i] * (r.v[i] + vp[i]);
+    }
+    pp = gm1 * (up[D + 1] - real(0.5) * kep);
+    p = r.p + pp;
+}
+
+// F(u).n - F(u_r).n (n not normalised); vn = v.n and c^2 of the full state
+template <int D, typename real>
+__device__ __forceinline__ void flux_normal_pert(const real *up, const real *n, const RefState<real> &r,
+                                                 real gm1, real gamma, real *F, real &vn, real &c2) {
+    real rho, vp[D], v[D], pp, p;
+    prim_pert<D>(up, r, gm1, rho, vp, v, pp, p);
+    real vnr = 0, vnp = 0, mn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        vnr += r.v[j] * n[j];
+        vnp += vp[j] * n[j];
+        mn += up[1 + j] * n[j];
+    }
+    F[0] = mn;
+#pragma unroll
+    for (int i = 0; i < D; ++i) F[1 + i] = up[1 + i] * (vnr + vnp) + r.m[i] * vnp + pp * n[i];
+    const real Hp = up[D + 1] + pp;
+    F[D + 1] = Hp * (vnr + vnp) + r.H * vnp;
+    vn = vnr + vnp;
+    c2 = gamma * p / rho;
+}
+
+template <int D, typename real>
+__device__ __forceinline__ void rusanov_pert(const real *uL, const real *uR, const real *n,
+                                             const RefState<real> &r, real gamma, real *F) {
+    constexpr int V = D + 2;
+    const real gm1 = gamma - real(1);
+    real nn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn += n[j] * n[j];
+    const real nm = sqrt(nn);
+    real FL[V], FR[V], vnL, vnR, c2L, c2R;
+    flux_normal_pert<D>(uL, n, r, gm1, gamma, FL, vnL, c2L);
+    flux_normal_pert<D>(uR, n, r, gm1, gamma, FR, vnR, c2R);
+    const real lam = fmax(fabs(vnL) / nm + sqrt(c2L), fabs(vnR) / nm + sqrt(c2R));
+#pragma unroll
+    for (int v = 0; v < V; ++v) F[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * (lam * nm) * (uR[v] - uL[v]);
+}
+
+// Roe: averaged state from the full states, wave strengths from the
+// perturbation jumps (identical to the jumps of the full states)
+template <int D, typename real>
+__device__ __forceinline__ void roe_pert(const real *uL, const real *uR, const real *n, const RefState<real> &r,
+                                         real gamma, real *F) {
+    constexpr int V = D + 2;
+    const real gm1 = gamma - real(1);
+    real nn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn += n[j] * n[j];
+    const real nm = sqrt(nn), inm = real(1) / nm;
+    real nh[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) nh[j] = n[j] * inm;
+    real FL[V], FR[V], vnL, vnR, c2L, c2R;
+    flux_normal_pert<D>(uL, n, r, gm1, gamma, FL, vnL, c2L);
+    flux_normal_pert<D>(uR, n, r, gm1, gamma, FR, vnR, c2R);
+    real rL, vpL[D], vL[D], ppL, pL, rR, vpR[D], vR[D], ppR, pR;
+    prim_pert<D>(uL, r, gm1, rL, vpL, vL, ppL, pL);
+    prim_pert<D>(uR, r, gm1, rR, vpR, vR, ppR, pR);
+    const real HL = (r.H + uL[V - 1] + ppL) / rL, HR = (r.H + uR[V - 1] + ppR) / rR;
+    const real sL = sqrt(rL), sR = sqrt(rR), isum = real(1) / (sL + sR);
+    const real wL = sL * isum, wR = sR * isum, rt = sL * sR;
+    real vt[D], q2 = 0, vnt = 0, dvn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        vt[j] = wL * vL[j] + wR * vR[j];
+        q2 += vt[j] * vt[j];
+        vnt += vt[j] * nh[j];
+        dvn += (vpR[j] - vpL[j]) * nh[j];
+    }
+    const real Ht = wL * HL + wR * HR;
+    const real ct = sqrt(gm1 * (Ht - real(0.5) * q2));
+    const real ic2 = real(1) / (ct * ct);
+    const real drho = uR[0] - uL[0], dp = ppR - ppL;
+    const real a1 = (dp - rt * ct * dvn) * real(0.5) * ic2;
+    const real a2 = drho - dp * ic2;
+    const real a3 = (dp + rt * ct * dvn) * real(0.5) * ic2;
+    real l1 = fabs(vnt - ct), l2 = fabs(vnt), l3 = fabs(vnt + ct);
+    const real del = real(0.1) * ct;
+    if (l1 < del) l1 = ((vnt - ct) * (vnt - ct) + del * del) / (real(2) * del);
+    if (l3 < del) l3 = ((vnt + ct) * (vnt + ct) + del * del) / (real(2) * del);
+    real diss[V];
+    const real w1 = l1 * a1, w2 = l2 * a2, w3 = l3 * a3;
+    diss[0] = w1 + w2 + w3;
+    real vdt = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        const real dvt = (vpR[j] - vpL[j]) - dvn * nh[j];
+        vdt += vt[j] * dvt;
+        diss[1 + j] = w1 * (vt[j] - ct * nh[j]) + w2 * vt[j] + w3 * (vt[j] + ct * nh[j]) + l2 * rt * dvt;
+    }
+    diss[V - 1] = w1 * (Ht - vnt * ct) + w2 * real(0.5) * q2 + w3 * (Ht + vnt * ct) + l2 * rt * vdt;
+#pragma unroll
+    for (int v = 0; v < V; ++v) F[v] = real(0.5) * (FL[v] + FR[v]) - real(0.5) * nm * diss[v];
+}
+
+template <int D, typename real>
+__device__ __forceinline__ void common_inviscid_pert(int flux, const real *uL, const real *uR, const real *n,
+                                                     const RefState<real> &r, real gamma, real *F) {
+    if (flux == 1) roe_pert<D>(uL, uR, n, r, gamma, F);
+    else rusanov_pert<D>(uL, uR, n, r, gamma, F);
+}
+
+// F_j(u) - F_j(u_r), j = 0..D-1
+template <int D, typename real>
+__device__ __forceinline__ void flux_inv_pert(const real *up, const RefState<real> &r, real gm1,
+                                              real (*F)[D + 2]) {
+    real rho, vp[D], v[D], pp, p;
+    prim_pert<D>(up, r, gm1, rho, vp, v, pp, p);
+    const real Hp = up[D + 1] + pp;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        F[j][0] = up[1 + j];
+#pragma unroll
+        for (int i = 0; i < D; ++i)
+            F[j][1 + i] = up[1 + i] * v[j] + r.m[i] * vp[j] + (i == j ? pp : real(0));
+        F[j][D + 1] = Hp * v[j] + r.H * vp[j];
+    }
+}
+
+// Element-local reference of the flux evaluation (FP32 path).  The stored
+// perturbation u' is relative to the global reference u_r; an element whose
+// state is far from u_r (a wall cell of a flow at rest there) would evaluate
+// fluxes that are O(F(u_r)) and cancel.  So each element evaluates its
+// fluxes about its own reference u_c = u_r + du, du = the perturbation at its
+// first solution point with u_r + du made exact in FP32: states enter as
+// u' - du, and every common flux of the element is taken relative to
+// n . F(u_c).  The element's residual is unchanged in exact arithmetic
+// wherever the element preserves a uniform flow (the FR residual of the
+// constant F(u_c) vanishes); groups whose reference-flux residual is not
+// zero (DIVREF) keep the global reference.
+template <int D, typename real>
+struct LocalRef {
+    RefState<real> r;     // u_c and its derived quantities
+    real du[D + 2];       // u_c - u_r (exact)
+    real bv[3];           // v_c - v_r: shifts the boundary reference velocities
+};
+
+template <int D, typename real>
+__device__ __forceinline__ void make_local_ref(const RefState<real> &g, const real *u0, real gamma,
+                                               LocalRef<D, real> &L) {
+    constexpr int V = D + 2;
+    const real gm1 = gamma - real(1);
+    // c = fl(g + u0) and du = c - g exactly (the difference of the two is exact)
+    real c[V];
+    c[0] = g.rho + u0[0];
+    L.du[0] = c[0] - g.rho;
+#pragma unroll
+    for (int i = 0; i < D; ++i) {
+        c[1 + i] = g.m[i] + u0[1 + i];
+        L.du[1 + i] = c[1 + i] - g.m[i];
+    }
+    c[V - 1] = g.E + u0[V - 1];
+    L.du[V - 1] = c[V - 1] - g.E;
+    RefState<real> &r = L.r;
+    r.rho = c[0];
+    r.E = c[V - 1];
+    real ke = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        r.m[i] = i < D ? c[1 + i] : real(0);
+        r.v[i] = i < D ? c[1 + i] / c[0] : real(0);
+        ke += real(0.5) * r.m[i] * r.v[i];
+        L.bv[i] = r.v[i] - g.v[i];
+    }
+    r.ke = ke;
+    r.p = gm1 * (r.E - ke);
+    r.H = r.E + r.p;
+    r.c_inf = g.c_inf;
+    r.drho_inf = (g.rho + g.drho_inf) - r.rho;
+    r.dp_inf = (g.p + g.dp_inf) - r.p;
+}
+
+// full state u_r + u'
+template <int V, typename real>
+__device__ __forceinline__ void add_ref(const RefState<real> &r, const real *up, real *u) {
+    constexpr int D = V - 2;
+    u[0] = r.rho + up[0];
+#pragma unroll
+    for (int i = 0; i < D; ++i) u[1 + i] = r.m[i] + up[1 + i];
+    u[V - 1] = r.E + up[V - 1];
+}
+
+// Boundary states as perturbations (the construction of bc_states).  bvp is
+// the boundary point's reference velocity minus v_r.
+template <int D, typename real>
+__device__ __forceinline__ void bc_states_pert(int tag, const real *uL, const real *n, const real *bvp,
+                                               const RefState<real> &r, real gamma, real *ug, real *ub) {
+    constexpr int V = D + 2;
+    const real gm1 = gamma - real(1);
+    real nn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) nn += n[j] * n[j];
+    const real inm = rsqrt_(nn);
+    real nh[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) nh[j] = n[j] * inm;
+    real rL, vpL[D], vL[D], ppL, pL;
+    prim_pert<D>(uL, r, gm1, rL, vpL, vL, ppL, pL);
+    if (tag == BC_WALL) {
+        real mn = 0;
+#pragma unroll
+        for (int j = 0; j < D; ++j) mn += (r.m[j] + uL[1 + j]) * nh[j];
+        ug[0] = uL[0];
+#pragma unroll
+        for (int j = 0; j < D; ++j) ug[1 + j] = uL[1 + j] - real(2) * mn * nh[j];
+        ug[V - 1] = uL[V - 1];
+        // zero velocity, interior density and pressure
+        ub[0] = uL[0];
+#pragma unroll
+        for (int j = 0; j < D; ++j) ub[1 + j] = -r.m[j];
+        ub[V - 1] = ppL / gm1 - r.ke;
+        return;
+    }
+    const real rinf = r.rho + r.drho_inf, cinf = r.c_inf;
+    const real cL = sqrt(gamma * pL / rL);
+    // cL^2 - cinf^2 = gamma (pL rinf - pinf rL) / (rL rinf), pinf = p_r + dp_inf
+    const real num = r.p * (r.drho_inf - uL[0]) + ppL * rinf - r.dp_inf * rL;
+    const real dc = gamma * num / (rL * rinf) / (cL + cinf);          // cL - cinf
+    real vnr = 0, dvn = 0;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        vnr += (r.v[j] + bvp[j]) * nh[j];
+        dvn += (vpL[j] - bvp[j]) * nh[j];                              // vnL - vnr
+    }
+    const real vnb = vnr + real(0.5) * dvn + dc / gm1;
+    const real dcb = real(0.25) * gm1 * dvn + real(0.5) * dc;          // cb - cinf
+    const real cb = cinf + dcb;
+    const bool out = vnb > real(0);
+    const real ex = real(2) / gm1;
+    real rbp, vbp[D];
+    if (out) {
+        // entropy of the interior: rb = rL (cb / cL)^(2/(gamma-1))
+        rbp = uL[0] + rL * expm1(ex * log1p((dcb - dc) / cL));
+        const real s = -real(0.5) * dvn + dc / gm1;                    // vnb - vnL
+#pragma unroll
+        for (int j = 0; j < D; ++j) vbp[j] = vpL[j] + s * nh[j];
+    } else {
+        // entropy of the far field: rb = rinf (cb / cinf)^(2/(gamma-1))
+        rbp = r.drho_inf + rinf * expm1(ex * log1p(dcb / cinf));
+        const real s = real(0.5) * dvn + dc / gm1;                     // vnb - vnr
+#pragma unroll
+        for (int j = 0; j < D; ++j) vbp[j] = bvp[j] + s * nh[j];
+    }
+    const real rb = r.rho + rbp;
+    // pb - p_r = ((rb - rinf) cb^2 + rinf (cb^2 - cinf^2)) / gamma + dp_inf
+    const real pbp = ((rbp - r.drho_inf) * cb * cb + rinf * dcb * (cb + cinf)) / gamma + r.dp_inf;
+    real vr2 = 0, vv = 0;
+    ub[0] = rbp;
+#pragma unroll
+    for (int j = 0; j < D; ++j) {
+        ub[1 + j] = rbp * r.v[j] + rb * vbp[j];
+        vr2 += r.v[j] * r.v[j];
+        vv += vbp[j] * (real(2) * r.v[j] + vbp[j]);
+    }
+    ub[V - 1] = pbp / gm1 + real(0.5) * (rbp * vr2 + rb * vv);
 #pragma unroll
     for (int v = 0; v < V; ++v) ug[v] = ub[v];
 }
@@ -569,6 +939,110 @@ __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const 
     }
 }
 
+// shared-memory slots (in reals) of the tile's local references
+template <int D, int N, typename real>
+__host__ __device__ constexpr int lr_slots() {
+    return pad4((int)((sizeof(LocalRef<D, real>) * Geo<D, N>::NE + sizeof(real) - 1) / sizeof(real)));
+}
+
+// --------------------------------------------------------------------------
+// Tensor-core line contraction (FP32 option, chosen per solver by the
+// autotuner): the divergence + correction of every line of a tile as 3xTF32
+// mma.sync products.  For direction k the rows (element, line, variable) of
+// a 16 x 8 A tile hold the line's N transformed fluxes and its two common
+// normal fluxes (K = N + 2 <= 8, the rest zero); the 8 x 8 B operator holds
+// DT^T, -g_L' and g_R' (the same for every direction and tile, kept in
+// registers).  x = hi + lo with hi = tf32(x), lo = tf32(x - hi); the product
+// keeps hi*hi + lo*hi + hi*lo (FP32 accumulation), an error of a few 2^-22
+// relative to the terms.  Each direction's result goes to sDiv[k][j][s][v].
+// --------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                 "{%0,%1,%2,%3};\n"
+                 : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+                 : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+template <int D, int N>
+__device__ __forceinline__ void tc_divergence(const float *sF, const float *sC, const float *DT, const float *GL,
+                                              const float *GR, float *sDiv, int ne) {
+    static_assert(N + 2 <= 8, "line plus two faces must fit K = 8");
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, NFP = G::NFP, NFPF = G::NFPF, V = G::V, NE = G::NE;
+    constexpr int NL = NSP / N;                 // lines per direction and element
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    // B fragments: b0 = B[t][g], b1 = B[t + 4][g], B[c][i] = operator row c, output position i
+    auto bval = [&](int c, int i) -> float {
+        if (i >= N) return 0.f;
+        if (c < N) return DT[i * N + c];
+        if (c == N) return -GL[i];
+        if (c == N + 1) return GR[i];
+        return 0.f;
+    };
+    const float bv0 = bval(t, g), bv1 = bval(t + 4, g);
+    const uint32_t b0h = to_tf32(bv0), b1h = to_tf32(bv1);
+    const uint32_t b0l = to_tf32(bv0 - __uint_as_float(b0h)), b1l = to_tf32(bv1 - __uint_as_float(b1h));
+    const int rows = ne * NL * V;
+    const int tiles = (rows + 15) / 16;
+    for (int tile = warp; tile < D * tiles; tile += nw) {
+        const int k = tile / tiles, r0 = (tile % tiles) * 16;
+        const int st = G::stride(k);
+        uint32_t ah[4], al[4];
+        int sp[2] = {0, 0}, jj[2] = {0, 0}, vv[2] = {0, 0};
+        bool ok[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int r = r0 + g + 8 * h;
+            ok[h] = r < rows;
+            float x0 = 0.f, x1 = 0.f;
+            if (ok[h]) {
+                const int v = r % V, l = (r / V) % NL, j = r / (V * NL);
+                int kk, side;
+                const int fm = 2 * k * NFPF + l;               // the line's - face point
+                const int base = G::line_base(fm, kk, side);
+                sp[h] = base;
+                jj[h] = j;
+                vv[h] = v;
+                auto xval = [&](int c) -> float {
+                    if (c < N) return sF[((j * D + k) * NSP + base + c * st) * V + v];
+                    if (c == N) return sC[(j * NFP + fm) * V + v];
+                    if (c == N + 1) return sC[(j * NFP + fm + NFPF) * V + v];
+                    return 0.f;
+                };
+                x0 = xval(t);
+                x1 = xval(t + 4);
+            }
+            // a0/a1: column t of rows g / g+8; a2/a3: column t+4
+            const uint32_t h0 = to_tf32(x0), h1 = to_tf32(x1);
+            ah[h] = h0;
+            ah[2 + h] = h1;
+            al[h] = to_tf32(x0 - __uint_as_float(h0));
+            al[2 + h] = to_tf32(x1 - __uint_as_float(h1));
+        }
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        mma_tf32(d, ah, b0h, b1h);
+        mma_tf32(d, al, b0h, b1h);
+        mma_tf32(d, ah, b0l, b1l);
+        // d0/d1: row g, columns 2t, 2t+1; d2/d3: row g+8
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!ok[h]) continue;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const int i = 2 * t + q;
+                if (i < N) sDiv[((k * NE + jj[h]) * NSP + sp[h] + i * st) * V + vv[h]] = d[2 * h + q];
+            }
+        }
+    }
+}
+
 // minimum CTAs per SM requested from the register allocator
 // Measured on the 32-airfoil poll (2-D, p=3, FP32): the flux kernel is
 // fastest at 6 resident CTAs (40 registers, a few spills), the gradient
@@ -588,15 +1062,22 @@ __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const 
 #ifndef FR_MINB_GRAD_3D_F32
 #define FR_MINB_GRAD_3D_F32 0
 #endif
-template <int D, typename real, bool GRAD = false, int N = 4>
+// L: register level chosen by the autotuner (fr_tune); level 1 asks for one
+// resident CTA fewer per SM, i.e. more registers per thread
+template <int D, typename real, bool GRAD = false, int N = 4, int L = 0>
 struct MinBlocks {
     static constexpr int flux3 = FR_MINB_FLUX_3D_F32 > 0 ? FR_MINB_FLUX_3D_F32 : (N >= 5 ? 4 : 3);
     static constexpr int grad3 = FR_MINB_GRAD_3D_F32 > 0 ? FR_MINB_GRAD_3D_F32 : (N >= 4 ? 5 : 4);
-    static constexpr int value =
+    static constexpr int base =
         sizeof(real) == 8 ? 1
         : (D == 2 ? (GRAD ? FR_MINB_GRAD_2D_F32 : FR_MINB_FLUX_2D_F32)
                   : (GRAD ? grad3 : flux3));
+    static constexpr int value = base - L > 1 ? base - L : 1;
 };
+// register levels compiled: FP32 kernels of degree >= 2 have two
+constexpr int kRegLevels = 2;
+template <int N, typename real>
+__host__ __device__ constexpr bool has_level1() { return sizeof(real) == 4 && N >= 3; }
 
 // --------------------------------------------------------------------------
 // K_GRAD: BR2 face gradient Q = interp((1/J) S^T D u) + eta r_f and the
@@ -608,11 +1089,12 @@ struct MinBlocks {
 // state) are issued before the tile barrier so that their latency overlaps
 // the tile load.
 // --------------------------------------------------------------------------
-template <int D, int N, typename real>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true, N>::value))
+template <int D, int N, typename real, int L = 0>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true, N, L>::value))
 k_grad(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
+    constexpr bool PERT = sizeof(real) == 4;   // FP32 state: perturbations about a.ref
     constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
@@ -675,7 +1157,8 @@ k_grad(const KArgs<real> a) {
             real vref[D], ug[V];
 #pragma unroll
             for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d];
-            bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, ug, ub);
+            if constexpr (PERT) bc_states_pert<D>(a.BTAG[b], uL, nr[it], vref, a.ref, a.gamma, ug, ub);
+            else bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, ug, ub);
 #pragma unroll
             for (int v = 0; v < V; ++v) uc[v] = ub[v];
         }
@@ -775,7 +1258,13 @@ k_grad(const KArgs<real> a) {
 #pragma unroll
             for (int v = 0; v < V; ++v) Q[jd][v] += eta * lf[jd] * dd[v];
         real Fv[D][V];
-        flux_vis<D>(ub, Q, a.gamma, a.mu, a.prandtl, Fv);
+        real ubf[V];
+        if constexpr (PERT) add_ref<V>(a.ref, ub, ubf);
+        else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) ubf[v] = ub[v];
+        }
+        flux_vis<D>(ubf, Q, a.gamma, a.mu, a.prandtl, Fv);
         real fvn[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) {
@@ -792,12 +1281,23 @@ k_grad(const KArgs<real> a) {
             // face quadrature weight: product of the free directions' weights
             const int l = f % G::NFPF;
             const double wf = (D == 2) ? a.opW[l] : a.opW[l % N] * a.opW[l / N];
-            real rho, vel[D], p;
-            primitives<D>(ub, a.gamma - real(1), rho, vel, p);
+            double pw;
+            if constexpr (PERT) {
+                // p - p_r only: sum w p_r n over a closed wall is a per-step
+                // constant the host adds (fr_forces), so the atomic sums stay
+                // small and their order barely matters
+                real rho, vp[D], vel[D], pp, p;
+                prim_pert<D>(ub, a.ref, a.gamma - real(1), rho, vp, vel, pp, p);
+                pw = (double)pp;
+            } else {
+                real rho, vel[D], p;
+                primitives<D>(ub, a.gamma - real(1), rho, vel, p);
+                pw = (double)p;
+            }
             const int inst = a.EINST[e];
 #pragma unroll
             for (int d = 0; d < D; ++d)
-                atomicAdd(&a.force_acc[inst * 3 + d], wf * ((double)p * (double)nr[it][d] - (double)fvn[1 + d]));
+                atomicAdd(&a.force_acc[inst * 3 + d], wf * (pw * (double)nr[it][d] - (double)fvn[1 + d]));
         }
     }
 }
@@ -805,11 +1305,12 @@ k_grad(const KArgs<real> a) {
 // --------------------------------------------------------------------------
 // K_FLUX: fused common flux + transformed flux + divergence/correction + RK
 // --------------------------------------------------------------------------
-template <int D, int N, typename real, bool VISC>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N>::value))
+template <int D, int N, typename real, bool VISC, int L = 0>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, L>::value))
 k_flux(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
+    constexpr bool PERT = sizeof(real) == 4;   // FP32 state: perturbations about a.ref
     constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
     constexpr int ITS = (NE * NSP + G::THREADS - 1) / G::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -820,6 +1321,8 @@ k_flux(const KArgs<real> a) {
     real *sC = sM + pad4(NE * NSP * MS);
     real *sD = sC + pad4(NE * NFP * V);
     real *sF = sD + (VISC ? pad4(NE * NFP * V) : 0);   // [j][k][s][v]
+    LocalRef<D, real> *sLR = reinterpret_cast<LocalRef<D, real> *>(sF + pad4(NE * D * NSP * V));
+    real *sDiv = sF + pad4(NE * D * NSP * V) + lr_slots<D, N, real>();   // [k][j][s][v] (tensor-core option)
     const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N, *DT = GR + N;
 
     const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
@@ -880,6 +1383,11 @@ k_flux(const KArgs<real> a) {
     load_state_rows<N, V, PAD>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
     __syncthreads();
+    const bool local = PERT && a.local_ref && !a.DIVREF;
+    if (PERT && local) {
+        if (tid < ne) make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
+        __syncthreads();
+    }
 
     // 1) common normal flux at every own flux point
 #pragma unroll
@@ -892,17 +1400,42 @@ k_flux(const KArgs<real> a) {
         real ub[V], uRp[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) uRp[v] = uR[it][v];
+        // FP32: states relative to the element's reference (local) or the global one
+        const RefState<real> &rf = local ? sLR[j].r : a.ref;
+        real shift[V], bsh[D];
+#pragma unroll
+        for (int v = 0; v < V; ++v) shift[v] = local ? sLR[j].du[v] : real(0);
+#pragma unroll
+        for (int d = 0; d < D; ++d) bsh[d] = local ? sLR[j].bv[d] : real(0);
+        real uLl[V], uRl[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) { uLl[v] = uL[v] - shift[v]; uRl[v] = uRp[v] - shift[v]; }
         if (pt[it] < 0) {
             const int b = -1 - pt[it];
             real vref[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d];
-            bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, uRp, ub);
+            for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d] - bsh[d];
+            if constexpr (PERT) {
+                bc_states_pert<D>(a.BTAG[b], uLl, nr[it], vref, rf, a.gamma, uRl, ub);
+#pragma unroll
+                for (int v = 0; v < V; ++v) { uRp[v] = uRl[v] + shift[v]; ub[v] += shift[v]; }
+            } else {
+                bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, uRp, ub);
+            }
         }
         // mortar points take the common flux formed on the mortar (k_mortar)
         const bool mort = pt[it] >= a.fp_real;
         real Fs[V];
-        if (mort) ld_v<V>(a.MFLUX + (int64_t)(pt[it] - a.fp_real) * V, Fs);
+        if (mort) {
+            ld_v<V>(a.MFLUX + (int64_t)(pt[it] - a.fp_real) * V, Fs);
+            if (PERT && local) {
+                // the mortar flux is relative to n . F(u_r): take n . (F(u_c) - F(u_r)) off
+                real Fc[V], vn, c2;
+                flux_normal_pert<D>(shift, nr[it], a.ref, a.gamma - real(1), a.gamma, Fc, vn, c2);
+#pragma unroll
+                for (int v = 0; v < V; ++v) Fs[v] -= Fc[v];
+            }
+        } else if constexpr (PERT) common_inviscid_pert<D>(a.flux, uLl, uRl, nr[it], rf, a.gamma, Fs);
         else common_inviscid<D>(a.flux, uL, uRp, nr[it], a.gamma, Fs);
         if (VISC) {
             real dd[V];
@@ -941,7 +1474,14 @@ k_flux(const KArgs<real> a) {
         real uu[V];
         ld_v<V>(sU + G::template slot<PAD>(j * NSP + s) * V, uu);
         real F[D][V];
-        flux_inv<D>(uu, a.gamma - real(1), F);
+        if constexpr (PERT) {
+            real ul[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) ul[v] = uu[v] - (local ? sLR[j].du[v] : real(0));
+            flux_inv_pert<D>(ul, local ? sLR[j].r : a.ref, a.gamma - real(1), F);
+        } else {
+            flux_inv<D>(uu, a.gamma - real(1), F);
+        }
         if (VISC) {
             const real iJ = M[D * D];
             real Gk[D][V];
@@ -975,7 +1515,13 @@ k_flux(const KArgs<real> a) {
                     gr[jd][v] = g * iJ;
                 }
             real Fv[D][V];
-            flux_vis<D>(uu, gr, a.gamma, a.mu, a.prandtl, Fv);
+            real uf[V];
+            if constexpr (PERT) add_ref<V>(a.ref, uu, uf);
+            else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) uf[v] = uu[v];
+            }
+            flux_vis<D>(uf, gr, a.gamma, a.mu, a.prandtl, Fv);
 #pragma unroll
             for (int jd = 0; jd < D; ++jd)
 #pragma unroll
@@ -1001,6 +1547,13 @@ k_flux(const KArgs<real> a) {
     // flux is minus the flux polynomial's value there) is linear in the line's
     // flux values, so the polynomial's end values are folded into the
     // derivative operator (DT) and only the common fluxes are added here.
+    const bool tc = PERT && a.tc;
+    if constexpr (PERT) {
+        if (tc) {
+            tc_divergence<D, N>(sF, sC, DT, GL, GR, sDiv, ne);
+            __syncthreads();
+        }
+    }
 #pragma unroll
     for (int it = 0; it < ITS; ++it) {
         const int w = tid + it * G::THREADS;
@@ -1010,8 +1563,18 @@ k_flux(const KArgs<real> a) {
         real div[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) div[v] = 0;
+        if (tc) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                real x[V];
+                ld_v<V>(sDiv + ((k * NE + j) * NSP + s) * V, x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) div[v] += x[v];
+            }
+        }
 #pragma unroll
         for (int k = 0; k < D; ++k) {
+            if (tc) break;
             const int ik = G::digit(s, k), st = G::stride(k);
             const real *row = DT + ik * N;
             const int q0 = (j * D + k) * NSP + s - ik * st;
@@ -1031,6 +1594,13 @@ k_flux(const KArgs<real> a) {
         }
         const real iJ = sM[(j * NSP + s) * MS + D * D];
         const int64_t g = (e * NSP + s) * V;
+        if (PERT && a.DIVREF) {
+            // the constant reference flux's share of the divergence
+            real dr[V];
+            ldg_v<V>(a.DIVREF + g, dr);
+#pragma unroll
+            for (int v = 0; v < V; ++v) div[v] += dr[v];
+        }
         real *su = sU + G::template slot<PAD>(j * NSP + s) * V;
         real u0[V], un[V], R[V];
         ld_v<V>(su, u0);
@@ -1089,6 +1659,494 @@ k_flux(const KArgs<real> a) {
         interp_line<D, N, V, PAD>(sU, j, f, Lm, Lp, uf);
         st_v<V>(a.UFout + (int64_t)pt[it] * V, uf);
     }
+}
+
+// --------------------------------------------------------------------------
+// K_STAGE: one RK stage of the BR2 Navier-Stokes residual in one kernel (no
+// separate gradient kernel).  Every element sends its partners, at the end
+// of a stage, its face state and the gradient part of its viscous normal
+// flux F_v(u_f, grad u_f) . n (grad u_f: its uncorrected physical gradient
+// interpolated to the face).  The next stage forms both sides' BR2 viscous
+// fluxes locally: its own in full, the partner's as that gradient part plus
+// the rank-one lifting term F_v(u_R, eta lf_R (x) dd_R) . n_R, with the
+// partner's lifting coefficients lf_R precomputed per point (geometry) and
+// n_R = -n.  Same arithmetic as K_GRAD + K_FLUX up to rounding; conforming
+// faces only (a batch with mortar faces or LDG uses those kernels).
+// --------------------------------------------------------------------------
+// uncorrected physical gradient (1/J) S^T D u at every solution point of the
+// tile into sG [j][s][jd][v]
+template <int D, int N, bool PAD, typename real>
+__device__ __forceinline__ void tile_gradient(const real *sU, const real *sM, const real *D1, real *sG, int ne) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, V = G::V, MS = G::MS;
+    for (int w = threadIdx.x; w < ne * NSP; w += blockDim.x) {
+        const int j = w / NSP, s = w % NSP;
+        const real *M = sM + (j * NSP + s) * MS;
+        const real iJ = M[D * D];
+        real Gk[D][V];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int ik = G::digit(s, k), st = G::stride(k);
+            const real *row = D1 + ik * N;
+            const int q0 = j * NSP + s - ik * st;
+#pragma unroll
+            for (int v = 0; v < V; ++v) Gk[k][v] = 0;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                real x[V];
+                ld_v<V>(sU + G::template slot<PAD>(q0 + m * st) * V, x);
+                const real c = row[m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) Gk[k][v] += c * x[v];
+            }
+        }
+        real *dst = sG + (j * NSP + s) * D * V;
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd) {
+            real g[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                real t = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) t += M[k * D + jd] * Gk[k][v];
+                g[v] = t * iJ;
+            }
+            st_v<V>(dst + jd * V, g);
+        }
+    }
+}
+
+// interpolated gradient Q [D][V] of sG at flux point f of tile element j
+template <int D, int N, typename real>
+__device__ __forceinline__ void interp_grad(const real *sG, int j, int f, const real *Lm, const real *Lp,
+                                            real (*Q)[D + 2]) {
+    using G = Geo<D, N>;
+    constexpr int V = D + 2;
+    int k, side;
+    const int base = G::line_base(f, k, side);
+    const int st = G::stride(k);
+    const real *L = side ? Lp : Lm;
+#pragma unroll
+    for (int jd = 0; jd < D; ++jd)
+#pragma unroll
+        for (int v = 0; v < V; ++v) Q[jd][v] = 0;
+#pragma unroll
+    for (int m = 0; m < N; ++m) {
+        const real c = L[m];
+        const real *gd = sG + (j * G::NSP + base + m * st) * D * V;
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd) {
+            real g[V];
+            ld_v<V>(gd + jd * V, g);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Q[jd][v] += c * g[v];
+        }
+    }
+}
+
+// face state and gradient part of the viscous normal flux of every own flux
+// point with a partner, stored in the partner's inbound slots
+template <int D, int N, bool PAD, typename real>
+__device__ __forceinline__ void send_faces(const KArgs<real> &a, const real *sU, const real *sG, const real *Lm,
+                                           const real *Lp, int64_t e0, int ne) {
+    using G = Geo<D, N>;
+    constexpr int NFP = G::NFP, V = G::V;
+    constexpr bool PERT = sizeof(real) == 4;
+    for (int w = threadIdx.x; w < ne * NFP; w += blockDim.x) {
+        const int j = w / NFP, f = w % NFP;
+        const int64_t gf = (e0 + j) * NFP + f;
+        const int32_t pt = __ldg(a.PART + gf);
+        if (pt < 0) continue;
+        real uf[V], Q[D][V], nr[D], fvg[V], ufull[V];
+        interp_line<D, N, V, PAD>(sU, j, f, Lm, Lp, uf);
+        interp_grad<D, N>(sG, j, f, Lm, Lp, Q);
+        ldg_n<D>(a.NRM + gf * D, nr);
+        if constexpr (PERT) add_ref<V>(a.ref, uf, ufull);
+        else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) ufull[v] = uf[v];
+        }
+        flux_vis_n<D>(ufull, Q, nr, a.gamma, a.mu, a.prandtl, fvg);
+        st_v<V>(a.UFout + (int64_t)pt * V, uf);
+        st_v<V>(a.FVout + (int64_t)pt * V, fvg);
+    }
+}
+
+template <int D, int N, typename real, int L = 0>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, L>::value))
+k_stage(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
+    constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
+    constexpr int ITS = (NE * NSP + G::THREADS - 1) / G::THREADS;
+    constexpr bool PERT = sizeof(real) == 4;   // FP32 state: perturbations about a.ref
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sOp = reinterpret_cast<real *>(smem_raw);
+    real *sU = sOp + ops_slots(N);
+    constexpr bool PAD = G::FLUX_PAD;
+    real *sM = sU + pad4(NE * G::template slots<PAD>() * V);
+    real *sC = sM + pad4(NE * NSP * MS);
+    real *sD = sC + pad4(NE * NFP * V);
+    real *sF = sD + pad4(NE * NFP * V);   // [j][k][s][v]; also the gradient sG [j][s][jd][v]
+    real *sG = sF;
+    LocalRef<D, real> *sLR = reinterpret_cast<LocalRef<D, real> *>(sF + pad4(NE * D * NSP * V));
+    real *sDiv = sF + pad4(NE * D * NSP * V) + lr_slots<D, N, real>();   // [k][j][s][v] (tensor-core option)
+    const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N, *GL = Lp + N, *GR = GL + N, *DT = GR + N;
+
+    const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
+    const int64_t e_end = a.elem0 + a.n_elem;
+    if (e0 >= e_end) return;
+    const int ne = (int)min((int64_t)NE, e_end - e0);
+    const int tid = threadIdx.x;
+    const int mode = a.mode;
+
+    // face data of this thread's flux points, issued first: partner index,
+    // normal, the partner's face state and gradient flux part, its lifting
+    // coefficients
+    int32_t pt[IT];
+    real nr[IT][D], uR[IT][V], fvp[IT][V], lfp[IT][D];
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        pt[it] = INT32_MIN;
+        if (w < ne * NFP) {
+            const int64_t gf = (e0 + w / NFP) * NFP + w % NFP;
+            pt[it] = __ldg(a.PART + gf);
+            ldg_n<D>(a.NRM + gf * D, nr[it]);
+            if (pt[it] >= 0) {
+                ldg_v<V>(a.UFin + gf * V, uR[it]);
+                ldg_v<V>(a.FVin + gf * V, fvp[it]);
+                ldg_n<D>(a.LFP + gf * D, lfp[it]);
+            }
+        }
+    }
+    real r1[ITS][V], r2[ITS][V];
+    const bool need_r1 = mode == M_LSRK || mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
+    const bool need_r2 = mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
+#pragma unroll
+    for (int it = 0; it < ITS; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w < ne * NSP) {
+            const int64_t g = ((e0 + w / NSP) * NSP + w % NSP) * V;
+            if (need_r1) ld_v<V>(a.R1 + g, r1[it]);
+            if (need_r2) ld_v<V>(a.R2 + g, r2[it]);
+        }
+    }
+    load_ops(a, sOp, N);
+    load_state_rows<N, V, PAD>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
+    load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
+    __syncthreads();
+    const bool local = PERT && a.local_ref && !a.DIVREF;
+    if (PERT && local && tid < ne)
+        make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
+    tile_gradient<D, N, PAD>(sU, sM, D1, sG, ne);
+    __syncthreads();
+
+    // 1) common normal flux (inviscid - BR2 viscous) at every own flux point
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NFP) continue;
+        const int j = w / NFP, f = w % NFP;
+        real uL[V], Q[D][V], lf[D];
+        interp_line<D, N, V, PAD>(sU, j, f, Lm, Lp, uL);
+        interp_grad<D, N>(sG, j, f, Lm, Lp, Q);
+        {
+            // own lifting coefficients: sum_m l_m g'_side(m) (1/J) S[k][:] along the line
+            int k, side;
+            const int base = G::line_base(f, k, side);
+            const int st = G::stride(k);
+            const real *L = side ? Lp : Lm;
+            const real *Gs = side ? GR : GL;
+#pragma unroll
+            for (int jd = 0; jd < D; ++jd) lf[jd] = 0;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                const real *M = sM + (j * NSP + base + m * st) * MS;
+                const real cg = L[m] * Gs[m] * M[D * D];
+#pragma unroll
+                for (int jd = 0; jd < D; ++jd) lf[jd] += cg * M[k * D + jd];
+            }
+        }
+        // FP32: inviscid terms relative to the element's reference (local) or the global one
+        const RefState<real> &rf = local ? sLR[j].r : a.ref;
+        real shift[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) shift[v] = local ? sLR[j].du[v] : real(0);
+        real ub[V], uRp[V], uLl[V], uRl[V];
+        const bool inner = pt[it] >= 0;
+        if (inner) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                uRp[v] = uR[it][v];
+                ub[v] = uL[v];
+                uLl[v] = uL[v] - shift[v];
+                uRl[v] = uRp[v] - shift[v];
+            }
+        } else {
+            const int b = -1 - pt[it];
+            real vref[D];
+#pragma unroll
+            for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d] - (local ? sLR[j].bv[d] : real(0));
+            if constexpr (PERT) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) uLl[v] = uL[v] - shift[v];
+                bc_states_pert<D>(a.BTAG[b], uLl, nr[it], vref, rf, a.gamma, uRl, ub);
+#pragma unroll
+                for (int v = 0; v < V; ++v) { uRp[v] = uRl[v] + shift[v]; ub[v] += shift[v]; }
+            } else {
+                bc_states<D>(a.BTAG[b], uL, nr[it], vref, a.gamma, a.rho_inf, a.p_inf, uRp, ub);
+            }
+        }
+        real Fs[V];
+        if constexpr (PERT) common_inviscid_pert<D>(a.flux, uLl, uRl, nr[it], rf, a.gamma, Fs);
+        else common_inviscid<D>(a.flux, uL, uRp, nr[it], a.gamma, Fs);
+        real dd[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) dd[v] = inner ? real(0.5) * (uRp[v] - uL[v]) : ub[v] - uL[v];
+        // own side: F_v(u_b, Q + eta lf (x) dd) . n
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd)
+#pragma unroll
+            for (int v = 0; v < V; ++v) Q[jd][v] += a.eta * lf[jd] * dd[v];
+        real ubf[V], fvo[V];
+        if constexpr (PERT) add_ref<V>(a.ref, ub, ubf);
+        else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) ubf[v] = ub[v];
+        }
+        flux_vis_n<D>(ubf, Q, nr[it], a.gamma, a.mu, a.prandtl, fvo);
+        if (inner) {
+            // partner side: its gradient part plus its lifting of its jump -dd,
+            // along its normal -n; common flux 1/2 (own - partner) along n
+            real uRf[V], lfe[D], ddp[V], nn[D], fl[V];
+            if constexpr (PERT) add_ref<V>(a.ref, uRp, uRf);
+            else {
+#pragma unroll
+                for (int v = 0; v < V; ++v) uRf[v] = uRp[v];
+            }
+#pragma unroll
+            for (int d = 0; d < D; ++d) { lfe[d] = a.eta * lfp[it][d]; nn[d] = -nr[it][d]; }
+#pragma unroll
+            for (int v = 0; v < V; ++v) ddp[v] = -dd[v];
+            flux_vis_lift_n<D>(uRf, lfe, ddp, nn, a.gamma, a.mu, a.prandtl, fl);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Fs[v] -= real(0.5) * (fvo[v] - (fvp[it][v] + fl[v]));
+        } else {
+            if (a.BTAG[-1 - pt[it]] == BC_WALL) fvo[V - 1] = 0;   // adiabatic wall
+#pragma unroll
+            for (int v = 0; v < V; ++v) Fs[v] -= fvo[v];
+        }
+        st_v<V>(sD + (j * NFP + f) * V, dd);
+        st_v<V>(sC + (j * NFP + f) * V, Fs);
+    }
+    __syncthreads();
+
+    // 2) transformed flux at the solution points with the corrected gradient
+    // (uncorrected gradient from sG plus the face jumps' correction); sF
+    // overwrites sG, so every thread takes its points' gradients first
+    real gu[ITS][D][V];
+#pragma unroll
+    for (int it = 0; it < ITS; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NSP) continue;
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd) ld_v<V>(sG + w * D * V + jd * V, gu[it][jd]);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int it = 0; it < ITS; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NSP) continue;
+        const int j = w / NSP, s = w % NSP;
+        const real *M = sM + (j * NSP + s) * MS;
+        const real iJ = M[D * D];
+        real uu[V];
+        ld_v<V>(sU + G::template slot<PAD>(j * NSP + s) * V, uu);
+        real F[D][V];
+        if constexpr (PERT) {
+            real ul[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) ul[v] = uu[v] - (local ? sLR[j].du[v] : real(0));
+            flux_inv_pert<D>(ul, local ? sLR[j].r : a.ref, a.gamma - real(1), F);
+        } else {
+            flux_inv<D>(uu, a.gamma - real(1), F);
+        }
+        real Ck[D][V];
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            const int ik = G::digit(s, k);
+            real dm[V], dp[V];
+            ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 0)) * V, dm);
+            ld_v<V>(sD + (j * NFP + G::fp_of(s, k, 1)) * V, dp);
+#pragma unroll
+            for (int v = 0; v < V; ++v) Ck[k][v] = GL[ik] * dm[v] + GR[ik] * dp[v];
+        }
+        real gr[D][V];
+#pragma unroll
+        for (int jd = 0; jd < D; ++jd)
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                real g = 0;
+#pragma unroll
+                for (int k = 0; k < D; ++k) g += M[k * D + jd] * Ck[k][v];
+                gr[jd][v] = gu[it][jd][v] + g * iJ;
+            }
+        real uf[V], Fv[D][V];
+        if constexpr (PERT) add_ref<V>(a.ref, uu, uf);
+        else {
+#pragma unroll
+            for (int v = 0; v < V; ++v) uf[v] = uu[v];
+        }
+        flux_vis<D>(uf, gr, a.gamma, a.mu, a.prandtl, Fv);
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            real t[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                real acc = 0;
+#pragma unroll
+                for (int jd = 0; jd < D; ++jd) acc += M[k * D + jd] * (F[jd][v] - Fv[jd][v]);
+                t[v] = acc;
+            }
+            st_v<V>(sF + ((j * D + k) * NSP + s) * V, t);
+        }
+    }
+    __syncthreads();
+
+    // 3) divergence + correction, residual, RK update (as K_FLUX)
+    const bool tc = PERT && a.tc;
+    if constexpr (PERT) {
+        if (tc) {
+            tc_divergence<D, N>(sF, sC, DT, GL, GR, sDiv, ne);
+            __syncthreads();
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < ITS; ++it) {
+        const int w = tid + it * G::THREADS;
+        if (w >= ne * NSP) continue;
+        const int j = w / NSP, s = w % NSP;
+        const int64_t e = e0 + j;
+        real div[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) div[v] = 0;
+        if (tc) {
+#pragma unroll
+            for (int k = 0; k < D; ++k) {
+                real x[V];
+                ld_v<V>(sDiv + ((k * NE + j) * NSP + s) * V, x);
+#pragma unroll
+                for (int v = 0; v < V; ++v) div[v] += x[v];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < D; ++k) {
+            if (tc) break;
+            const int ik = G::digit(s, k), st = G::stride(k);
+            const real *row = DT + ik * N;
+            const int q0 = (j * D + k) * NSP + s - ik * st;
+#pragma unroll
+            for (int m = 0; m < N; ++m) {
+                real x[V];
+                ld_v<V>(sF + (q0 + m * st) * V, x);
+                const real c = row[m];
+#pragma unroll
+                for (int v = 0; v < V; ++v) div[v] += c * x[v];
+            }
+            real jm[V], jp[V];
+            ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 0)) * V, jm);
+            ld_v<V>(sC + (j * NFP + G::fp_of(s, k, 1)) * V, jp);
+#pragma unroll
+            for (int v = 0; v < V; ++v) div[v] += GR[ik] * jp[v] - GL[ik] * jm[v];
+        }
+        const real iJ = sM[(j * NSP + s) * MS + D * D];
+        const int64_t g = (e * NSP + s) * V;
+        if (PERT && a.DIVREF) {
+            real dr[V];
+            ldg_v<V>(a.DIVREF + g, dr);
+#pragma unroll
+            for (int v = 0; v < V; ++v) div[v] += dr[v];
+        }
+        real *su = sU + G::template slot<PAD>(j * NSP + s) * V;
+        real u0[V], un[V], R[V];
+        ld_v<V>(su, u0);
+#pragma unroll
+        for (int v = 0; v < V; ++v) R[v] = -div[v] * iJ;
+        if (mode == M_RESIDUAL) {
+            st_v<V>(a.RES + g, R);
+            continue;
+        }
+        if (mode == M_RESIDUAL_J) {
+            real jr[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) jr[v] = -div[v];
+            st_v<V>(a.RES + g, jr);
+            continue;
+        }
+        if (mode == M_LSRK_FIRST || mode == M_LSRK) {
+            real dU[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                dU[v] = (mode == M_LSRK) ? a.rk_a * r1[it][v] + a.dt * R[v] : a.dt * R[v];
+                un[v] = u0[v] + a.rk_b * dU[v];
+            }
+            st_v<V>(a.R1 + g, dU);
+        } else if (mode == M_RK4_1) {
+            st_v<V>(a.R1 + g, u0);
+            st_v<V>(a.R2 + g, R);
+#pragma unroll
+            for (int v = 0; v < V; ++v) un[v] = u0[v] + a.rk_c * R[v];
+        } else if (mode == M_RK4_2 || mode == M_RK4_3) {
+            real acc[V];
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                acc[v] = r2[it][v] + real(2) * R[v];
+                un[v] = r1[it][v] + a.rk_c * R[v];
+            }
+            st_v<V>(a.R2 + g, acc);
+        } else {  // M_RK4_4
+#pragma unroll
+            for (int v = 0; v < V; ++v) un[v] = r1[it][v] + a.rk_c * (r2[it][v] + R[v]);
+        }
+        st_v<V>(a.U + g, un);
+        st_v<V>(su, un);
+    }
+    if (mode == M_RESIDUAL || mode == M_RESIDUAL_J) return;
+    __syncthreads();
+
+    // 4) the new state's gradient, then face state + gradient flux part to
+    // the partners' inbound slots for the next stage
+    tile_gradient<D, N, PAD>(sU, sM, D1, sG, ne);
+    __syncthreads();
+    send_faces<D, N, PAD>(a, sU, sG, Lm, Lp, e0, ne);
+}
+
+// K_INTERP of the fused viscous stage: face states and gradient flux parts
+// of the current state (after fr_set_state)
+template <int D, int N, typename real>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS)
+k_interp_visc(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, V = G::V, MS = G::MS, NE = G::NE;
+    constexpr bool PAD = G::FLUX_PAD;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    real *sOp = reinterpret_cast<real *>(smem_raw);
+    real *sU = sOp + ops_slots(N);
+    real *sM = sU + pad4(NE * G::template slots<PAD>() * V);
+    real *sG = sM + pad4(NE * NSP * MS);
+    const real *D1 = sOp, *Lm = sOp + N * N, *Lp = Lm + N;
+    const int64_t e0 = a.elem0 + (int64_t)blockIdx.x * NE;
+    const int64_t e_end = a.elem0 + a.n_elem;
+    if (e0 >= e_end) return;
+    const int ne = (int)min((int64_t)NE, e_end - e0);
+    load_ops(a, sOp, N);
+    load_state_rows<N, V, PAD>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
+    load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
+    __syncthreads();
+    tile_gradient<D, N, PAD>(sU, sM, D1, sG, ne);
+    __syncthreads();
+    send_faces<D, N, PAD>(a, sU, sG, Lm, Lp, e0, ne);
 }
 
 // --------------------------------------------------------------------------
@@ -1154,10 +2212,15 @@ __global__ void k_probe(const KArgs<real> a) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) u[v] += __shfl_xor_sync(0xffffffffu, u[v], o);
     if (lane != 0) return;
+    if (sizeof(real) == 4) {
+        // perturbation storage: the weights sum to one, so the reference is added once
+#pragma unroll
+        for (int v = 0; v < V; ++v) u[v] += a.uref64[v];
+    }
     double ke = 0.0;
 #pragma unroll
     for (int i = 0; i < D; ++i) ke += u[1 + i] * u[1 + i];
-    const double p = ((double)a.gamma - 1.0) * (u[V - 1] - 0.5 * ke / u[0]);
+    const double p = (a.gamma64 - 1.0) * (u[V - 1] - 0.5 * ke / u[0]);
     ProbeAcc &A = a.pacc[pr];
     const double n = A.count + 1.0;
     A.count = n;
@@ -1196,15 +2259,22 @@ __global__ void k_integral(const KArgs<real> a) {
 #pragma unroll
         for (int d = 0; d < D; ++d) { w *= a.opW[t % N]; t /= N; }
         const real *src;
+        double off[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) off[v] = 0.0;
         if (a.integral_src == 0) {
             w /= (double)a.MET[(e * NSP + s) * MS + D * D];
             src = a.U + (e * NSP + s) * V;
+            if (sizeof(real) == 4) {
+#pragma unroll
+                for (int v = 0; v < V; ++v) off[v] = a.uref64[v];
+            }
         } else {
             src = a.RES + (e * NSP + s) * V;
         }
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            const double x = (double)src[v];
+            const double x = (double)src[v] + off[v];
             if (!isfinite(x)) bad += 1.0;
             acc[v] += w * x;
         }
@@ -1233,22 +2303,72 @@ __global__ void k_integral(const KArgs<real> a) {
     }
 }
 
+// One block of kReduceThreads threads: thread t folds a fixed contiguous
+// run of the partial-sum blocks in order (Neumaier), then a fixed-shape
+// pairwise tree combines the threads' compensated sums.  The shape depends
+// only on the number of partials, so the result is deterministic.
+constexpr int kReduceThreads = 256;
+
 template <int D, int N, typename real>
-__global__ void k_reduce(const KArgs<real> a) {
+__global__ void __launch_bounds__(kReduceThreads) k_reduce(const KArgs<real> a) {
     constexpr int V = D + 2;
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double ss[kReduceThreads][V], sc[kReduceThreads][V], sb[kReduceThreads];
+    const int t = threadIdx.x;
     double s[V], c[V], bad = 0.0;
+#pragma unroll
     for (int v = 0; v < V; ++v) { s[v] = 0.0; c[v] = 0.0; }
-    for (int64_t b = 0; b < a.n_partials; ++b) {
+    const int64_t per = (a.n_partials + kReduceThreads - 1) / kReduceThreads;
+    const int64_t b0 = (int64_t)t * per, b1 = min(a.n_partials, b0 + per);
+    for (int64_t b = b0; b < b1; ++b) {
         const double *in = a.partials + b * (2 * V + 1);
+#pragma unroll
         for (int v = 0; v < V; ++v) {
             neumaier_add(s[v], c[v], in[v]);
             neumaier_add(s[v], c[v], in[V + v]);
         }
         bad += in[2 * V];
     }
-    for (int v = 0; v < V; ++v) a.reduce_out[v] = s[v] + c[v];
-    a.reduce_out[V] = bad;
+#pragma unroll
+    for (int v = 0; v < V; ++v) { ss[t][v] = s[v]; sc[t][v] = c[v]; }
+    sb[t] = bad;
+    __syncthreads();
+    for (int h = kReduceThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+#pragma unroll
+            for (int v = 0; v < V; ++v) {
+                double x = ss[t][v], cx = sc[t][v];
+                neumaier_add(x, cx, ss[t + h][v]);
+                ss[t][v] = x;
+                sc[t][v] = cx + sc[t + h][v];
+            }
+            sb[t] += sb[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        for (int v = 0; v < V; ++v) a.reduce_out[v] = ss[0][v] + sc[0][v];
+        a.reduce_out[V] = sb[0];
+    }
+}
+
+// --------------------------------------------------------------------------
+// K_FINITE: scan the state of an element range; an instance with a NaN or
+// Inf value gets its flag set (sticky until its state is set again)
+// --------------------------------------------------------------------------
+template <int D, int N, typename real>
+__global__ void k_finite(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int V = G::V, NSP = G::NSP;
+    const int64_t total = a.n_elem * NSP;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = a.elem0 + i / NSP;
+        const real *u = a.U + (e * NSP + i % NSP) * V;
+        bool bad = false;
+#pragma unroll
+        for (int v = 0; v < V; ++v) bad |= !isfinite(u[v]);
+        if (bad) atomicOr(&a.FLAGS[a.EINST[e]], 1);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -1260,8 +2380,11 @@ __global__ void k_to_real(const KArgs<real> a) {
     const int64_t total = a.n_elem * G::NSP * G::V;
     const int64_t off = a.elem0 * G::NSP * G::V;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x)
-        a.U[off + i] = (real)a.stage64[i];
+         i += (int64_t)gridDim.x * blockDim.x) {
+        // FP32: store the perturbation about the reference state
+        const double r = sizeof(real) == 4 ? a.uref64[i % G::V] : 0.0;
+        a.U[off + i] = (real)(a.stage64[i] - r);
+    }
 }
 
 template <int D, int N, typename real>
@@ -1270,9 +2393,10 @@ __global__ void k_to_f64(const KArgs<real> a) {
     const int64_t total = a.n_elem * G::NSP * G::V;
     const int64_t off = a.elem0 * G::NSP * G::V;
     const real *src = a.integral_src ? a.RES : a.U;
+    const bool shift = sizeof(real) == 4 && !a.integral_src;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x)
-        a.stage64_out[i] = (double)src[off + i];
+        a.stage64_out[i] = (double)src[off + i] + (shift ? a.uref64[i % G::V] : 0.0);
 }
 
 // --------------------------------------------------------------------------
@@ -1313,6 +2437,7 @@ struct MArgs {
     const real *mats;
     real gamma, ldg_beta, ldg_tau;
     int flux, ldg, visc, pass;
+    RefState<real> ref;        // FP32: states are perturbations about it
 };
 
 template <int D, typename real>
@@ -1367,7 +2492,8 @@ __global__ void __launch_bounds__(128) k_mortar(const MArgs<real> a) {
         }
 #pragma unroll
         for (int d = 0; d < D; ++d) nr[d] = a.NRM[F.ghi][hf * D + d];
-        common_inviscid<D>(a.flux, uL, uR, nr, a.gamma, Fs);
+        if constexpr (sizeof(real) == 4) common_inviscid_pert<D>(a.flux, uL, uR, nr, a.ref, a.gamma, Fs);
+        else common_inviscid<D>(a.flux, uL, uR, nr, a.gamma, Fs);
         if (a.visc) {
             real fl[V];
 #pragma unroll
@@ -1425,19 +2551,27 @@ cudaError_t launch_mortar(const MArgs<real> &a, cudaStream_t st) {
 // launch glue (instantiated per dimension and precision)
 // --------------------------------------------------------------------------
 template <int D, int N, typename real>
-size_t smem_bytes(int kind, bool visc) {
+size_t smem_bytes(int kind, bool visc, bool tc = false) {
     using G = Geo<D, N>;
     constexpr int NE = G::NE, NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS;
     size_t n = ops_slots(N);
     constexpr bool GP = G::GRAD_PAD, FP = G::FLUX_PAD;
+    constexpr int LR = lr_slots<D, N, real>();
+    // tensor-core option (FP32): per-direction results [k][j][s][v]
+    const int TC = (tc && sizeof(real) == 4) ? pad4(D * NE * NSP * V) : 0;
     if (kind == K_FLUX) {
         n += pad4(NE * G::template slots<FP>() * V) + pad4(NE * NSP * MS) +
-             pad4(NE * NFP * V) * (visc ? 2 : 1) + pad4(NE * D * NSP * V);
+             pad4(NE * NFP * V) * (visc ? 2 : 1) + pad4(NE * D * NSP * V) + LR + TC;
     } else if (kind == K_GRAD) {
         n += pad4(NE * G::template slots<GP>() * V) + pad4(NE * NSP * MS) + 2 * pad4(NE * NFP * V) +
              pad4(NE * NSP * D * V + (GP ? NE * (NSP / N) * V : 0));
     } else if (kind == K_INTERP) {
         n += pad4(NE * NSP * V);
+    } else if (kind == K_STAGE) {
+        n += pad4(NE * G::template slots<FP>() * V) + pad4(NE * NSP * MS) + 2 * pad4(NE * NFP * V) +
+             pad4(NE * D * NSP * V) + LR + TC;
+    } else if (kind == K_INTERP_VISC) {
+        n += pad4(NE * G::template slots<FP>() * V) + pad4(NE * NSP * MS) + pad4(NE * NSP * D * V);
     }
     return n * sizeof(real);
 }
@@ -1453,16 +2587,17 @@ template <int D, int N, typename real>
 cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, cudaStream_t st) {
     using G = Geo<D, N>;
     const int64_t tiles = (a.n_elem + G::NE - 1) / G::NE;
+    const bool l1 = has_level1<N, real>() && a.regs_level == 1;
     if (kind == K_FLUX) {
         if (a.n_elem <= 0) return cudaSuccess;
-        const size_t sm = smem_bytes<D, N, real>(K_FLUX, visc);
+        const size_t sm = smem_bytes<D, N, real>(K_FLUX, visc, a.tc != 0);
         if (visc) {
-            auto k = k_flux<D, N, real, true>;
+            auto k = l1 ? k_flux<D, N, real, true, has_level1<N, real>() ? 1 : 0> : k_flux<D, N, real, true, 0>;
             cudaError_t err = prep_smem(k, sm);
             if (err != cudaSuccess) return err;
             k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
         } else {
-            auto k = k_flux<D, N, real, false>;
+            auto k = l1 ? k_flux<D, N, real, false, has_level1<N, real>() ? 1 : 0> : k_flux<D, N, real, false, 0>;
             cudaError_t err = prep_smem(k, sm);
             if (err != cudaSuccess) return err;
             k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
@@ -1470,7 +2605,7 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     } else if (kind == K_GRAD) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_GRAD, true);
-        auto k = k_grad<D, N, real>;
+        auto k = l1 ? k_grad<D, N, real, has_level1<N, real>() ? 1 : 0> : k_grad<D, N, real, 0>;
         cudaError_t err = prep_smem(k, sm);
         if (err != cudaSuccess) return err;
         k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
@@ -1481,17 +2616,34 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
         cudaError_t err = prep_smem(k, sm);
         if (err != cudaSuccess) return err;
         k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+    } else if (kind == K_STAGE) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        const size_t sm = smem_bytes<D, N, real>(K_STAGE, true, a.tc != 0);
+        auto k = l1 ? k_stage<D, N, real, has_level1<N, real>() ? 1 : 0> : k_stage<D, N, real, 0>;
+        cudaError_t err = prep_smem(k, sm);
+        if (err != cudaSuccess) return err;
+        k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+    } else if (kind == K_INTERP_VISC) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        const size_t sm = smem_bytes<D, N, real>(K_INTERP_VISC, true);
+        auto k = k_interp_visc<D, N, real>;
+        cudaError_t err = prep_smem(k, sm);
+        if (err != cudaSuccess) return err;
+        k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
     } else if (kind == K_PROBE) {
         if (a.n_probe <= 0) return cudaSuccess;
         k_probe<D, N, real><<<(a.n_probe + 3) / 4, 128, 0, st>>>(a);
     } else if (kind == K_INTEGRAL) {
         k_integral<D, N, real><<<grid_hint, 256, 0, st>>>(a);
     } else if (kind == K_REDUCE) {
-        k_reduce<D, N, real><<<1, 32, 0, st>>>(a);
+        k_reduce<D, N, real><<<1, kReduceThreads, 0, st>>>(a);
     } else if (kind == K_TO_REAL) {
         k_to_real<D, N, real><<<grid_hint, 256, 0, st>>>(a);
     } else if (kind == K_TO_F64) {
         k_to_f64<D, N, real><<<grid_hint, 256, 0, st>>>(a);
+    } else if (kind == K_FINITE) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        k_finite<D, N, real><<<grid_hint, 256, 0, st>>>(a);
     } else {
         return cudaErrorInvalidValue;
     }

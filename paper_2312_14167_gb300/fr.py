@@ -34,6 +34,8 @@ EXPORTED = ["fr_mesh_create", "fr_mesh_create_varp", "fr_mesh_degrees", "fr_mesh
             "fr_probe_history",
             "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
             "fr_integral", "fr_integral_static", "fr_last_launch_count", "fr_profile_steps",
+            "fr_instance_status", "fr_force_coefficients", "fr_tune", "fr_schedule", "fr_tune_lookup",
+            "fr_alu_peak",
             "fr_last_error"]
 
 
@@ -49,14 +51,15 @@ class Config(C.Structure):
                 ("inflow_delta", C.c_double), ("inflow_ywall", C.c_double),
                 ("br2_eta", C.c_double), ("dt", C.c_double), ("viscous", C.c_int),
                 ("rk", C.c_int), ("precision", C.c_int), ("flux", C.c_int),
-                ("viscous_scheme", C.c_int), ("reserved", C.c_int), ("ldg_beta", C.c_double),
-                ("ldg_tau", C.c_double)]
+                ("viscous_scheme", C.c_int), ("check_every", C.c_int), ("ldg_beta", C.c_double),
+                ("ldg_tau", C.c_double), ("flux_reference", C.c_int), ("reserved", C.c_int)]
 
 
 def make_config(dim, gamma=1.4, prandtl=0.71, mu=0.0, rho_inf=1.0, v_inf=None, p_inf=1.0,
                 inflow_delta=0.0, inflow_ywall=0.0, br2_eta=0.0, dt=1e-3, viscous=False,
                 rk=FR_LSRK45, precision=FR_FP64, flux=FR_FLUX_RUSANOV,
-                viscous_scheme=FR_VISC_BR2, ldg_beta=0.5, ldg_tau=0.1) -> Config:
+                viscous_scheme=FR_VISC_BR2, ldg_beta=0.5, ldg_tau=0.1, check_every=0,
+                flux_reference=0) -> Config:
     c = Config()
     c.gamma, c.prandtl, c.mu = gamma, prandtl, mu
     c.rho_inf, c.p_inf = rho_inf, p_inf
@@ -67,6 +70,8 @@ def make_config(dim, gamma=1.4, prandtl=0.71, mu=0.0, rho_inf=1.0, v_inf=None, p
     c.br2_eta, c.dt = br2_eta, dt
     c.viscous, c.rk, c.precision, c.flux = int(bool(viscous)), rk, precision, flux
     c.viscous_scheme, c.ldg_beta, c.ldg_tau = viscous_scheme, ldg_beta, ldg_tau
+    c.check_every = int(check_every)
+    c.flux_reference = int(flux_reference)
     return c
 
 
@@ -103,7 +108,7 @@ def lib():
     L.fr_accumulators_size.argtypes = [P]
     L.fr_accumulators_size.restype = C.c_int64
     L.fr_get_accumulators.argtypes = [P, dp]
-    L.fr_set_accumulators.argtypes = [P, dp]
+    L.fr_set_accumulators.argtypes = [P, dp, I64]
     L.fr_get_states.argtypes = [P, dp]
     L.fr_residual.argtypes = [P, I, dp]
     L.fr_rk_step.argtypes = [P, I]
@@ -117,6 +122,12 @@ def lib():
     L.fr_conservation.argtypes = [P, I, dp]
     L.fr_integral.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
     L.fr_integral_static.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
+    L.fr_instance_status.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(I)]
+    L.fr_force_coefficients.argtypes = [P, I, D, dp, dp]
+    L.fr_tune.argtypes = [P, C.c_char_p, I, C.c_char_p, C.c_size_t]
+    L.fr_schedule.argtypes = [P, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t]
+    L.fr_tune_lookup.argtypes = [C.c_char_p, C.c_char_p, C.c_char_p, C.c_size_t]
+    L.fr_alu_peak.argtypes = [I, dp]
     L.fr_last_launch_count.argtypes = [P]
     L.fr_last_launch_count.restype = C.c_int64
     L.fr_profile_steps.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
@@ -128,6 +139,20 @@ def lib():
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
+
+
+def alu_peak(precision):
+    """fr_alu_peak: measured FMA-pipe peak of the current GPU in flop/s."""
+    out = C.c_double()
+    _check(lib().fr_alu_peak(precision, C.byref(out)), "fr_alu_peak")
+    return out.value
+
+
+def tune_lookup(cache_path, key):
+    """fr_tune_lookup (host only): the cached schedule under key, or None."""
+    buf = C.create_string_buffer(256)
+    st = lib().fr_tune_lookup(os.fsencode(cache_path), key.encode(), buf, 256)
+    return buf.value.decode() if st == FR_OK else None
 
 
 def _check(st, where):
@@ -290,7 +315,7 @@ class Solver:
         acc = np.ascontiguousarray(acc, dtype=np.float64)
         if acc.size != int(lib().fr_accumulators_size(self.handle)):
             raise ValueError("accumulator checkpoint size")
-        _check(lib().fr_set_accumulators(self.handle, _dptr(acc)), "fr_set_accumulators")
+        _check(lib().fr_set_accumulators(self.handle, _dptr(acc), acc.size), "fr_set_accumulators")
 
     def residual(self, inst, out=None):
         out = self._out(inst, out)
@@ -340,6 +365,13 @@ class Solver:
         _check(lib().fr_forces(self.handle, inst, _dptr(out)), "fr_forces")
         return out[:self.dim]
 
+    def force_coefficients(self, inst, a_ref):
+        """(mean C_L, mean C_D) of fr_force_coefficients."""
+        cl, cd = C.c_double(), C.c_double()
+        _check(lib().fr_force_coefficients(self.handle, inst, a_ref, C.byref(cl), C.byref(cd)),
+               "fr_force_coefficients")
+        return cl.value, cd.value
+
     def conservation(self, inst):
         out = np.zeros(self.V)
         _check(lib().fr_conservation(self.handle, inst, _dptr(out)), "fr_conservation")
@@ -372,6 +404,32 @@ class Solver:
         if st not in (0, 5):
             _check(st, "fr_integral_static")
         return out, bad.value
+
+    def tune(self, cache_path=None, mode=0):
+        """fr_tune: measure (or look up) the stage schedule; returns the
+        choice string.  Call before set_state (it starts from the free
+        stream)."""
+        buf = C.create_string_buffer(512)
+        path = None if cache_path is None else os.fsencode(cache_path)
+        _check(lib().fr_tune(self.handle, path, mode, buf, 512), "fr_tune")
+        return buf.value.decode()
+
+    def schedule(self):
+        """(schedule string, cache key) of fr_schedule."""
+        a, b = C.create_string_buffer(256), C.create_string_buffer(256)
+        _check(lib().fr_schedule(self.handle, a, 256, b, 256), "fr_schedule")
+        return a.value.decode(), b.value.decode()
+
+    def instance_status(self):
+        """(flags, first_bad) of fr_instance_status: one flag per instance,
+        set where a scan found NaN/Inf (needs check_every > 0 in the config);
+        first_bad = -1 when none."""
+        flags = np.zeros(len(self.meshes), dtype=np.int32)
+        first = C.c_int()
+        st = lib().fr_instance_status(self.handle, flags.ctypes.data_as(C.POINTER(C.c_int32)), C.byref(first))
+        if st not in (0, 5):
+            _check(st, "fr_instance_status")
+        return flags, first.value
 
     def synchronize(self):
         self.stream.synchronize()

@@ -1,13 +1,14 @@
 """Host-side optimisation loop around the GPU FR solver.
 
-The outer level of the paper's two-level parallelism (Sec. 2.2, Algorithm 1):
-MADS with a minimal positive basis (Delta_p = n sqrt(Delta_m)) or OrthoMADS
-with a maximal basis (Delta_p = sqrt(Delta_m)); the mesh size grows by 4
-after a successful poll and shrinks by 4 after an unsuccessful one, is capped
-at its initial value, and the loop stops once Delta_m < 1e-6 and the design
-changed by less than 1 % between consecutive iterations.  All candidates of a
-poll are evaluated concurrently: ``BatchedPollEvaluator`` advances them as one
-batch of instances in a single solver on the GPU.
+The outer level of the paper's two-level parallelism (Sec. 2.2): mesh
+adaptive direct search with a minimal positive basis (poll size
+n sqrt(mesh size)) or the OrthoMADS maximal basis (poll size
+sqrt(mesh size)); the mesh coarsens four-fold after an improving poll and
+refines four-fold after a failed one, never beyond its initial size, and the
+search ends once the mesh is finer than 1e-6 and the design moved by less
+than 1 % over a poll.  All candidates of a poll are evaluated concurrently:
+``BatchedPollEvaluator`` advances them as one batch of instances in a single
+solver on the GPU.
 
 Also here: the penalised airfoil objective of Sec. 5.2 and a Welch power
 spectral density of observer signals (Welch's averaged modified periodogram,
@@ -83,64 +84,83 @@ def poll_directions(t: int, n: int, delta_m: float, delta_p: float, basis: str) 
 
 
 # --------------------------------------------------------------------------
-# Algorithm 1
+# the optimisation loop (Sec. 2.2)
 # --------------------------------------------------------------------------
 
 @dataclass
 class MadsResult:
     x: np.ndarray
     f: float
-    iterations: int           # successful iterations ("iter" of Algorithm 1)
-    polls: int                # k
+    iterations: int           # polls that improved the incumbent
+    polls: int
     evaluations: int
-    # per poll: (k, Delta_m used by the poll, Delta_m after the update, incumbent, its objective)
+    # per poll: (poll number, mesh size the poll used, mesh size after it,
+    # incumbent after it, its objective)
     history: list = field(default_factory=list)
+
+
+def _trial_points(centre, poll_no, mesh_size, basis, lower, upper):
+    """The poll's trial designs: centre + each direction of the poll set
+    built for this poll (its own Halton point), dropping the null direction
+    and anything outside the bounds (an extreme barrier: never evaluated)."""
+    n = centre.size
+    dirs = poll_directions(poll_no, n, mesh_size, poll_size(mesh_size, n, basis), basis)
+    pts = (centre + d for d in dirs if np.any(d))
+    return [q for q in pts if np.all(q >= lower) and np.all(q <= upper)]
+
+
+def _improvement(scores, best):
+    """Index of the best strictly improving score, or None."""
+    if not scores:
+        return None
+    i = int(np.argmin(scores))
+    return i if scores[i] < best else None
+
+
+def _settled(mesh_size, x, before, tol_m, tol_x):
+    """Stopping rule: the mesh is finer than tol_m and no design variable
+    moved by more than tol_x (relative) over the last poll."""
+    moved = np.max(np.abs(x - before) / np.maximum(np.abs(before), 1e-300))
+    return mesh_size < tol_m and moved < tol_x
 
 
 def mads(evaluate_poll, x0, delta_m0: float, lower, upper, basis: str = "maximal",
          max_polls: int = 200, tol_m: float = 1e-6, tol_x: float = 0.01) -> MadsResult:
-    """Run Algorithm 1.  ``evaluate_poll(list of designs) -> list of
-    objective values`` evaluates all candidates of a poll together (they are
-    independent: one batched solver run).  Candidates outside [lower, upper]
-    are not evaluated (objective +inf)."""
-    x = np.asarray(x0, float)
+    """Mesh adaptive direct search (Sec. 2.2, Algorithm 1).
+
+    Each poll evaluates the trial designs around the incumbent together
+    (``evaluate_poll(list of designs) -> list of objective values``; the
+    candidates are independent, so one batched solver run serves a whole
+    poll).  The mesh size a poll uses never exceeds the initial one; an
+    improving poll moves the incumbent to the best trial and coarsens the
+    mesh four-fold, a failed one refines it four-fold.  Trial designs outside
+    [lower, upper] are never evaluated."""
     lower, upper = np.asarray(lower, float), np.asarray(upper, float)
-    n = x.size
-    f_inc = float(evaluate_poll([x])[0])
-    n_eval = 1
-    dm = float(delta_m0)
-    k = it = 0
-    t = 1
-    x_prev = x.copy()
-    hist = []
-    while True:
-        if dm > delta_m0:
-            dm = delta_m0
-        dm_poll = dm
-        x_prev = x.copy()          # design of the previous iteration
-        dp = poll_size(dm, n, basis)
-        D = poll_directions(t, n, dm, dp, basis)
-        t += 1
-        cands = [x + d for d in D if np.any(d)]
-        feas = [c for c in cands if np.all(c >= lower) and np.all(c <= upper)]
-        fvals = [float(v) for v in evaluate_poll(feas)] if feas else []
-        n_eval += len(feas)
-        if fvals and min(fvals) < f_inc:
-            best = int(np.argmin(fvals))
-            dm *= 4.0
-            it += 1
-            x = feas[best]
-            f_inc = fvals[best]
+    incumbent = np.asarray(x0, float)
+    best = float(evaluate_poll([incumbent])[0])
+    evaluations, successes = 1, 0
+    mesh_size = float(delta_m0)
+    record = []
+    poll_no = 0
+    while poll_no < max_polls:
+        poll_no += 1
+        used = min(mesh_size, float(delta_m0))
+        before = incumbent.copy()
+        trials = _trial_points(incumbent, poll_no, used, basis, lower, upper)
+        scores = [float(v) for v in evaluate_poll(trials)] if trials else []
+        evaluations += len(trials)
+        win = _improvement(scores, best)
+        if win is None:
+            mesh_size = used / 4.0
         else:
-            dm /= 4.0
-        k += 1
-        hist.append((k, dm_poll, dm, x.copy(), f_inc))
-        rel = np.max(np.abs(x - x_prev) / np.maximum(np.abs(x_prev), 1e-300))
-        if dm < tol_m and rel < tol_x:
+            incumbent, best = trials[win], scores[win]
+            successes += 1
+            mesh_size = used * 4.0
+        record.append((poll_no, used, mesh_size, incumbent.copy(), best))
+        if _settled(mesh_size, incumbent, before, tol_m, tol_x):
             break
-        if k >= max_polls:
-            break
-    return MadsResult(x=x, f=f_inc, iterations=it, polls=k, evaluations=n_eval, history=hist)
+    return MadsResult(x=incumbent, f=best, iterations=successes, polls=poll_no,
+                      evaluations=evaluations, history=record)
 
 
 # --------------------------------------------------------------------------
@@ -202,19 +222,25 @@ class BatchedPollEvaluator:
     make_mesh(design) -> mesh (a ``synth.meshes.Mesh``-like object) with
     ``info["probe"]`` or ``info["probes"]``; ``start(x, design, mesh) -> u``
     gives the initial state at the solution points; ``objective(oaspl,
-    force, design) -> float`` turns the observer level and the mean wall force
-    into the objective.  Each call runs ``n_transient`` steps, resets the
-    observers, runs ``n_average`` steps and reads the OASPL (running-mean
-    reading of Eqs. 11-12) and the time-mean wall force of every candidate.
-    ``p`` is one degree for every element, or a callable mesh -> degree per
-    element (the far-field sponge zones of Sec. 5.1)."""
+    forces, design) -> float`` turns the observer level and the wall forces
+    into the objective, ``forces`` being the mean wall force vector, or, with
+    ``a_ref`` given, the pair (mean C_L, mean C_D) for that reference length
+    or area.  Each call runs ``n_transient`` steps, resets the observers,
+    runs ``n_average`` steps and reads the OASPL (running-mean reading of
+    Eqs. 11-12).  ``p`` is one degree for every element, or a callable
+    mesh -> degree per element (the far-field sponge zones of Sec. 5.1).
+    With ``config.check_every > 0`` a candidate whose flow went non-finite
+    during the run is flagged by the solver and scores +inf (rejected, like
+    an infeasible design)."""
 
     def __init__(self, make_mesh, p: int, config, n_transient: int, n_average: int, start,
-                 objective, p_ref: float = 2e-5, p_scale: float = 1.0, mean_mode: int = 0):
+                 objective, p_ref: float = 2e-5, p_scale: float = 1.0, mean_mode: int = 0,
+                 a_ref: float | None = None):
         self.make_mesh, self.p, self.cfg = make_mesh, p, config
         self.n_transient, self.n_average = n_transient, n_average
         self.start, self.objective = start, objective
         self.p_ref, self.p_scale, self.mean_mode = p_ref, p_scale, mean_mode
+        self.a_ref = a_ref
         self.last = None
 
     def __call__(self, designs):
@@ -232,11 +258,15 @@ class BatchedPollEvaluator:
         sol.rk_step(self.n_transient)
         sol.probe_reset()
         sol.rk_step(self.n_average)
+        failed = sol.instance_status()[0] if self.cfg.check_every > 0 else np.zeros(len(designs), np.int32)
         out = []
         for i, d in enumerate(designs):
+            if failed[i]:
+                out.append(math.inf)
+                continue
             level = sol.oaspl(ids[i], self.p_ref, self.p_scale, self.mean_mode)
-            force = sol.forces(i)
-            out.append(self.objective(level, force, d))
-        self.last = {"designs": list(designs), "objectives": out}
+            forces = sol.forces(i) if self.a_ref is None else sol.force_coefficients(i, self.a_ref)
+            out.append(self.objective(level, forces, d))
+        self.last = {"designs": list(designs), "objectives": out, "failed": [int(f) for f in failed]}
         sol.close()
         return out

@@ -21,6 +21,20 @@ def primitive_to_conserved(rho, vel, p, gamma=GAMMA):
     return np.concatenate([rho[..., None], mom, (p / (gamma - 1.0) + ke)[..., None]], -1)
 
 
+def reference_conserved(dim, rho_inf=1.0, v_inf=None, p_inf=1.0, gamma=GAMMA):
+    """Conserved free stream [rho, rho v, p/(gamma-1) + rho |v|^2 / 2]."""
+    v = np.zeros(dim) if v_inf is None else np.asarray(v_inf, float)[:dim]
+    return primitive_to_conserved(np.asarray(rho_inf, float), v, np.asarray(p_inf, float), gamma)
+
+
+def fp32_perturbation_input(u, uref):
+    """The state a mixed-precision (FP32) solver holds for the FP64 state u:
+    it stores the FP32 rounding of u - u_ref, u_ref's components themselves
+    rounded to FP32, so its arithmetic sees u_ref + fl32(u - u_ref)."""
+    r = np.asarray(uref, float).astype(np.float32).astype(np.float64)
+    return r + (u - r).astype(np.float32).astype(np.float64)
+
+
 # ---------------------------------------------------------------------------
 # isentropic vortex (Shu's form; beta=5, M=0.5 in the tiny workload)
 # ---------------------------------------------------------------------------

@@ -29,6 +29,7 @@ class Case:
     inflow_ywall: float = 0.0
     flux: str = "rusanov"
     viscous_scheme: str = "br2"
+    p_ref: float = 0.0             # free-stream pressure if not 1/(gamma M^2)
 
     @property
     def dim(self):
@@ -36,7 +37,7 @@ class Case:
 
     @property
     def p_inf(self):
-        return 1.0 / (GAMMA * self.mach ** 2)
+        return self.p_ref if self.p_ref > 0 else 1.0 / (GAMMA * self.mach ** 2)
 
 
 def oracle_disc(case: Case, inst: int = 0):
@@ -91,6 +92,13 @@ def cfl_dt(meshes, mach, p, cfl=0.4):
     return cfl * hmin / ((1.0 + c) * (p + 1) ** 2)
 
 
+def fp32_input(case: Case, u):
+    """The state the mixed-precision path computes with for the FP64 state u
+    (FP32 perturbation about the case's free stream)."""
+    ur = S.reference_conserved(case.dim, 1.0, case.v_inf[:case.dim], case.p_inf, GAMMA)
+    return S.fp32_perturbation_input(u, ur)
+
+
 def rel_l2(a, b):
     return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
 
@@ -101,7 +109,7 @@ def rel_l2(a, b):
 
 def vortex_case(n=16, p=2, jitter=0.0):
     return Case("vortex", [M.vortex_mesh(n, jitter=jitter)], p, False, 0.0, 0.5, rk="rk4",
-                dt=1e-3, v_inf=(0.5 * np.sqrt(GAMMA), 0.0))
+                dt=1e-3, v_inf=(0.5 * np.sqrt(GAMMA), 0.0), p_ref=1.0)
 
 
 def periodic_ns_case(n=6, p=3, jitter=0.2):

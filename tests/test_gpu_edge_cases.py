@@ -163,6 +163,7 @@ def test_checkpoint_resume_with_observers_is_bitwise_equal():
     states = [first.get_state(i) for i in range(2)]
     acc = first.get_accumulators()
     assert acc.size == fr.lib().fr_accumulators_size(first.handle) and acc[0] == 3 and acc[1] == 2
+    assert acc[2] == 2
     resumed = FC.lib_solver(case, "fp32")
     ids2 = [resumed.probe_add(i, np.asarray(case.meshes[i].info["probe"], float)) for i in range(2)]
     for i in range(2):
@@ -175,6 +176,49 @@ def test_checkpoint_resume_with_observers_is_bitwise_equal():
         assert np.allclose(resumed.forces(i), full.forces(i), rtol=1e-12, atol=0.0)
         assert np.array_equal(resumed.probe_history(ids2[i]), full.probe_history(ids[i]))
     lone = FC.lib_solver(case, "fp32")                 # no probes: the checkpoint does not fit
-    assert fr.lib().fr_set_accumulators(lone.handle, fr._dptr(acc)) == 1
+    assert fr.lib().fr_set_accumulators(lone.handle, fr._dptr(acc), acc.size) == 1
     with pytest.raises(ValueError):
         lone.set_accumulators(acc)
+    # same probe count, other locations: the fingerprint refuses it
+    other = FC.lib_solver(case, "fp32")
+    for i in range(2):
+        other.probe_add(i, np.asarray(case.meshes[i].info["probe"], float) + np.array([0.3, 0.2]))
+    assert fr.lib().fr_set_accumulators(other.handle, fr._dptr(acc), acc.size) == 1
+    # a solver with one instance fewer: the size check refuses it before any read
+    single = fr.Solver([fr.Mesh(case.meshes[0], case.p)], FC.lib_config(case, "fp32"))
+    single.probe_add(0, np.asarray(case.meshes[0].info["probe"], float))
+    single.probe_add(0, np.asarray(case.meshes[0].info["probe"], float))
+    assert fr.lib().fr_set_accumulators(single.handle, fr._dptr(acc), acc.size) == 1
+
+
+def test_non_finite_instance_is_flagged_inside_the_time_loop():
+    """A NaN planted (on the host) in one instance of a batch: the scan that
+    fr_rk_step appends every check_every steps flags that instance alone,
+    and the other instances advance exactly as they do alone."""
+    from paper_2312_14167_gb300 import fr
+    case = FC.airfoil_case(n_inst=3)
+    cfg = FC.lib_config(case, "fp32")
+    cfg.check_every = 2
+    ms = [fr.Mesh(m, case.p) for m in case.meshes]
+    sol = fr.Solver(ms, cfg)
+    us = [FC.initial_state(case, ms[i].sol_coords(), i) for i in range(3)]
+    bad = us[1].copy()
+    bad[5, 3, 0] = np.nan
+    for i in range(3):
+        sol.set_state(i, bad if i == 1 else us[i])
+    flags, first = sol.instance_status()
+    assert first == -1 and not flags.any()          # no scan has run yet
+    sol.rk_step(4)
+    flags, first = sol.instance_status()
+    assert first == 1 and list(flags) == [0, 1, 0]
+    assert sol.last_launch_count() > 0
+    for i in (0, 2):
+        solo = fr.Solver([ms[i]], cfg)
+        solo.set_state(0, us[i])
+        solo.rk_step(4)
+        assert np.array_equal(sol.get_state(i), solo.get_state(0))
+    # setting the instance's state again clears its flag
+    sol.set_state(1, us[1])
+    assert sol.instance_status()[1] == -1
+    sol.rk_step(2)
+    assert sol.instance_status()[1] == -1

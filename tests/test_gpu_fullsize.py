@@ -61,7 +61,7 @@ def _check_sampled(case, inst, sol_by_prec, us):
         print(f"{case.name}[{inst}] fp64 sampled: {FC.rel_l2(Rg, R64):.3e} (tol {tol:.3e})")
         assert FC.rel_l2(Rg, R64) < tol
     if "fp32" in sol_by_prec:
-        u32 = u.astype(np.float32).astype(np.float64)
+        u32 = FC.fp32_input(case, u)
         R32, mag = disc.residual(u32, el, magnitude=True)
         Rg = sol_by_prec["fp32"].residual(inst)[el]
         err = FC.rel_l2(Rg, R32)
@@ -181,7 +181,7 @@ def test_airfoil_sponge_candidate_full_size_parity():
     assert err < tol
     s32 = fr.Solver([fr.Mesh(m, ep)], FC.lib_config(case, "fp32"))
     s32.set_state(0, u)
-    u32 = u.astype(np.float32).astype(np.float64)
+    u32 = FC.fp32_input(case, u)
     R32, mag32 = d.residual(u32, magnitude=True)
     err32 = FC.rel_l2(s32.residual(0), R32)
     bound = 16 * EPS32 * np.linalg.norm(mag32) / np.linalg.norm(R32)

@@ -76,7 +76,7 @@ def _fp32_check(case, label):
     """Mixed-path residual against the oracle on the FP32-rounded input,
     within the forward error bound; prints the errors for the record."""
     sol, disc, states, Rg, Rr = _residual_pair(case, "fp32")
-    u32 = states[0].astype(np.float32).astype(np.float64)
+    u32 = FC.fp32_input(case, states[0])
     Rr32, mag = disc.residual(u32, magnitude=True)
     e_arith = FC.rel_l2(Rg, Rr32)
     e_total = FC.rel_l2(Rg, Rr)
@@ -247,6 +247,33 @@ def test_wall_force_matches_oracle():
     gross = case.p_inf * 2.2
     print("force gpu", got, "oracle", want)
     assert np.all(np.abs(got - want) < 1e-12 * gross)
+    # coefficients: free stream along +x, chord 1 -> C_D = F_x / q, C_L = F_y / q
+    q = 0.5 * 1.0 * 1.0 * 1.0
+    cl, cd = sol.force_coefficients(0, 1.0)
+    assert abs(cd - want[0] / q) < 1e-12 * gross / q and abs(cl - want[1] / q) < 1e-12 * gross / q
+
+
+def test_force_coefficients_rotate_into_the_wind_axes():
+    """A free stream at 30 degrees: drag is the force along it, lift the
+    force along it turned by +90 degrees (same wall forces, other axes)."""
+    from paper_2312_14167_gb300 import fr
+    case = FC.airfoil_case(n_inst=1, e_lo=400, e_hi=401)
+    u = FC.initial_state(case, FC.oracle_disc(case).sol_coords())
+    a = np.deg2rad(30.0)
+    cfg = FC.lib_config(case, "fp64")
+    cfg.v_inf[0], cfg.v_inf[1] = np.cos(a), np.sin(a)
+    sol = fr.Solver([fr.Mesh(case.meshes[0], case.p)], cfg)
+    sol.set_state(0, u)
+    sol.probe_reset()
+    sol.rk_step(2)
+    F = sol.forces(0)
+    cl, cd = sol.force_coefficients(0, 2.0)
+    q = 0.5 * 1.0 * 1.0 * 2.0
+    assert abs(cd - (F[0] * np.cos(a) + F[1] * np.sin(a)) / q) < 1e-13 * np.abs(F).max() / q
+    assert abs(cl - (-F[0] * np.sin(a) + F[1] * np.cos(a)) / q) < 1e-13 * np.abs(F).max() / q
+    import pytest as _pt
+    with _pt.raises(fr.FRError):
+        sol.force_coefficients(0, 0.0)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -266,7 +293,7 @@ def test_tandem_cylinders_3d_p4_batch_residual(precision):
         if precision == "fp64":
             assert FC.rel_l2(sol.residual(i), disc.residual(us[i])) < 1e-12
         else:
-            u32 = us[i].astype(np.float32).astype(np.float64)
+            u32 = FC.fp32_input(case, us[i])
             R32, mag = disc.residual(u32, magnitude=True)
             err = FC.rel_l2(sol.residual(i), R32)
             bound = C_FP32 * EPS32 * np.linalg.norm(mag) / np.linalg.norm(R32)

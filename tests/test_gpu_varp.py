@@ -156,7 +156,7 @@ def test_fp32_residual_within_forward_error_bound(name, scheme):
     sol = _solver([(m, ep)], True, scheme, "rusanov", "fp32", mu=mu)
     u = _state(sol.meshes[0].sol_coords(), m.dim, mesh=m)
     sol.set_state(0, u)
-    u32 = u.astype(np.float32).astype(np.float64)
+    u32 = S.fp32_perturbation_input(u, S.reference_conserved(m.dim, 1.0, (1.0, 0.0, 0.0), 1.0 / (GAMMA * MACH ** 2), GAMMA))
     R, mag = d.residual(u32, magnitude=True)
     err = _rel(sol.residual(0), R)
     bound = 16 * EPS32 * np.linalg.norm(mag) / np.linalg.norm(R)

@@ -129,3 +129,21 @@ def test_variable_degree_mesh_errors(fr):
     with pytest.raises(fr.FRError) as e:
         fr.Mesh(mesh, ep)
     assert e.value.status == 3
+
+
+def test_tuning_cache_lookup_and_fallback(fr, tmp_path):
+    """fr_tune_lookup reads the JSON cache fr_tune writes (one "key":
+    "value" pair per line); a missing key, a missing file or a line that is
+    not a pair gives no schedule (the solver then keeps or measures its own)."""
+    import json
+    path = tmp_path / "tune.json"
+    entries = {"sm_103|dim=2|p=3|V=4|fp32|br2|rusanov|mortar=0|log2sp=23": "stage=split;regs=1;ms=0.8",
+               "sm_103|dim=3|p=4|V=5|fp32|br2|rusanov|mortar=0|log2sp=24": "stage=fused;regs=0;ms=2.1"}
+    path.write_text(json.dumps(entries, indent=2))
+    for k, v in entries.items():
+        assert fr.tune_lookup(str(path), k) == v
+    assert fr.tune_lookup(str(path), "sm_103|dim=2|p=2|V=4|fp32|br2|rusanov|mortar=0|log2sp=23") is None
+    assert fr.tune_lookup(str(tmp_path / "missing.json"), next(iter(entries))) is None
+    path.write_text('{\n  not a pair\n  "k": "v"\n}\n')
+    assert fr.tune_lookup(str(path), "k") == "v"
+    assert fr.tune_lookup(str(path), "not a pair") is None

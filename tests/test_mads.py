@@ -138,3 +138,21 @@ def test_batched_poll_evaluator_runs_a_poll_on_the_gpu():
                                     cfg, 5, 20, start, objective, p_scale=101325 * 1.4 * 0.04)
     vals2 = ev2([np.array([0.02, 0.12]), np.array([0.03, 0.10])])
     assert len(vals2) == 2 and all(np.isfinite(vals2))
+    # coefficients from the library (chord 1) and the in-loop health scan: the
+    # objective sees (C_L, C_D); a candidate started from a NaN is rejected
+    cfg.check_every = 5
+
+    def objective_c(level, coeffs, d):
+        return mads.penalised_objective(level, coeffs[0], coeffs[1], 0.3, 0.05)
+
+    def start_bad(x, d, m):
+        u = start(x, d, m)
+        if d[0] > 0.025:
+            u[0, 0, 0] = np.nan
+        return u
+
+    ev3 = mads.BatchedPollEvaluator(make_mesh, 3, cfg, 5, 20, start_bad, objective_c,
+                                    p_scale=101325 * 1.4 * 0.04, a_ref=1.0)
+    vals3 = ev3([np.array([0.02, 0.12]), np.array([0.03, 0.10])])
+    assert np.isfinite(vals3[0]) and vals3[0] == pytest.approx(vals[0], rel=1e-12)
+    assert vals3[1] == math.inf and ev3.last["failed"] == [0, 1]
