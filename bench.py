@@ -325,7 +325,7 @@ class Clocks:
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                                       "-lms", "200", "-i", str(self.dev)], stdout=self.f,
+                                       "-lms", "50", "-i", str(self.dev)], stdout=self.f,
                                       stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -372,6 +372,11 @@ def algorithmic_bytes(E, s, kind, p=None):
     if kind == "flux":
         per = (NSP * V * s * (3 + 0.8) + NSP * MS * s + NFP * D * s + NFP * 4 + NFP * V * s
                + 2 * NFP * V * s + NFP * V * s)
+    elif kind == "stage":
+        # fused stage: state r+w, RK register (w + r in 4 of 5 stages), metrics,
+        # normals and partner lifting coefficients, partner indices, inbound and
+        # outbound face state and gradient flux part
+        per = (NSP * V * s * (3 + 0.8) + NSP * MS * s + 2 * NFP * D * s + NFP * 4 + 4 * NFP * V * s)
     else:
         per = NSP * V * s + NSP * MS * s + NFP * D * s + NFP * 4 + NFP * V * s + NFP * V * s
     return per * E
@@ -532,10 +537,12 @@ def run_gpu(args):
     kms, kcnt = sol.profile_steps(n_prof)
     kinds = ["flux", "grad", "probe", "force", "other"]
     share = {kinds[k]: float(kms[k] * kcnt[k]) for k in range(5)}
+    fused = "stage=fused" in schedule
     dom = max(("flux", "grad"), key=lambda k: share[k])
     kdx = kinds.index(dom)
+    dom_model = "stage" if (fused and dom == "flux") else dom
     # one stage's launches of the dominant kind (one per degree group)
-    alg = sum(algorithmic_bytes(int(by_p[q]), 4, dom, q) for q in range(0, 5) if by_p[q])
+    alg = sum(algorithmic_bytes(int(by_p[q]), 4, dom_model, q) for q in range(0, 5) if by_p[q])
     stage_kernel_ms = float(kms[kdx] * kcnt[kdx]) / (n_prof * STAGES)
     achieved = alg / (stage_kernel_ms / 1e3) / 1e9
     peaks = {}
@@ -550,14 +557,16 @@ def run_gpu(args):
     if rec and W.name == rec.get("workload", "airfoil"):
         traffic = rec[f"{dom}_bytes_per_elem"] * E
     groups = [q for q in range(0, 5) if by_p[q]]
-    kname = (f"k_{dom}<{W.dim},{W.p + 1},float>" if len(groups) == 1 else
-             f"k_{dom}<{W.dim},N,float> over the degree groups N = {[q + 1 for q in groups]}, "
+    kbase = "k_stage" if dom_model == "stage" else f"k_{dom}"
+    kname = (f"{kbase}<{W.dim},{W.p + 1},float>" if len(groups) == 1 else
+             f"{kbase}<{W.dim},N,float> over the degree groups N = {[q + 1 for q in groups]}, "
              "one launch each per stage")
     # the whole stage at the method's minimum bytes per update: the bench's
     # updates/s times those bytes, against the measured copy bandwidth
     pts = {q: int(by_p[q]) * W.sizes(q)[0] for q in range(0, 5) if by_p[q]}
     b_upd = sum(method_bytes_per_update(q) * n for q, n in pts.items()) / max(sum(pts.values()), 1)
-    design_b = sum((algorithmic_bytes(int(by_p[q]), 4, "flux", q) + algorithmic_bytes(int(by_p[q]), 4, "grad", q))
+    design_b = sum((algorithmic_bytes(int(by_p[q]), 4, "stage", q) if fused else
+                    algorithmic_bytes(int(by_p[q]), 4, "flux", q) + algorithmic_bytes(int(by_p[q]), 4, "grad", q))
                    for q in range(0, 5) if by_p[q]) / max(sum(pts.values()), 1)
     achieved_stage = value / world * b_upd / 1e9
     roof = {"bound": "hbm", "kernel": "the whole RK stage (every kernel of the step)",
@@ -566,8 +575,8 @@ def run_gpu(args):
             "bytes_per_update": b_upd, "design_bytes_per_update": design_b,
             "how": "achieved = (sol-pt stage updates/s per GPU) x the method's minimum bytes per update "
                    "(4 V s + (1 + d^2) s_g + (2d/n)((2V + 2dV) s + d s_g), FP32); peak = measured copy "
-                   "bandwidth; design_bytes_per_update = what this kernel design moves (flux + gradient "
-                   "kernels)",
+                   "bandwidth; design_bytes_per_update = what the chosen schedule's kernels move "
+                   "(fused stage kernel, or flux + gradient kernels)",
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if peaks else "fallback 6800",
             "dominant_kernel": {"kernel": kname, "achieved": achieved, "unit": "GB/s", "frac": achieved / peak,
                                 "traffic": traffic, "algorithmic_bytes_per_launch": alg,
@@ -672,6 +681,107 @@ def run_gpu(args):
     return 0
 
 
+# --------------------------------------------------------------------------
+# long-horizon observer runs (--observe N): not a throughput measurement
+# --------------------------------------------------------------------------
+
+def _gauss_derivative(n):
+    """Gauss-Legendre points and the derivative matrix of the Lagrange basis
+    on them (post-processing of sampled states only)."""
+    x, w = np.polynomial.legendre.leggauss(n)
+    c = np.array([np.prod([x[i] - x[k] for k in range(n) if k != i]) for i in range(n)])
+    Dm = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            if i != j:
+                Dm[i, j] = c[i] / (c[j] * (x[i] - x[j]))
+        Dm[i, i] = -Dm[i].sum()
+    return x, w, Dm
+
+
+def tgv_diagnostics(u, n_el, p):
+    """Volume means of the kinetic energy rho |v|^2 / 2 and of the enstrophy
+    rho |omega|^2 / 2 of a Taylor-Green state on the uniform (2 pi)^3 box of
+    n_el^3 hexes (Gauss quadrature, tensor derivative of the velocity)."""
+    n = p + 1
+    _, w, Dm = _gauss_derivative(n)
+    h = 2 * np.pi / n_el
+    rho = u[..., 0]
+    vel = u[..., 1:4] / rho[..., None]
+    W = np.einsum("i,j,k->kji", w, w, w).reshape(-1)            # sp = i + n j + n^2 k
+    J = (h / 2) ** 3
+    vol = (2 * np.pi) ** 3
+    ek = float(np.einsum("es,s->", 0.5 * rho * np.sum(vel * vel, -1), W) * J / vol)
+    V = vel.reshape(vel.shape[0], n, n, n, 3)                      # [e][k][j][i][comp]
+    dxi = np.einsum("ai,ekjic->ekjac", Dm, V) * (2 / h)            # d/dx
+    deta = np.einsum("aj,ekjic->ekaic", Dm, V) * (2 / h)           # d/dy
+    dzeta = np.einsum("ak,ekjic->eajic", Dm, V) * (2 / h)          # d/dz
+    om = np.stack([deta[..., 2] - dzeta[..., 1], dzeta[..., 0] - dxi[..., 2], dxi[..., 1] - deta[..., 0]], -1)
+    om2 = np.sum(om * om, -1).reshape(vel.shape[0], -1)
+    ens = float(np.einsum("es,s->", 0.5 * rho * om2, W) * J / vol)
+    return ek, ens
+
+
+def run_observe(args):
+    """Long-horizon observer results of one workload, FP32 (mixed, batched)
+    and FP64 side by side: OASPL of every candidate over the second half of
+    N steps (both mean readings), mean C_L / C_D, and for the Taylor-Green
+    workload the kinetic-energy and enstrophy series."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2312_14167_gb300 import fr
+    meshes = make_meshes(0)
+    dt = cfl_dt(meshes)
+    ph = W.physics()
+    common = dict(gamma=GAMMA, prandtl=PR, mu=ph["mu"], rho_inf=1.0, v_inf=ph["v_inf"], p_inf=ph["p_inf"],
+                  inflow_delta=W.inflow_delta, inflow_ywall=0.0, dt=dt, viscous=True, rk=fr.FR_LSRK45,
+                  check_every=100)
+    fms = [fr.Mesh(m, W.p if W.degrees is None else W.elem_degrees(m)) for m in meshes]
+    n = args.observe
+    out = {"workload": workload_text(), "steps": n, "dt": dt, "window": "second half"}
+    a_ref = 1.0 if W.dim == 2 else float(np.pi)
+    for name, prec in (("fp32", fr.FR_FP32), ("fp64", fr.FR_FP64)):
+        sol = fr.Solver(fms, fr.make_config(W.dim, precision=prec, **common))
+        sol.tune(None, mode=1)
+        for i, m in enumerate(fms):
+            sol.set_state(i, initial_state(m.sol_coords(), i, meshes[i]))
+        pids = [[sol.probe_add(i, x) for x in probe_points(meshes[i])] for i in range(len(fms))]
+        series = []
+        t0 = time.perf_counter()
+        chunk = max(1, n // 20) if W.start == "tgv" else n // 2
+        done = 0
+        while done < n:
+            if W.start == "tgv":
+                ek, ens = tgv_diagnostics(sol.get_state(0), round(len(meshes[0].elem_vert) ** (1 / 3)), W.p)
+                series.append({"step": done, "t": done * dt, "E_k": ek, "enstrophy": ens})
+            k = min(chunk, n - done)
+            sol.rk_step(k)
+            done += k
+            if done == n // 2:
+                sol.probe_reset()
+        sol.synchronize()
+        res = {"seconds": time.perf_counter() - t0, "health": sol.instance_status()[1]}
+        if any(pids):
+            res["oaspl_db_mode0"] = [sol.oaspl(ids, p_ref=2e-5, p_scale=101325.0 / ph["p_inf"], mean_mode=0)
+                                     for ids in pids if ids]
+            res["oaspl_db_mode1"] = [sol.oaspl(ids, p_ref=2e-5, p_scale=101325.0 / ph["p_inf"], mean_mode=1)
+                                     for ids in pids if ids]
+        if "wall_points" in meshes[0].info and W.name != "cavity":
+            res["mean_cl_cd"] = [sol.force_coefficients(i, a_ref) for i in range(len(fms))]
+        if series:
+            ek, ens = tgv_diagnostics(sol.get_state(0), round(len(meshes[0].elem_vert) ** (1 / 3)), W.p)
+            series.append({"step": n, "t": n * dt, "E_k": ek, "enstrophy": ens})
+            res["series"] = series
+        out[name] = res
+        del sol
+        torch.cuda.empty_cache()
+    if "oaspl_db_mode0" in out["fp32"]:
+        out["oaspl_fp32_minus_fp64_db"] = [a - b for a, b in zip(out["fp32"]["oaspl_db_mode0"],
+                                                               out["fp64"]["oaspl_db_mode0"])]
+    print(json.dumps({"observe": out}), flush=True)
+    return 0
+
+
 def sol_bytes(E, p=None):
     s = 4
     NSP, NFP = W.sizes(W.p if p is None else p)
@@ -695,6 +805,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="airfoil", choices=sorted(WORKLOADS))
     ap.add_argument("--candidates", type=int, default=0)
+    ap.add_argument("--observe", type=int, default=0,
+                    help="long-horizon observer run of N steps (OASPL over the second half, FP32 vs FP64)")
     ap.add_argument("--schedule", default="",
                     help="fixed schedule, e.g. 'stage=split;regs=0;contract=simt' (no autotuning)")
     args = ap.parse_args()
@@ -705,6 +817,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.observe > 0:
+        return run_observe(args)
     return run_gpu(args)
 
 

@@ -707,6 +707,16 @@ __device__ __forceinline__ void make_local_ref(const RefState<real> &g, const re
     r.dp_inf = (g.p + g.dp_inf) - r.p;
 }
 
+// the global reference as a LocalRef (no shift)
+template <int D, typename real>
+__device__ __forceinline__ void global_ref(const RefState<real> &g, LocalRef<D, real> &L) {
+    L.r = g;
+#pragma unroll
+    for (int v = 0; v < D + 2; ++v) L.du[v] = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) L.bv[i] = 0;
+}
+
 // full state u_r + u'
 template <int V, typename real>
 __device__ __forceinline__ void add_ref(const RefState<real> &r, const real *up, real *u) {
@@ -1383,9 +1393,14 @@ k_flux(const KArgs<real> a) {
     load_state_rows<N, V, PAD>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
     __syncthreads();
+    // FP32: every element's flux reference in shared memory (its own, or the
+    // global one where local references are off or the group adds DIVREF)
     const bool local = PERT && a.local_ref && !a.DIVREF;
-    if (PERT && local) {
-        if (tid < ne) make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
+    if (PERT) {
+        if (tid < ne) {
+            if (local) make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
+            else global_ref<D>(a.ref, sLR[tid]);
+        }
         __syncthreads();
     }
 
@@ -1401,12 +1416,12 @@ k_flux(const KArgs<real> a) {
 #pragma unroll
         for (int v = 0; v < V; ++v) uRp[v] = uR[it][v];
         // FP32: states relative to the element's reference (local) or the global one
-        const RefState<real> &rf = local ? sLR[j].r : a.ref;
+        const RefState<real> &rf = sLR[j].r;
         real shift[V], bsh[D];
 #pragma unroll
-        for (int v = 0; v < V; ++v) shift[v] = local ? sLR[j].du[v] : real(0);
+        for (int v = 0; v < V; ++v) shift[v] = PERT ? sLR[j].du[v] : real(0);
 #pragma unroll
-        for (int d = 0; d < D; ++d) bsh[d] = local ? sLR[j].bv[d] : real(0);
+        for (int d = 0; d < D; ++d) bsh[d] = PERT ? sLR[j].bv[d] : real(0);
         real uLl[V], uRl[V];
 #pragma unroll
         for (int v = 0; v < V; ++v) { uLl[v] = uL[v] - shift[v]; uRl[v] = uRp[v] - shift[v]; }
@@ -1477,8 +1492,8 @@ k_flux(const KArgs<real> a) {
         if constexpr (PERT) {
             real ul[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) ul[v] = uu[v] - (local ? sLR[j].du[v] : real(0));
-            flux_inv_pert<D>(ul, local ? sLR[j].r : a.ref, a.gamma - real(1), F);
+            for (int v = 0; v < V; ++v) ul[v] = uu[v] - sLR[j].du[v];
+            flux_inv_pert<D>(ul, sLR[j].r, a.gamma - real(1), F);
         } else {
             flux_inv<D>(uu, a.gamma - real(1), F);
         }
@@ -1837,8 +1852,10 @@ k_stage(const KArgs<real> a) {
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
     __syncthreads();
     const bool local = PERT && a.local_ref && !a.DIVREF;
-    if (PERT && local && tid < ne)
-        make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
+    if (PERT && tid < ne) {
+        if (local) make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
+        else global_ref<D>(a.ref, sLR[tid]);
+    }
     tile_gradient<D, N, PAD>(sU, sM, D1, sG, ne);
     __syncthreads();
 
@@ -1869,10 +1886,10 @@ k_stage(const KArgs<real> a) {
             }
         }
         // FP32: inviscid terms relative to the element's reference (local) or the global one
-        const RefState<real> &rf = local ? sLR[j].r : a.ref;
+        const RefState<real> &rf = sLR[j].r;
         real shift[V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) shift[v] = local ? sLR[j].du[v] : real(0);
+        for (int v = 0; v < V; ++v) shift[v] = PERT ? sLR[j].du[v] : real(0);
         real ub[V], uRp[V], uLl[V], uRl[V];
         const bool inner = pt[it] >= 0;
         if (inner) {
@@ -1887,7 +1904,7 @@ k_stage(const KArgs<real> a) {
             const int b = -1 - pt[it];
             real vref[D];
 #pragma unroll
-            for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d] - (local ? sLR[j].bv[d] : real(0));
+            for (int d = 0; d < D; ++d) vref[d] = a.BVREF[(int64_t)b * D + d] - (PERT ? sLR[j].bv[d] : real(0));
             if constexpr (PERT) {
 #pragma unroll
                 for (int v = 0; v < V; ++v) uLl[v] = uL[v] - shift[v];
@@ -1967,8 +1984,8 @@ k_stage(const KArgs<real> a) {
         if constexpr (PERT) {
             real ul[V];
 #pragma unroll
-            for (int v = 0; v < V; ++v) ul[v] = uu[v] - (local ? sLR[j].du[v] : real(0));
-            flux_inv_pert<D>(ul, local ? sLR[j].r : a.ref, a.gamma - real(1), F);
+            for (int v = 0; v < V; ++v) ul[v] = uu[v] - sLR[j].du[v];
+            flux_inv_pert<D>(ul, sLR[j].r, a.gamma - real(1), F);
         } else {
             flux_inv<D>(uu, a.gamma - real(1), F);
         }

@@ -74,3 +74,35 @@ def test_reference_arm_prints_one_contract_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
+
+
+def test_bench_taylor_green_diagnostics_match_the_closed_forms():
+    """The observer run's kinetic-energy and enstrophy means of the exact
+    Taylor-Green field: 1/8 and 3/8 (rho = 1 + O(M^2) at M = 0.1), the
+    enstrophy converging with the mesh, and the bench's method bytes per
+    update reproducing the scope table's figures (188, 378, 326.4 B)."""
+    import numpy as np
+    import bench
+    from synth import meshes as M, states as S
+
+    def field(n, p):
+        m = M.tgv_mesh(n)
+        # solution points of the uniform box, in the bench's ordering (xi fastest)
+        x1, _, _ = bench._gauss_derivative(p + 1)
+        h = 2 * np.pi / n
+        lo = m.xyz[m.elem_vert].min(axis=1)
+        t = (x1 + 1) / 2 * h
+        pts = np.stack(np.meshgrid(t, t, t, indexing="ij"), -1)       # [i][j][k]
+        pts = pts.transpose(2, 1, 0, 3).reshape(-1, 3)                 # i fastest
+        return S.taylor_green(lo[:, None, :] + pts[None], mach=0.1)
+
+    ek4, en4 = bench.tgv_diagnostics(field(4, 3), 4, 3)
+    ek8, en8 = bench.tgv_diagnostics(field(8, 3), 8, 3)
+    assert abs(ek8 - 0.125) < 1e-4 and abs(en8 - 0.375) < abs(en4 - 0.375) < 0.05
+    saved = bench.W
+    try:
+        for (w, p), want in ((("airfoil", 3), 188.0), (("tgv", 3), 378.0), (("tandem", 4), 326.4)):
+            bench.W = bench.WORKLOADS[w]
+            assert abs(bench.method_bytes_per_update(p) - want) < 1e-9
+    finally:
+        bench.W = saved
