@@ -141,12 +141,10 @@ CANDIDATES = W.candidates     # --candidates: a smaller poll (profiling captures
 # DRAM traffic of one launch of the dominant kernel from an ncu capture,
 # per element, valid only for the kernel source it was taken on.
 NCU_TRAFFIC = {
-    # dram__bytes_read.sum + dram__bytes_write.sum per element of one stage launch, ncu
-    # --set full on the 8-airfoil case (243,854 quads; see profiles/k_flux_airfoil8_full.md),
-    # scaled to a launch by the element count
-    "27cb25267663f2302c003941030f01c1edb87b8d534c2a1fdbedf362bd20cbd4":
-        {"flux_bytes_per_elem": (315.181568e6 + 149.768192e6) / 243854,
-         "grad_bytes_per_elem": (249.938432e6 + 45.308928e6) / 243854},
+    # ncu --set full of k_flux<2,4,float,1,0> on the 8-airfoil case (243,854 quads), mean of two
+    # launches (profiles/k_flux_airfoil8_full.md), scaled to a launch by the element count
+    "919282f386fbf2fd13d1f28a2440189c1f6ba1e16fee9d848496ed3f20a34519":
+        {"flux_bytes_per_elem": ((340.126976e6 + 383.497472e6) / 2 + (154.825728e6 + 159.185408e6) / 2) / 243854},
 }
 
 
@@ -154,7 +152,11 @@ NCU_TRAFFIC = {
 # FP64 path (DFMA counted twice, DADD and DMUL once), from an ncu capture of
 # its stage kernels on the 8-candidate airfoil case, valid only for the
 # kernel source it was taken on
-NCU_FP64_FLOPS = {}
+NCU_FP64_FLOPS = {
+    # k_grad<2,4,double> 1.9361e8 + k_flux<2,4,double> 3.6875e8 flops per stage over candidate 0
+    # (33,800 quads x 16 points), split schedule; profiles/fp64_stage_airfoil8_flops.md
+    "919282f386fbf2fd13d1f28a2440189c1f6ba1e16fee9d848496ed3f20a34519": (1.9361e8 + 3.6875e8) / (33800 * 16),
+}
 
 
 def kernel_source_hash():
@@ -555,7 +557,8 @@ def run_gpu(args):
     traffic = None
     rec = NCU_TRAFFIC.get(kernel_source_hash())
     if rec and W.name == rec.get("workload", "airfoil"):
-        traffic = rec[f"{dom}_bytes_per_elem"] * E
+        per_elem = rec.get(f"{dom_model}_bytes_per_elem")
+        traffic = per_elem * E if per_elem else None
     groups = [q for q in range(0, 5) if by_p[q]]
     kbase = "k_stage" if dom_model == "stage" else f"k_{dom}"
     kname = (f"{kbase}<{W.dim},{W.p + 1},float>" if len(groups) == 1 else
@@ -613,10 +616,12 @@ def run_gpu(args):
 
     # the plain single-instance FP64 path, candidates one after another
     n64 = 10
+    fp64_sched = []
     t64 = 0.0
     for i, m in enumerate(fms):
         s64 = fr.Solver([m], cfg64)
-        s64.tune(tune_cache, mode=0)              # one measurement per size bucket
+        sched64 = s64.tune(tune_cache, mode=0)    # one measurement per size bucket
+        fp64_sched.append(sched64.split(";source")[0])
         s64.set_state(0, states[i])
         s64.rk_step(1)
         s64.synchronize()
@@ -669,7 +674,8 @@ def run_gpu(args):
                                          "ratio_mixed_batched_over_fp64": value / world / fp64_val,
                                          "how": f"FP64 path, one candidate per solver, {n64} steps each, "
                                                 "candidates one after another, device time summed",
-                                         "roofline": fp64_alu},
+                                         "roofline": fp64_alu,
+                                         "schedules": sorted(set(fp64_sched))},
                 "parity": parity,
                 "observers": {"oaspl_db_first4": oaspl,
                               "oaspl_window_samples": args.steps,
