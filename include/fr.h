@@ -320,7 +320,8 @@ fr_status fr_instance_status(fr_solver *solver, int32_t *flags, int *first_bad);
  * solver's stage schedule -- for BR2 batches without mortar faces, one
  * fused kernel per RK stage or a gradient kernel plus a flux kernel -- the
  * register level of its stage kernels (FP32: 0 = the default residency,
- * 1 = one resident CTA fewer per SM and more registers per thread) and, in
+ * 1 = one resident CTA fewer per SM and more registers per thread, 2 = one
+ * more CTA per SM and fewer registers) and, in
  * FP32, the contraction of the divergence + correction operators (SIMT
  * sum factorisation, or 3xTF32 tensor-core mma products of every element
  * line: FP32-level accuracy, FP32 accumulation) are measured on the

@@ -34,7 +34,14 @@ static cudaError_t prepare_n(bool visc) {
     if (e != cudaSuccess) return e;
     e = prep_smem(k_grad<2, N, float, L1>, smem_bytes<2, N, float>(K_GRAD, true));
     if (e != cudaSuccess) return e;
-    return prep_smem(k_stage<2, N, float, L1>, smem_bytes<2, N, float>(K_STAGE, true));
+    e = prep_smem(k_stage<2, N, float, L1>, smem_bytes<2, N, float>(K_STAGE, true));
+    if (e != cudaSuccess) return e;
+    constexpr int L2 = has_level1<N, float>() ? 2 : 0;
+    e = prep_smem(k_flux<2, N, float, true, L2>, smem_bytes<2, N, float>(K_FLUX, true));
+    if (e != cudaSuccess) return e;
+    e = prep_smem(k_grad<2, N, float, L2>, smem_bytes<2, N, float>(K_GRAD, true));
+    if (e != cudaSuccess) return e;
+    return prep_smem(k_stage<2, N, float, L2>, smem_bytes<2, N, float>(K_STAGE, true));
 }
 
 cudaError_t prepare_2_f32(int N, bool visc) {

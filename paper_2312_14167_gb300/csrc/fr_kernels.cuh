@@ -928,6 +928,21 @@ __device__ __forceinline__ void load_state_rows(real *dst, const real *src, cons
     }
 }
 
+// Every tile element's flux reference into sLR, one thread per element: the
+// element's own (from the stored state at its first solution point) when
+// local references are on, else the global reference.  (The element mean
+// instead of the first point measured no more accurate on the wall-bounded
+// cases and 9 % slower.)
+template <int D, int N, bool PAD, typename real>
+__device__ __forceinline__ void tile_local_refs(const RefState<real> &g, real gamma, const real *sU,
+                                                LocalRef<D, real> *sLR, int ne, bool local) {
+    using G = Geo<D, N>;
+    const int j = threadIdx.x;
+    if (j >= ne) return;
+    if (local) make_local_ref<D>(g, sU + G::template slot<PAD>(j * G::NSP) * (D + 2), gamma, sLR[j]);
+    else global_ref<D>(g, sLR[j]);
+}
+
 // value at flux point f of the degree-p interpolant along its line
 template <int D, int N, int V, bool PAD, typename real>
 __device__ __forceinline__ void interp_line(const real *sX, int j, int f, const real *Lm, const real *Lp,
@@ -1072,8 +1087,9 @@ __device__ __forceinline__ void tc_divergence(const float *sF, const float *sC, 
 #ifndef FR_MINB_GRAD_3D_F32
 #define FR_MINB_GRAD_3D_F32 0
 #endif
-// L: register level chosen by the autotuner (fr_tune); level 1 asks for one
-// resident CTA fewer per SM, i.e. more registers per thread
+// L: register level chosen by the autotuner (fr_tune): level 1 asks for one
+// resident CTA fewer per SM (more registers per thread), level 2 for one
+// more (fewer registers, more residency)
 template <int D, typename real, bool GRAD = false, int N = 4, int L = 0>
 struct MinBlocks {
     static constexpr int flux3 = FR_MINB_FLUX_3D_F32 > 0 ? FR_MINB_FLUX_3D_F32 : (N >= 5 ? 4 : 3);
@@ -1082,10 +1098,10 @@ struct MinBlocks {
         sizeof(real) == 8 ? 1
         : (D == 2 ? (GRAD ? FR_MINB_GRAD_2D_F32 : FR_MINB_FLUX_2D_F32)
                   : (GRAD ? grad3 : flux3));
-    static constexpr int value = base - L > 1 ? base - L : 1;
+    static constexpr int value = L == 2 ? base + 1 : (base - L > 1 ? base - L : 1);
 };
-// register levels compiled: FP32 kernels of degree >= 2 have two
-constexpr int kRegLevels = 2;
+// register levels compiled: FP32 kernels of degree >= 2 have three
+constexpr int kRegLevels = 3;
 template <int N, typename real>
 __host__ __device__ constexpr bool has_level1() { return sizeof(real) == 4 && N >= 3; }
 
@@ -1099,8 +1115,8 @@ __host__ __device__ constexpr bool has_level1() { return sizeof(real) == 4 && N 
 // state) are issued before the tile barrier so that their latency overlaps
 // the tile load.
 // --------------------------------------------------------------------------
-template <int D, int N, typename real, int L = 0>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true, N, L>::value))
+template <int D, int N, typename real, int RL = 0>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true, N, RL>::value))
 k_grad(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
@@ -1315,8 +1331,8 @@ k_grad(const KArgs<real> a) {
 // --------------------------------------------------------------------------
 // K_FLUX: fused common flux + transformed flux + divergence/correction + RK
 // --------------------------------------------------------------------------
-template <int D, int N, typename real, bool VISC, int L = 0>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, L>::value))
+template <int D, int N, typename real, bool VISC, int RL = 0>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, RL>::value))
 k_flux(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
@@ -1377,18 +1393,12 @@ k_flux(const KArgs<real> a) {
         }
     }
     // RK registers of this thread's solution points
+    // RK registers: loaded just before the update (phase 3), not here: keeping
+    // them live through phases 1-2 costs spills at the register cap (measured
+    // 3 % slower)
     real r1[ITS][V], r2[ITS][V];
     const bool need_r1 = mode == M_LSRK || mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
     const bool need_r2 = mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
-#pragma unroll
-    for (int it = 0; it < ITS; ++it) {
-        const int w = tid + it * G::THREADS;
-        if (w < ne * NSP) {
-            const int64_t g = ((e0 + w / NSP) * NSP + w % NSP) * V;
-            if (need_r1) ld_v<V>(a.R1 + g, r1[it]);
-            if (need_r2) ld_v<V>(a.R2 + g, r2[it]);
-        }
-    }
     load_ops(a, sOp, N);
     load_state_rows<N, V, PAD>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
@@ -1397,10 +1407,7 @@ k_flux(const KArgs<real> a) {
     // global one where local references are off or the group adds DIVREF)
     const bool local = PERT && a.local_ref && !a.DIVREF;
     if (PERT) {
-        if (tid < ne) {
-            if (local) make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
-            else global_ref<D>(a.ref, sLR[tid]);
-        }
+        tile_local_refs<D, N, PAD>(a.ref, a.gamma, sU, sLR, ne, local);
         __syncthreads();
     }
 
@@ -1618,6 +1625,8 @@ k_flux(const KArgs<real> a) {
         }
         real *su = sU + G::template slot<PAD>(j * NSP + s) * V;
         real u0[V], un[V], R[V];
+        if (need_r1) ld_v<V>(a.R1 + g, r1[it]);
+        if (need_r2) ld_v<V>(a.R2 + g, r2[it]);
         ld_v<V>(su, u0);
 #pragma unroll
         for (int v = 0; v < V; ++v) R[v] = -div[v] * iJ;
@@ -1787,8 +1796,8 @@ __device__ __forceinline__ void send_faces(const KArgs<real> &a, const real *sU,
     }
 }
 
-template <int D, int N, typename real, int L = 0>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, L>::value))
+template <int D, int N, typename real, int RL = 0>
+__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, RL>::value))
 k_stage(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
@@ -1835,27 +1844,18 @@ k_stage(const KArgs<real> a) {
             }
         }
     }
+    // RK registers: loaded just before the update (phase 3), not here: keeping
+    // them live through phases 1-2 costs spills at the register cap (measured
+    // 3 % slower)
     real r1[ITS][V], r2[ITS][V];
     const bool need_r1 = mode == M_LSRK || mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
     const bool need_r2 = mode == M_RK4_2 || mode == M_RK4_3 || mode == M_RK4_4;
-#pragma unroll
-    for (int it = 0; it < ITS; ++it) {
-        const int w = tid + it * G::THREADS;
-        if (w < ne * NSP) {
-            const int64_t g = ((e0 + w / NSP) * NSP + w % NSP) * V;
-            if (need_r1) ld_v<V>(a.R1 + g, r1[it]);
-            if (need_r2) ld_v<V>(a.R2 + g, r2[it]);
-        }
-    }
     load_ops(a, sOp, N);
     load_state_rows<N, V, PAD>(sU, a.U, (const int32_t *)nullptr, e0, ne, NSP);
     load_tile(sM, a.MET, (const int32_t *)nullptr, e0, ne, NSP * MS);
     __syncthreads();
     const bool local = PERT && a.local_ref && !a.DIVREF;
-    if (PERT && tid < ne) {
-        if (local) make_local_ref<D>(a.ref, sU + G::template slot<PAD>(tid * NSP) * V, a.gamma, sLR[tid]);
-        else global_ref<D>(a.ref, sLR[tid]);
-    }
+    if (PERT) tile_local_refs<D, N, PAD>(a.ref, a.gamma, sU, sLR, ne, local);
     tile_gradient<D, N, PAD>(sU, sM, D1, sG, ne);
     __syncthreads();
 
@@ -2087,6 +2087,8 @@ k_stage(const KArgs<real> a) {
         }
         real *su = sU + G::template slot<PAD>(j * NSP + s) * V;
         real u0[V], un[V], R[V];
+        if (need_r1) ld_v<V>(a.R1 + g, r1[it]);
+        if (need_r2) ld_v<V>(a.R2 + g, r2[it]);
         ld_v<V>(su, u0);
 #pragma unroll
         for (int v = 0; v < V; ++v) R[v] = -div[v] * iJ;
@@ -2605,16 +2607,18 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     using G = Geo<D, N>;
     const int64_t tiles = (a.n_elem + G::NE - 1) / G::NE;
     const bool l1 = has_level1<N, real>() && a.regs_level == 1;
+    const bool l2 = has_level1<N, real>() && a.regs_level == 2;
+    constexpr int R1 = has_level1<N, real>() ? 1 : 0, R2 = has_level1<N, real>() ? 2 : 0;
     if (kind == K_FLUX) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_FLUX, visc, a.tc != 0);
         if (visc) {
-            auto k = l1 ? k_flux<D, N, real, true, has_level1<N, real>() ? 1 : 0> : k_flux<D, N, real, true, 0>;
+            auto k = l2 ? k_flux<D, N, real, true, R2> : l1 ? k_flux<D, N, real, true, R1> : k_flux<D, N, real, true, 0>;
             cudaError_t err = prep_smem(k, sm);
             if (err != cudaSuccess) return err;
             k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
         } else {
-            auto k = l1 ? k_flux<D, N, real, false, has_level1<N, real>() ? 1 : 0> : k_flux<D, N, real, false, 0>;
+            auto k = l2 ? k_flux<D, N, real, false, R2> : l1 ? k_flux<D, N, real, false, R1> : k_flux<D, N, real, false, 0>;
             cudaError_t err = prep_smem(k, sm);
             if (err != cudaSuccess) return err;
             k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
@@ -2622,7 +2626,7 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     } else if (kind == K_GRAD) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_GRAD, true);
-        auto k = l1 ? k_grad<D, N, real, has_level1<N, real>() ? 1 : 0> : k_grad<D, N, real, 0>;
+        auto k = l2 ? k_grad<D, N, real, R2> : l1 ? k_grad<D, N, real, R1> : k_grad<D, N, real, 0>;
         cudaError_t err = prep_smem(k, sm);
         if (err != cudaSuccess) return err;
         k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
@@ -2636,7 +2640,7 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     } else if (kind == K_STAGE) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_STAGE, true, a.tc != 0);
-        auto k = l1 ? k_stage<D, N, real, has_level1<N, real>() ? 1 : 0> : k_stage<D, N, real, 0>;
+        auto k = l2 ? k_stage<D, N, real, R2> : l1 ? k_stage<D, N, real, R1> : k_stage<D, N, real, 0>;
         cudaError_t err = prep_smem(k, sm);
         if (err != cudaSuccess) return err;
         k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);

@@ -30,7 +30,7 @@ def test_tune_measures_caches_and_reuses(tmp_path):
     parts = dict(kv.split("=", 1) for kv in choice.split(";"))
     assert parts["source"] == "measured" and parts["stage"] in ("fused", "split")
     cands = {c.split("=")[0]: float(c.split("=")[1]) for c in parts["candidates"].split(",")}
-    assert set(cands) == {f"{st}/{r}/{c}" for st in ("split", "fused") for r in (0, 1) for c in ("simt", "tc")}
+    assert set(cands) == {f"{st}/{r}/{c}" for st in ("split", "fused") for r in (0, 1, 2) for c in ("simt", "tc")}
     best = min(cands, key=cands.get)
     assert best == f"{parts['stage']}/{parts['regs']}/{parts['contract']}"
     _, key = sol.schedule()
@@ -47,7 +47,7 @@ def test_tune_measures_caches_and_reuses(tmp_path):
 
 @pytest.mark.parametrize("contract", ["simt", "tc"])
 @pytest.mark.parametrize("stage", ["split", "fused"])
-@pytest.mark.parametrize("regs", [0, 1])
+@pytest.mark.parametrize("regs", [0, 1, 2])
 def test_every_schedule_matches_the_oracle(tmp_path, stage, regs, contract):
     case = FC.airfoil_case(n_inst=2)
     sol = FC.lib_solver(case, "fp32")
