@@ -187,6 +187,13 @@ struct Geo {
     // elements per CTA: about 256 threads of one solution point each
     static constexpr int NE = (256 / NSP) > 0 ? (256 / NSP) : 1;
     static constexpr int THREADS = ((NE * NSP + 31) / 32) * 32;
+    // The gradient and fused-stage kernels spend most of their work at flux
+    // points; on hexes with p >= 3 (more flux than solution points per
+    // element) they run one thread per flux point (measured: 256 threads
+    // left a second, mostly idle pass over the flux points; the tandem p = 4
+    // poll ran 9.6 % slower that way).
+    static constexpr bool WIDE = D == 3 && N >= 4;
+    static constexpr int GTHREADS = WIDE ? ((NE * NFP + 31) / 32) * 32 : THREADS;
 
     __device__ __forceinline__ static int stride(int k) { return k == 0 ? 1 : (k == 1 ? N : N * N); }
     // Shared-memory vector slot of point i (element-major) with one pad slot
@@ -1090,10 +1097,14 @@ __device__ __forceinline__ void tc_divergence(const float *sF, const float *sC, 
 // L: register level chosen by the autotuner (fr_tune): level 1 asks for one
 // resident CTA fewer per SM (more registers per thread), level 2 for one
 // more (fewer registers, more residency)
-template <int D, typename real, bool GRAD = false, int N = 4, int L = 0>
+template <int D, typename real, bool GRAD = false, int N = 4, int L = 0, bool WIDE = false>
 struct MinBlocks {
-    static constexpr int flux3 = FR_MINB_FLUX_3D_F32 > 0 ? FR_MINB_FLUX_3D_F32 : (N >= 5 ? 4 : 3);
-    static constexpr int grad3 = FR_MINB_GRAD_3D_F32 > 0 ? FR_MINB_GRAD_3D_F32 : (N >= 4 ? 5 : 4);
+    // WIDE (one thread per flux point, 384 or 320 threads): about the same
+    // threads per SM as the 256-thread residency
+    static constexpr int flux3 = FR_MINB_FLUX_3D_F32 > 0 ? FR_MINB_FLUX_3D_F32
+                               : WIDE ? (N >= 5 ? 3 : 2) : (N >= 5 ? 4 : 3);
+    static constexpr int grad3 = FR_MINB_GRAD_3D_F32 > 0 ? FR_MINB_GRAD_3D_F32
+                               : WIDE ? (N >= 5 ? 4 : 3) : (N >= 4 ? 5 : 4);
     static constexpr int base =
         sizeof(real) == 8 ? 1
         : (D == 2 ? (GRAD ? FR_MINB_GRAD_2D_F32 : FR_MINB_FLUX_2D_F32)
@@ -1116,12 +1127,13 @@ __host__ __device__ constexpr bool has_level1() { return sizeof(real) == 4 && N 
 // the tile load.
 // --------------------------------------------------------------------------
 template <int D, int N, typename real, int RL = 0>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, true, N, RL>::value))
+__global__ void __launch_bounds__(Geo<D, N>::GTHREADS, (MinBlocks<D, real, true, N, RL, Geo<D, N>::WIDE>::value))
 k_grad(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
     constexpr bool PERT = sizeof(real) == 4;   // FP32 state: perturbations about a.ref
-    constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
+    constexpr int TH = G::GTHREADS;
+    constexpr int IT = (NE * NFP + TH - 1) / TH;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
     real *sU = sOp + ops_slots(N);
@@ -1145,7 +1157,7 @@ k_grad(const KArgs<real> a) {
     real nr[IT][D], uR[IT][V];
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         pt[it] = -1;
         if (w < ne * NFP) {
             const int64_t e = elem_of<real>(a.elist, e0, w / NFP);
@@ -1163,7 +1175,7 @@ k_grad(const KArgs<real> a) {
     // face phase: jumps u_c - u_f and the state used in the viscous flux
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         real uL[V];
@@ -1243,7 +1255,7 @@ k_grad(const KArgs<real> a) {
     // face phase: Q and the viscous normal flux
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         const int64_t e = elem_of<real>(a.elist, e0, j);
@@ -1797,12 +1809,13 @@ __device__ __forceinline__ void send_faces(const KArgs<real> &a, const real *sU,
 }
 
 template <int D, int N, typename real, int RL = 0>
-__global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, RL>::value))
+__global__ void __launch_bounds__(Geo<D, N>::GTHREADS, (MinBlocks<D, real, false, N, RL, Geo<D, N>::WIDE>::value))
 k_stage(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int NSP = G::NSP, NFP = G::NFP, V = G::V, MS = G::MS, NE = G::NE;
-    constexpr int IT = (NE * NFP + G::THREADS - 1) / G::THREADS;
-    constexpr int ITS = (NE * NSP + G::THREADS - 1) / G::THREADS;
+    constexpr int TH = G::GTHREADS;
+    constexpr int IT = (NE * NFP + TH - 1) / TH;
+    constexpr int ITS = (NE * NSP + TH - 1) / TH;
     constexpr bool PERT = sizeof(real) == 4;   // FP32 state: perturbations about a.ref
     extern __shared__ __align__(16) unsigned char smem_raw[];
     real *sOp = reinterpret_cast<real *>(smem_raw);
@@ -1831,7 +1844,7 @@ k_stage(const KArgs<real> a) {
     real nr[IT][D], uR[IT][V], fvp[IT][V], lfp[IT][D];
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         pt[it] = INT32_MIN;
         if (w < ne * NFP) {
             const int64_t gf = (e0 + w / NFP) * NFP + w % NFP;
@@ -1862,7 +1875,7 @@ k_stage(const KArgs<real> a) {
     // 1) common normal flux (inviscid - BR2 viscous) at every own flux point
 #pragma unroll
     for (int it = 0; it < IT; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         if (w >= ne * NFP) continue;
         const int j = w / NFP, f = w % NFP;
         real uL[V], Q[D][V], lf[D];
@@ -1965,7 +1978,7 @@ k_stage(const KArgs<real> a) {
     real gu[ITS][D][V];
 #pragma unroll
     for (int it = 0; it < ITS; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         if (w >= ne * NSP) continue;
 #pragma unroll
         for (int jd = 0; jd < D; ++jd) ld_v<V>(sG + w * D * V + jd * V, gu[it][jd]);
@@ -1973,7 +1986,7 @@ k_stage(const KArgs<real> a) {
     __syncthreads();
 #pragma unroll
     for (int it = 0; it < ITS; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         if (w >= ne * NSP) continue;
         const int j = w / NSP, s = w % NSP;
         const real *M = sM + (j * NSP + s) * MS;
@@ -2041,7 +2054,7 @@ k_stage(const KArgs<real> a) {
     }
 #pragma unroll
     for (int it = 0; it < ITS; ++it) {
-        const int w = tid + it * G::THREADS;
+        const int w = tid + it * TH;
         if (w >= ne * NSP) continue;
         const int j = w / NSP, s = w % NSP;
         const int64_t e = e0 + j;
@@ -2629,7 +2642,7 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
         auto k = l2 ? k_grad<D, N, real, R2> : l1 ? k_grad<D, N, real, R1> : k_grad<D, N, real, 0>;
         cudaError_t err = prep_smem(k, sm);
         if (err != cudaSuccess) return err;
-        k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+        k<<<(unsigned)tiles, G::GTHREADS, sm, st>>>(a);
     } else if (kind == K_INTERP) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_INTERP, false);
@@ -2643,7 +2656,7 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
         auto k = l2 ? k_stage<D, N, real, R2> : l1 ? k_stage<D, N, real, R1> : k_stage<D, N, real, 0>;
         cudaError_t err = prep_smem(k, sm);
         if (err != cudaSuccess) return err;
-        k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+        k<<<(unsigned)tiles, G::GTHREADS, sm, st>>>(a);
     } else if (kind == K_INTERP_VISC) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_INTERP_VISC, true);
