@@ -143,8 +143,8 @@ CANDIDATES = W.candidates     # --candidates: a smaller poll (profiling captures
 NCU_TRAFFIC = {
     # ncu --set full of k_flux<2,4,float,1,0> on the 8-airfoil case (243,854 quads), mean of two
     # launches (profiles/k_flux_airfoil8_full.md), scaled to a launch by the element count
-    "919282f386fbf2fd13d1f28a2440189c1f6ba1e16fee9d848496ed3f20a34519":
-        {"flux_bytes_per_elem": ((340.126976e6 + 383.497472e6) / 2 + (154.825728e6 + 159.185408e6) / 2) / 243854},
+    "9ce1259f965df7a6229c93f4b0d7905bb8e40b0ec59992f643dadead8b30bb73":
+        {"flux_bytes_per_elem": ((316.185344e6 + 378.621184e6) / 2 + (151.570944e6 + 153.314560e6) / 2) / 243854},
 }
 
 
@@ -155,7 +155,7 @@ NCU_TRAFFIC = {
 NCU_FP64_FLOPS = {
     # k_grad<2,4,double> 1.9361e8 + k_flux<2,4,double> 3.6875e8 flops per stage over candidate 0
     # (33,800 quads x 16 points), split schedule; profiles/fp64_stage_airfoil8_flops.md
-    "919282f386fbf2fd13d1f28a2440189c1f6ba1e16fee9d848496ed3f20a34519": (1.9361e8 + 3.6875e8) / (33800 * 16),
+    "9ce1259f965df7a6229c93f4b0d7905bb8e40b0ec59992f643dadead8b30bb73": (1.9361e8 + 3.6875e8) / (33800 * 16),
 }
 
 
