@@ -102,3 +102,98 @@ def test_oaspl_multi_probe_averages_rms_then_converts():
     db = acoustics.oaspl([a, b], mode=1, p_ref=1.0)
     want = 20 * math.log10(2.0 / math.sqrt(2))
     assert abs(db - want) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# Adaptive steps (Bogacki-Shampine 3(2) pair, elementary controller)
+# ---------------------------------------------------------------------------
+
+def test_bs32_tableau_orders_exact():
+    """b meets every condition of order 3, bhat those of order 2 but not the
+    order-3 ones (so the difference estimates the error); the rows of a sum
+    to c; the last row of a is b with c = 1 (first same as last)."""
+    a, b, bh, c = timestep.BS32_A, timestep.BS32_B, timestep.BS32_BHAT, timestep.BS32_C
+    s = 4
+    for i in range(s):
+        assert sum(a[i]) == c[i]
+        assert all(a[i][j] == 0 for j in range(i, s))     # explicit
+    assert a[3] == b and c[3] == 1
+    ac = [sum(a[i][j] * c[j] for j in range(s)) for i in range(s)]
+    assert sum(b) == 1 and sum(b[i] * c[i] for i in range(s)) == Fraction(1, 2)
+    assert sum(b[i] * c[i] ** 2 for i in range(s)) == Fraction(1, 3)
+    assert sum(b[i] * ac[i] for i in range(s)) == Fraction(1, 6)
+    assert sum(bh) == 1 and sum(bh[i] * c[i] for i in range(s)) == Fraction(1, 2)
+    third = (sum(bh[i] * c[i] ** 2 for i in range(s)) - Fraction(1, 3),
+             sum(bh[i] * ac[i] for i in range(s)) - Fraction(1, 6))
+    assert third != (0, 0)
+
+
+def test_bs32_error_estimate_is_third_order_on_the_linear_equation():
+    """For y' = lambda y the estimate is h lambda (R(z) - Rhat(z)) y with
+    R - Rhat = O(z^3): halving h divides it by 8 in the limit, and the
+    third-order solution matches exp(z) to O(z^4)."""
+    lam = -1.3
+    ests, errs = [], []
+    for h in (0.08, 0.04, 0.02, 0.01):
+        u = np.array([1.0])
+        un, _, e = timestep.bs32_attempt(lambda y: lam * y, u, lam * u, h)
+        ests.append(abs(e[0]))
+        errs.append(abs(un[0] - math.exp(lam * h)))
+    r_est = [ests[i] / ests[i + 1] for i in range(3)]
+    r_err = [errs[i] / errs[i + 1] for i in range(3)]
+    assert abs(r_est[-1] - 8.0) < 0.2
+    assert abs(r_err[-1] - 16.0) < 0.5
+
+
+def _lotka(y):
+    return np.array([1.5 * y[0] - y[0] * y[1], -3.0 * y[1] + y[0] * y[1]])
+
+
+def test_adaptive_bs32_matches_scipy_rk23_on_an_ode():
+    """scipy's RK23 integrates with the same pair and the same elementary
+    controller: the accepted times and solution agree to rounding, through
+    a deliberately oversized first step (rejections) and the final step cut
+    to end on t_end."""
+    integrate = pytest.importorskip("scipy.integrate")
+    y0 = np.array([2.0, 1.0])
+    rtol, atol, h0, t_end = 1e-6, 1e-9, 0.5, 3.0
+    ad = timestep.AdaptiveBS32(_lotka, y0, h0, t_end, rtol, atol)
+    ad.run()
+    ref = integrate.solve_ivp(lambda t, y: _lotka(y), (0.0, t_end), y0, method="RK23",
+                              rtol=rtol, atol=atol, first_step=h0)
+    assert ref.status == 0
+    acc_t = [0.0] + [r["t"] + r["h"] for r in ad.records if r["accepted"]]
+    acc_t[-1] = ad.t
+    assert ad.n_rejected >= 1
+    assert len(acc_t) == ref.t.size
+    assert np.max(np.abs(np.array(acc_t) - ref.t)) < 1e-12 * t_end
+    assert np.max(np.abs(ad.u - ref.y[:, -1])) < 1e-10
+    assert ad.t == t_end
+
+
+def test_adaptive_bs32_matches_scipy_rk23_on_the_fr_semidiscretisation():
+    """The same agreement with the FR residual of a small isentropic vortex
+    (Euler, p = 2) as right-hand side, with one absolute tolerance per
+    conserved variable and a step cap."""
+    integrate = pytest.importorskip("scipy.integrate")
+    from tests import fr_cases as FC
+    case = FC.vortex_case(n=4, p=2)
+    disc = FC.oracle_disc(case)
+    u0 = FC.initial_state(case, disc.sol_coords())
+    shape = u0.shape
+    atol = np.array([1e-6, 1e-6, 1e-6, 1e-5])
+    rtol, h0, t_end, dt_max = 1e-5, 0.2, 0.3, 0.05
+    ad = timestep.AdaptiveBS32(disc.residual, u0, h0, t_end, rtol, atol, dt_max=dt_max)
+    ad.run()
+
+    def f(t, y):
+        return disc.residual(y.reshape(shape)).ravel()
+    ref = integrate.solve_ivp(f, (0.0, t_end), u0.ravel(), method="RK23", rtol=rtol,
+                              atol=np.broadcast_to(atol, shape).ravel(), first_step=h0,
+                              max_step=dt_max)
+    assert ref.status == 0
+    n_acc = sum(r["accepted"] for r in ad.records)
+    assert ad.n_rejected >= 1 and n_acc + 1 == ref.t.size
+    acc_t = np.cumsum([r["h"] for r in ad.records if r["accepted"]])
+    assert np.max(np.abs(acc_t - ref.t[1:])) < 1e-12
+    assert np.max(np.abs(ad.u.ravel() - ref.y[:, -1])) < 1e-11
