@@ -788,6 +788,83 @@ def run_observe(args):
     return 0
 
 
+def run_adaptive(args):
+    """Adaptive steps (FR_BS32) against fixed LSRK45 steps on one workload,
+    FP32 batched: simulated time advanced per second of device time (summed
+    over the candidates), the steps the controller takes against the fixed
+    CFL step, rejections, and the cost of one attempt against one LSRK45
+    step.  Each solver runs `--warmup` steps/attempts, then `--adaptive` timed
+    ones (CUDA events on the solver stream)."""
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2312_14167_gb300 import fr
+    meshes = make_meshes(0)
+    dt = cfl_dt(meshes)
+    ph = W.physics()
+    common = dict(gamma=GAMMA, prandtl=PR, mu=ph["mu"], rho_inf=1.0, v_inf=ph["v_inf"], p_inf=ph["p_inf"],
+                  inflow_delta=W.inflow_delta, inflow_ywall=0.0, dt=dt, viscous=True, precision=fr.FR_FP32,
+                  check_every=50)
+    fms = [fr.Mesh(m, W.p if W.degrees is None else W.elem_degrees(m)) for m in meshes]
+    n_inst = len(fms)
+    states = [initial_state(m.sol_coords(), i, meshes[i]) for i, m in enumerate(fms)]
+    out = {"workload": workload_text(), "cfl_dt": dt, "timed": args.adaptive, "warmup": args.warmup}
+
+    def timed(sol, n):
+        st = sol.stream
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        sol.rk_step(n)
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    runs = [("lsrk45", dict(rk=fr.FR_LSRK45), None)]
+    for rtol in args.adaptive_rtol:
+        # absolute tolerances at rtol times each variable's free-stream scale
+        at = [rtol * 1.0] + [rtol * 1.0] * W.dim + [rtol * ph["p_inf"] / (GAMMA - 1.0)]
+        runs.append((f"bs32_rtol{rtol:g}", dict(rk=fr.FR_BS32, rtol=rtol, atol=at), rtol))
+    for name, kw, rtol in runs:
+        sol = fr.Solver(fms, fr.make_config(W.dim, **{**common, **kw}))
+        sched = sol.tune(None, mode=1)
+        for i, u in enumerate(states):
+            sol.set_state(i, u)
+        sol.rk_step(args.warmup)
+        sol.synchronize()
+        if rtol is None:
+            t0 = [args.warmup * dt] * n_inst
+        else:
+            rec0 = [sol.step_control(i) for i in range(n_inst)]
+            t0 = [r["t"] for r in rec0]
+        ms = timed(sol, args.adaptive)
+        # first instance with a non-finite state (-1: none), scanned every 50 steps/attempts
+        res = {"ms": ms, "ms_per_step": ms / args.adaptive, "schedule": sched.split(";source")[0],
+               "first_nonfinite_instance": sol.instance_status()[1]}
+        if rtol is None:
+            adv = [args.adaptive * dt] * n_inst
+        else:
+            rec = [sol.step_control(i) for i in range(n_inst)]
+            adv = [r["t"] - a for r, a in zip(rec, t0)]
+            acc = [r["accepted"] - a["accepted"] for r, a in zip(rec, rec0)]
+            rej = [r["rejected"] - a["rejected"] for r, a in zip(rec, rec0)]
+            res.update({"accepted": int(sum(acc)), "rejected": int(sum(rej)),
+                        "mean_step_over_cfl_dt": float(np.sum(adv) / max(np.sum(acc), 1) / dt),
+                        "min_max_h_next_over_cfl_dt": [min(r["h_next"] for r in rec) / dt,
+                                                       max(r["h_next"] for r in rec) / dt]})
+        res["simulated_time_per_device_second"] = float(np.sum(adv) / (ms / 1e3))
+        kms, kcnt = sol.profile_steps(3)
+        res["kernel_ms_per_step"] = {k: float(kms[j] * kcnt[j] / 3)
+                                     for j, k in enumerate(["flux", "grad", "probe", "force", "other"])}
+        out[name] = res
+        del sol
+        torch.cuda.empty_cache()
+    base = out["lsrk45"]["simulated_time_per_device_second"]
+    for name, _, rtol in runs[1:]:
+        out[name]["speed_vs_lsrk45"] = out[name]["simulated_time_per_device_second"] / base
+    print(json.dumps({"adaptive": out}), flush=True)
+    return 0
+
+
 def sol_bytes(E, p=None):
     s = 4
     NSP, NFP = W.sizes(W.p if p is None else p)
@@ -813,6 +890,9 @@ def main():
     ap.add_argument("--candidates", type=int, default=0)
     ap.add_argument("--observe", type=int, default=0,
                     help="long-horizon observer run of N steps (OASPL over the second half, FP32 vs FP64)")
+    ap.add_argument("--adaptive", type=int, default=0,
+                    help="adaptive steps (FR_BS32) against LSRK45: N timed attempts / steps each")
+    ap.add_argument("--adaptive-rtol", type=float, nargs="+", default=[1e-6, 1e-4])
     ap.add_argument("--schedule", default="",
                     help="fixed schedule, e.g. 'stage=split;regs=0;contract=simt' (no autotuning)")
     args = ap.parse_args()
@@ -825,6 +905,8 @@ def main():
         return run_reference(args)
     if args.observe > 0:
         return run_observe(args)
+    if args.adaptive > 0:
+        return run_adaptive(args)
     return run_gpu(args)
 
 

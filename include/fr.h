@@ -59,6 +59,23 @@ typedef int fr_status;
 
 #define FR_RK4 0            /* classical 4-stage RK */
 #define FR_LSRK45 1         /* Carpenter-Kennedy 5-stage 4th-order 2N-storage */
+/* Adaptive steps.  The paper advances in time with a second-order scheme with
+ * adaptive steps (Sec. 2.3) whose coefficients it does not give; in its place
+ * this is the embedded 3(2) pair of Bogacki and Shampine (1989): third-order
+ * solution, second-order error estimate, the last stage derivative reused as
+ * the next step's first (three residual evaluations per attempt).  Every
+ * instance has its own time and step size.  Error norm of an attempt: the
+ * root mean square, over all of the instance's solution-point values, of
+ * e / (atol_v + rtol max(|u_n|, |u_n+1|)) (full conserved values, v the
+ * variable); accepted when below 1.  Next step: the elementary error-per-step
+ * controller (Hairer, Norsett and Wanner, Solving ODEs I, Sec. II.4),
+ * h_new = h min(10, max(0.2, 0.9 err^(-1/3))), the increase capped at 1 right
+ * after a rejection within the same step; every step is capped at dt_max
+ * and shortened to end exactly at t_end, after which the instance does
+ * nothing.  The decisions are taken on the device in FP64.  cfg.dt is the
+ * first proposed step; fr_rk_step(n) makes n attempts (accepted or not);
+ * observers and wall forces sample after accepted steps only. */
+#define FR_BS32 2
 
 #define FR_FLUX_RUSANOV 0   /* local Lax-Friedrichs: max |v.n| + c of both sides */
 #define FR_FLUX_ROE 1       /* Roe averages, Harten entropy fix on the acoustic waves */
@@ -99,9 +116,9 @@ typedef struct fr_config {
     double inflow_delta;   /* FR_TAG_INFLOW: v = v_inf tanh(3 (y - ywall)/delta); <= 0: uniform */
     double inflow_ywall;
     double br2_eta;        /* BR2 penalty; <= 0 selects the number of element faces */
-    double dt;             /* fixed time step of fr_rk_step */
+    double dt;             /* fixed time step of fr_rk_step (FR_BS32: the first proposed step) */
     int viscous;           /* 0: Euler, 1: Navier-Stokes (BR2) */
-    int rk;                /* FR_RK4 or FR_LSRK45 */
+    int rk;                /* FR_RK4, FR_LSRK45 or FR_BS32 */
     int precision;         /* FR_FP64 or FR_FP32 */
     int flux;              /* inviscid interface flux: FR_FLUX_RUSANOV or FR_FLUX_ROE */
     int viscous_scheme;    /* FR_VISC_BR2 or FR_VISC_LDG */
@@ -116,6 +133,12 @@ typedef struct fr_config {
                               stream); 1 = about the free stream everywhere (fewer
                               instructions, larger rounding in wall cells) */
     int reserved;
+    /* FR_BS32 only */
+    double t_end;          /* end time of every instance (<= 0: none) */
+    double dt_max;         /* largest step (<= 0: none) */
+    double rtol;           /* relative tolerance of the error norm (>= 0) */
+    double atol[5];        /* absolute tolerance per conserved variable (rho, rho v, rho E;
+                              >= 0, with atol_v + rtol > 0 for each variable used) */
 } fr_config;
 
 /* Build one mesh (host, FP64).  The FR discretisation is Huynh's Flux
@@ -207,8 +230,18 @@ fr_status fr_residual(fr_solver *solver, int inst, double *r);
 
 /* Advance every instance by n_steps fixed steps of cfg->dt with cfg->rk,
  * sampling every probe (and the wall force) after each completed step.  Work
- * is replayed from a CUDA graph captured on first use.  Asynchronous. */
+ * is replayed from a CUDA graph captured on first use.  Asynchronous.
+ * FR_BS32: n_steps attempts of every instance (see FR_BS32). */
 fr_status fr_rk_step(fr_solver *solver, int n_steps);
+
+/* FR_BS32: the step-control record of instance ``inst`` into out (8 doubles):
+ * time t of its current solution, proposed step, step of the next attempt,
+ * error norm of the last attempt, 1 if the step being made has had a
+ * rejected attempt, accepted attempts, rejected attempts, accepted steps
+ * since the last fr_probe_reset.  fr_set_state / fr_set_states restart the
+ * instance at t = 0 with the step cfg.dt.  Synchronises.  FR_ERR_INVALID_ARG
+ * for other schemes, a null output or an instance out of range. */
+fr_status fr_step_control(fr_solver *solver, int inst, double *out8);
 
 /* Add an observer at physical point x (dim values) of instance ``inst``; the
  * containing element and reference coordinates are found by Newton's method
@@ -224,8 +257,9 @@ fr_status fr_probe_pressure(fr_solver *solver, int probe_id, double *p_latest);
 fr_status fr_probe_history(fr_solver *solver, int probe_id, double *out, int max_n, int *n_out);
 /* Checkpoint of everything a step accumulates besides the flow state (which
  * fr_get_state / fr_set_state save): the number of steps in the current
- * averaging window, the wall-force sums of every instance, and every probe's
- * FP64 accumulators and sample ring.  fr_accumulators_size is the number of
+ * averaging window, the wall-force sums of every instance, every probe's
+ * FP64 accumulators and sample ring, and (FR_BS32) every instance's
+ * step-control record (restored after fr_set_state, it continues the run).  fr_accumulators_size is the number of
  * doubles (-1 for a null solver).  The checkpoint starts with a header: steps
  * in the window, number of probes, number of instances and a fingerprint of
  * the observers (instance and element of each, in order).
@@ -257,7 +291,8 @@ fr_status fr_probe_stats(fr_solver *solver, int probe_id, double *out4);
 
 /* Time-mean wall force of instance ``inst`` since the last reset (dim
  * values): sum over wall flux points of w (p n - tau . n) (the force behind
- * C_D, Sec. 3.1.2), averaged over the completed steps. */
+ * C_D, Sec. 3.1.2), averaged over the completed steps (FR_BS32: the
+ * instance's accepted steps). */
 fr_status fr_forces(fr_solver *solver, int inst, double *mean_force);
 /* Time-mean lift and drag coefficients of instance ``inst`` since the last
  * reset (Sec. 3.1.2; the objective of Sec. 5.2 penalises them):

@@ -92,6 +92,10 @@ struct Group {
     // fused viscous stage: second (ping-pong) buffer of the inbound gradient
     // flux parts (the first is FV) and the partner lifting coefficients
     char *FV2 = nullptr, *LFP = nullptr;
+    // adaptive steps: third RK register (u_n) and the group's first element
+    // in the batch's per-element error array
+    char *R3 = nullptr;
+    int64_t ebase = 0;
     int32_t *PART = nullptr, *EINST = nullptr, *WALL = nullptr;
     bool use_divref = false;   // FP32: the reference flux has a residual here
     int n_probe = 0;
@@ -166,6 +170,14 @@ struct fr_solver {
     int regs_level = 0;
     // FP32: line contractions on the tensor cores (3xTF32 mma.sync; fr_tune)
     bool tc = false;
+    // adaptive steps (FR_BS32): step-control records [n_inst][kAdStride],
+    // accepted flags, per-element error sums, instance ranges of those; the
+    // stage-1 evaluation of fresh instances is pending (bs_start)
+    bool adapt = false, bs_start = false;
+    double *ADAPT = nullptr, *ERRE = nullptr;
+    int32_t *ACC = nullptr;
+    frk::AdaptRange *ARANGE = nullptr;
+    std::vector<double> adapt_init;   // host: the initial record of every instance
     std::string schedule_source = "default";
     double schedule_ms = 0.0;
     std::vector<std::unique_ptr<fr_mesh>> host_meshes;   // for probe location
@@ -187,6 +199,23 @@ namespace {
         }                                                                          \
     } while (0)
 
+// propagate a failed fr_status
+#define FR_TRY(call)                      \
+    do {                                  \
+        const fr_status _st = (call);     \
+        if (_st != FR_OK) return _st;     \
+    } while (0)
+
+// adaptive steps: end time and step cap (<= 0 in the configuration: none)
+double eff_t_end(const fr_config &c) { return c.t_end > 0.0 ? c.t_end : INFINITY; }
+double eff_dt_max(const fr_config &c) { return c.dt_max > 0.0 ? c.dt_max : INFINITY; }
+// the first attempt's step from t = 0 (the rule of K_BS_CONTROL)
+double first_step(const fr_config &c) {
+    double h = std::min(c.dt, eff_dt_max(c));
+    if (0.0 + h > eff_t_end(c)) h = eff_t_end(c) - 0.0;
+    return std::max(h, 0.0);
+}
+
 fr_status check_batch(fr_mesh *const *meshes, int n_inst, const fr_config *cfg) {
     if (!meshes || n_inst <= 0 || !cfg) { set_error("invalid solver arguments"); return FR_ERR_INVALID_ARG; }
     for (int i = 0; i < n_inst; ++i) {
@@ -196,7 +225,16 @@ fr_status check_batch(fr_mesh *const *meshes, int n_inst, const fr_config *cfg) 
             return FR_ERR_UNSUPPORTED;
         }
     }
-    if (cfg->rk != FR_RK4 && cfg->rk != FR_LSRK45) { set_error("unknown rk scheme"); return FR_ERR_INVALID_ARG; }
+    if (cfg->rk != FR_RK4 && cfg->rk != FR_LSRK45 && cfg->rk != FR_BS32) { set_error("unknown rk scheme"); return FR_ERR_INVALID_ARG; }
+    if (cfg->rk == FR_BS32) {
+        const int V = meshes[0]->dim + 2;
+        bool ok = cfg->dt > 0.0 && cfg->rtol >= 0.0;
+        for (int v = 0; v < V; ++v) ok = ok && cfg->atol[v] >= 0.0 && cfg->atol[v] + cfg->rtol > 0.0;
+        if (!ok) {
+            set_error("adaptive steps need dt > 0, rtol >= 0 and atol_v >= 0 with atol_v + rtol > 0");
+            return FR_ERR_INVALID_ARG;
+        }
+    }
     if (cfg->check_every < 0) { set_error("check_every must be >= 0"); return FR_ERR_INVALID_ARG; }
     if (cfg->flux_reference != 0 && cfg->flux_reference != 1) { set_error("unknown flux reference"); return FR_ERR_INVALID_ARG; }
     if (cfg->precision != FR_FP64 && cfg->precision != FR_FP32) { set_error("unknown precision"); return FR_ERR_INVALID_ARG; }
@@ -254,14 +292,15 @@ Plan make_plan(fr_mesh *const *meshes, int n_inst) {
 }
 
 struct GroupLayout {
-    size_t U, R1, R2, RES, UF0, UF1, FV, MET, NRM, MFLUX, PART, EINST, WALL, DIVREF, FV2, LFP;
+    size_t U, R1, R2, RES, UF0, UF1, FV, MET, NRM, MFLUX, PART, EINST, WALL, DIVREF, FV2, LFP, R3;
 };
 struct Layout {
     GroupLayout g[frk::kMaxGroups];
-    size_t BTAG, BVREF, STAGE, PROBES, PACC, PHIST, FORCE, PART_SUMS, RED, MORT, MATS, FLAGS, total;
+    size_t BTAG, BVREF, STAGE, PROBES, PACC, PHIST, FORCE, PART_SUMS, RED, MORT, MATS, FLAGS;
+    size_t ERRE, ADAPT, ACC, ARANGE, total;
 };
 
-Layout make_layout(const Plan &P, int n_inst, bool fp64, bool visc) {
+Layout make_layout(const Plan &P, int n_inst, bool fp64, bool visc, bool adapt) {
     const size_t rs = fp64 ? 8 : 4;
     const int dim = P.dim, V = dim + 2, MS = dim * dim + 1;
     Layout L{};
@@ -289,6 +328,7 @@ Layout make_layout(const Plan &P, int n_inst, bool fp64, bool visc) {
         G.DIVREF = take(fp64 ? 16 : st);
         G.FV2 = take(visc ? fc : 16);
         G.LFP = take(visc ? (size_t)E * nfp * dim * rs : 16);
+        G.R3 = take(adapt ? st : 16);
     }
     L.BTAG = take((size_t)P.nb * 4);
     L.BVREF = take((size_t)P.nb * dim * rs);
@@ -302,6 +342,12 @@ Layout make_layout(const Plan &P, int n_inst, bool fp64, bool visc) {
     L.MORT = take((size_t)P.n_mortar * sizeof(frk::MortarFace));
     L.MATS = take((size_t)P.mat_reals * rs);
     L.FLAGS = take((size_t)n_inst * 4);
+    int64_t e_all = 0;
+    for (int g = 0; g < P.G; ++g) e_all += P.E[g];
+    L.ERRE = take(adapt ? (size_t)e_all * 8 : 16);
+    L.ADAPT = take((size_t)n_inst * frk::kAdStride * 8);
+    L.ACC = take((size_t)n_inst * 4);
+    L.ARANGE = take((size_t)n_inst * sizeof(frk::AdaptRange));
     L.total = o;
     return L;
 }
@@ -356,6 +402,17 @@ void fill_args(const fr_solver *s, int g, frk::KArgs<real> &a) {
     a.local_ref = s->local_ref ? 1 : 0;
     a.regs_level = s->regs_level;
     a.tc = (s->tc && !s->fp64) ? 1 : 0;
+    if (s->adapt) {
+        a.ADAPT = s->ADAPT;
+        a.ACC = s->ACC;
+        a.R3 = (real *)G.R3;
+        a.ERRE = s->ERRE + G.ebase;
+        a.ARANGE = s->ARANGE;
+        a.bs_rtol = (real)s->cfg.rtol;
+        for (int v = 0; v < s->V; ++v) a.bs_atol[v] = (real)s->cfg.atol[v];
+        a.t_end = eff_t_end(s->cfg);
+        a.dt_max = eff_dt_max(s->cfg);
+    }
     const RefElem &r = G.ref;
     for (int i = 0; i < G.N; ++i) {
         for (int mm = 0; mm < G.N; ++mm) a.opD1[i * frk::kMaxN + mm] = r.D1[i][mm];
@@ -492,57 +549,54 @@ int grid_for(int64_t items) {
 // inbound gradient-flux-part buffer of face parity par (fused stage)
 char *fvbuf(const Group &G, int par) { return par == 0 ? G.FV : G.FV2; }
 
-// One RK step starting from face-buffer parity p0; returns the launches issued.
-fr_status enqueue_step(fr_solver *s, int p0, int64_t *n_launch) {
-    int par = p0;
-    int64_t cnt = 0;
-    const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
-    const double dt = s->cfg.dt;
+// One stage evaluation reading face-buffer parity par (and writing par ^ 1):
+// [gradient kernels,] mortar common fluxes, stage kernels with RK mode
+// `mode`, mortar traces of the new state (not for M_BS_START and M_BS_4,
+// which leave the state and the face buffers as they are).
+fr_status enqueue_eval(fr_solver *s, int par, int mode, double rk_a, double rk_b, double rk_c, int64_t &cnt) {
     const int G = (int)s->grp.size();
-    for (int st = 0; st < stages; ++st) {
-        if (s->visc && !s->fused) {
-            for (int g = 0; g < G; ++g) {
-                Launch l;
-                l.kind = frk::K_GRAD;
-                l.g = g;
-                l.n_elem = s->grp[g].E;
-                l.UFin = s->grp[g].UF[par];
-                FR_CK(launch(s, l));
-                ++cnt;
-            }
-        }
-        if (s->n_mortar > 0) {
-            FR_CK(mortar(s, 1, par, 0, s->n_mortar));
-            ++cnt;
-        }
+    if (s->visc && !s->fused) {
         for (int g = 0; g < G; ++g) {
-            Launch f;
-            f.kind = s->fused ? frk::K_STAGE : frk::K_FLUX;
-            f.g = g;
-            f.n_elem = s->grp[g].E;
-            f.UFin = s->grp[g].UF[par];
-            f.UFout = s->grp[g].UF[par ^ 1];
-            f.FVin = fvbuf(s->grp[g], par);
-            f.FVout = fvbuf(s->grp[g], par ^ 1);
-            if (s->cfg.rk == FR_LSRK45) {
-                f.mode = st == 0 ? frk::M_LSRK_FIRST : frk::M_LSRK;
-                f.rk_a = kLsA[st];
-                f.rk_b = kLsB[st];
-            } else {
-                const int modes[4] = {frk::M_RK4_1, frk::M_RK4_2, frk::M_RK4_3, frk::M_RK4_4};
-                const double cs[4] = {0.5 * dt, 0.5 * dt, dt, dt / 6.0};
-                f.mode = modes[st];
-                f.rk_c = cs[st];
-            }
-            FR_CK(launch(s, f));
+            Launch l;
+            l.kind = frk::K_GRAD;
+            l.g = g;
+            l.n_elem = s->grp[g].E;
+            l.UFin = s->grp[g].UF[par];
+            FR_CK(launch(s, l));
             ++cnt;
         }
-        if (s->n_mortar > 0) {
-            FR_CK(mortar(s, 0, par ^ 1, 0, s->n_mortar));
-            ++cnt;
-        }
-        par ^= 1;
     }
+    if (s->n_mortar > 0) {
+        FR_CK(mortar(s, 1, par, 0, s->n_mortar));
+        ++cnt;
+    }
+    for (int g = 0; g < G; ++g) {
+        Launch f;
+        f.kind = s->fused ? frk::K_STAGE : frk::K_FLUX;
+        f.g = g;
+        f.n_elem = s->grp[g].E;
+        f.UFin = s->grp[g].UF[par];
+        f.UFout = s->grp[g].UF[par ^ 1];
+        f.FVin = fvbuf(s->grp[g], par);
+        f.FVout = fvbuf(s->grp[g], par ^ 1);
+        f.mode = mode;
+        f.rk_a = rk_a;
+        f.rk_b = rk_b;
+        f.rk_c = rk_c;
+        FR_CK(launch(s, f));
+        ++cnt;
+    }
+    if (s->n_mortar > 0 && mode != frk::M_BS_START && mode != frk::M_BS_4) {
+        FR_CK(mortar(s, 0, par ^ 1, 0, s->n_mortar));
+        ++cnt;
+    }
+    return FR_OK;
+}
+
+// Observers and wall forces after a step (face-buffer parity par holds the
+// faces of the step's final state).
+fr_status enqueue_samples(fr_solver *s, int par, int64_t &cnt) {
+    const int G = (int)s->grp.size();
     for (int g = 0; g < G; ++g) {
         if (s->grp[g].n_probe <= 0) continue;
         Launch pr;
@@ -563,6 +617,120 @@ fr_status enqueue_step(fr_solver *s, int p0, int64_t *n_launch) {
         FR_CK(launch(s, fo));
         ++cnt;
     }
+    return FR_OK;
+}
+
+// Face-buffer parity flips of one step (one per stage evaluation).
+int step_flips(const fr_solver *s) {
+    return s->cfg.rk == FR_RK4 ? 4 : s->cfg.rk == FR_LSRK45 ? 5 : 3;
+}
+
+// Face states (and, fused BR2, gradient flux parts) of the current state U
+// of every instance into face-buffer parity par, mortar traces included.
+fr_status enqueue_faces(fr_solver *s, int par, int64_t &cnt) {
+    for (size_t g = 0; g < s->grp.size(); ++g) {
+        const Group &G = s->grp[g];
+        Launch in;
+        in.kind = s->fused ? frk::K_INTERP_VISC : frk::K_INTERP;
+        in.g = (int)g;
+        in.n_elem = G.E;
+        in.UFout = G.UF[par];
+        in.FVout = fvbuf(G, par);
+        FR_CK(launch(s, in));
+        ++cnt;
+    }
+    if (s->n_mortar > 0) {
+        FR_CK(mortar(s, 0, par, 0, s->n_mortar));
+        ++cnt;
+    }
+    return FR_OK;
+}
+
+// One adaptive attempt (FR_BS32) from face-buffer parity p0: accept or roll
+// back the previous attempt and form the first stage state (K_BS_COMMIT), its
+// faces, the three stage evaluations (the last one computes k4 and the
+// per-element errors and writes no faces), the controller, then the samples
+// of accepted steps (on the faces of u_n+1, which the last evaluation read).
+fr_status enqueue_attempt(fr_solver *s, int p0, int64_t *n_launch) {
+    int par = p0;
+    int64_t cnt = 0;
+    for (size_t g = 0; g < s->grp.size(); ++g) {
+        const Group &G = s->grp[g];
+        Launch c;
+        c.kind = frk::K_BS_COMMIT;
+        c.g = (int)g;
+        c.n_elem = G.E;
+        c.grid = grid_for(G.E * G.nsp * s->V);
+        FR_CK(launch(s, c));
+        ++cnt;
+    }
+    FR_TRY(enqueue_faces(s, par, cnt));
+    const int modes[3] = {frk::M_BS_2, frk::M_BS_3, frk::M_BS_4};
+    for (int st = 0; st < 3; ++st) {
+        FR_TRY(enqueue_eval(s, par, modes[st], 0.0, 0.0, 0.0, cnt));
+        par ^= 1;
+    }
+    Launch ct;
+    ct.kind = frk::K_BS_CONTROL;
+    ct.g = 0;
+    ct.grid = s->n_inst;
+    FR_CK(launch(s, ct));
+    ++cnt;
+    FR_TRY(enqueue_samples(s, par ^ 1, cnt));
+    *n_launch = cnt;
+    return FR_OK;
+}
+
+// Adaptive steps, after the last attempt of a call: U back to u_n where the
+// last attempt was rejected, and the face data of every instance's current
+// solution into face-buffer parity s->parity (the last stage evaluation of an
+// attempt writes none), so that residuals, integrals and downloads between
+// calls see the solution.
+fr_status bs_settle(fr_solver *s, int64_t &cnt) {
+    for (size_t g = 0; g < s->grp.size(); ++g) {
+        const Group &G = s->grp[g];
+        Launch c;
+        c.kind = frk::K_BS_COMMIT;
+        c.mode = 1;
+        c.g = (int)g;
+        c.n_elem = G.E;
+        c.grid = grid_for(G.E * G.nsp * s->V);
+        FR_CK(launch(s, c));
+        ++cnt;
+    }
+    return enqueue_faces(s, s->parity, cnt);
+}
+
+// Adaptive steps: the first stage derivative k1 = R(u_n) of instances whose
+// state was just set (accepted flag kAccFresh), before their first attempt;
+// the others are left as they are.  Flips the face-buffer parity.
+fr_status bs_start_if_needed(fr_solver *s) {
+    if (!s->adapt || !s->bs_start) return FR_OK;
+    int64_t cnt = 0;
+    FR_TRY(enqueue_eval(s, s->parity, frk::M_BS_START, 0.0, 0.0, 0.0, cnt));
+    s->parity ^= 1;
+    s->bs_start = false;
+    return FR_OK;
+}
+
+// One RK step starting from face-buffer parity p0; returns the launches issued.
+fr_status enqueue_step(fr_solver *s, int p0, int64_t *n_launch) {
+    if (s->adapt) return enqueue_attempt(s, p0, n_launch);
+    int par = p0;
+    int64_t cnt = 0;
+    const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
+    const double dt = s->cfg.dt;
+    for (int st = 0; st < stages; ++st) {
+        if (s->cfg.rk == FR_LSRK45) {
+            FR_TRY(enqueue_eval(s, par, st == 0 ? frk::M_LSRK_FIRST : frk::M_LSRK, kLsA[st], kLsB[st], 0.0, cnt));
+        } else {
+            const int modes[4] = {frk::M_RK4_1, frk::M_RK4_2, frk::M_RK4_3, frk::M_RK4_4};
+            const double cs[4] = {0.5 * dt, 0.5 * dt, dt, dt / 6.0};
+            FR_TRY(enqueue_eval(s, par, modes[st], 0.0, 0.0, cs[st], cnt));
+        }
+        par ^= 1;
+    }
+    FR_TRY(enqueue_samples(s, par, cnt));
     *n_launch = cnt;
     return FR_OK;
 }
@@ -803,7 +971,7 @@ extern "C" size_t fr_workspace_bytes(fr_mesh *const *meshes, int n_inst, const f
     if (check_batch(meshes, n_inst, cfg) != FR_OK) return 0;
     const Plan P = make_plan(meshes, n_inst);
     if (P.G > frk::kMaxGroups) return 0;
-    return make_layout(P, n_inst, cfg->precision == FR_FP64, cfg->viscous != 0).total;
+    return make_layout(P, n_inst, cfg->precision == FR_FP64, cfg->viscous != 0, cfg->rk == FR_BS32).total;
 }
 
 namespace {
@@ -835,6 +1003,7 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
     s->cfg = *cfg;
     s->fp64 = cfg->precision == FR_FP64;
     s->visc = cfg->viscous != 0;
+    s->adapt = cfg->rk == FR_BS32;
     s->V = dim + 2;
     s->MS = dim * dim + 1;
     s->rsz = s->fp64 ? 8 : 4;
@@ -860,7 +1029,7 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
             return FR_ERR_UNSUPPORTED;
         }
     }
-    const Layout L = make_layout(P, n_inst, s->fp64, s->visc);
+    const Layout L = make_layout(P, n_inst, s->fp64, s->visc, s->adapt);
     if (ws_bytes < L.total) {
         set_error("workspace too small: need " + std::to_string(L.total) + " bytes");
         return FR_ERR_WORKSPACE;
@@ -877,6 +1046,7 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
         G.DIVREF = w + gl.DIVREF;
         G.FV2 = w + gl.FV2;
         G.LFP = w + gl.LFP;
+        G.R3 = w + gl.R3;
     }
     s->BTAG = (int32_t *)(w + L.BTAG); s->BVREF = w + L.BVREF;
     s->stage64 = (double *)(w + L.STAGE);
@@ -889,6 +1059,10 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
     s->MORT = (frk::MortarFace *)(w + L.MORT);
     s->FLAGS = (int32_t *)(w + L.FLAGS);
     s->MATS = w + L.MATS;
+    s->ERRE = (double *)(w + L.ERRE);
+    s->ADAPT = (double *)(w + L.ADAPT);
+    s->ACC = (int32_t *)(w + L.ACC);
+    s->ARANGE = (frk::AdaptRange *)(w + L.ARANGE);
 
     // element ranges of every instance in every group
     for (int g = 0; g < P.G; ++g) {
@@ -1135,6 +1309,35 @@ extern "C" fr_status fr_solver_create(fr_solver **out, fr_mesh *const *meshes, i
     FR_CK(cudaMemsetAsync(s->pacc, 0, sizeof(frk::ProbeAcc) * kMaxProbes, cs));
     FR_CK(cudaMemsetAsync(s->force_acc, 0, (size_t)n_inst * 3 * 8, cs));
     FR_CK(cudaMemsetAsync(s->FLAGS, 0, (size_t)n_inst * 4, cs));
+    if (s->adapt) {
+        // per-element error sums: the groups one after another; every
+        // instance's element ranges in them and its number of values
+        int64_t base = 0;
+        for (int g = 0; g < P.G; ++g) {
+            s->grp[g].ebase = base;
+            base += s->grp[g].E;
+        }
+        std::vector<frk::AdaptRange> ar(n_inst);
+        for (int i = 0; i < n_inst; ++i) {
+            std::memset(&ar[i], 0, sizeof(ar[i]));
+            for (int g = 0; g < P.G; ++g) {
+                ar[i].start[g] = s->grp[g].ebase + s->grp[g].off[i];
+                ar[i].count[g] = s->grp[g].ne[i];
+            }
+            ar[i].nval = (double)s->inst_nsp[i] * s->V;
+        }
+        FR_CK(up(s->ARANGE, ar.data(), ar.size() * sizeof(frk::AdaptRange)));
+        s->adapt_init.assign((size_t)n_inst * frk::kAdStride, 0.0);
+        for (int i = 0; i < n_inst; ++i) {
+            double *rec = &s->adapt_init[(size_t)i * frk::kAdStride];
+            rec[frk::kAdH] = cfg->dt;
+            rec[frk::kAdHuse] = first_step(*cfg);
+        }
+        FR_CK(up(s->ADAPT, s->adapt_init.data(), s->adapt_init.size() * 8));
+        const std::vector<int32_t> fresh(n_inst, frk::kAccFresh);
+        FR_CK(up(s->ACC, fresh.data(), fresh.size() * 4));
+        s->bs_start = true;
+    }
     FR_CK(cudaStreamSynchronize(cs));
     for (int g = 0; g < P.G; ++g) {
         const int N = s->grp[g].N;
@@ -1157,6 +1360,20 @@ extern "C" void fr_solver_destroy(fr_solver *s) {
 
 namespace {
 
+// Adaptive steps: instance inst (-1: every instance) restarts at t = 0 with
+// the first step of the configuration, its k1 still to be computed.
+const int32_t kFreshFlag = frk::kAccFresh;
+fr_status reset_step_control(fr_solver *s, int inst) {
+    const int i0 = inst < 0 ? 0 : inst, i1 = inst < 0 ? s->n_inst : inst + 1;
+    for (int i = i0; i < i1; ++i) {
+        FR_CK(cudaMemcpyAsync(s->ADAPT + (size_t)i * frk::kAdStride, &s->adapt_init[(size_t)i * frk::kAdStride],
+                              frk::kAdStride * 8, cudaMemcpyHostToDevice, s->stream));
+        FR_CK(cudaMemcpyAsync(s->ACC + i, &kFreshFlag, 4, cudaMemcpyHostToDevice, s->stream));
+    }
+    s->bs_start = true;
+    return FR_OK;
+}
+
 // Enqueue the upload of one instance's FP64 host state (the ABI's element
 // order) and the derivation of its face values; no synchronisation.  An
 // instance spread over several degree groups is reordered on the host into
@@ -1164,6 +1381,7 @@ namespace {
 fr_status enqueue_upload(fr_solver *s, int inst, const double *u, std::vector<double> &tmp) {
     const int V = s->V;
     FR_CK(cudaMemsetAsync(s->FLAGS + inst, 0, 4, s->stream));
+    if (s->adapt) FR_TRY(reset_step_control(s, inst));
     const size_t n = (size_t)s->inst_nsp[inst] * V;
     if (!spread(s, inst)) {
         FR_CK(cudaMemcpyAsync(s->stage64, u, n * 8, cudaMemcpyHostToDevice, s->stream));
@@ -1323,8 +1541,9 @@ extern "C" fr_status fr_residual(fr_solver *s, int inst, double *r) {
 extern "C" fr_status fr_rk_step(fr_solver *s, int n_steps) {
     fr::Range nvtx_range("fr_rk_step");
     if (!s || n_steps < 0) { set_error("invalid fr_rk_step arguments"); return FR_ERR_INVALID_ARG; }
-    const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
+    const int flips = step_flips(s);
     int64_t total = 0;
+    if (n_steps > 0) FR_TRY(bs_start_if_needed(s));
     for (int it = 0; it < n_steps; ++it) {
         const int p0 = s->parity;
         if (s->stream) {
@@ -1349,7 +1568,7 @@ extern "C" fr_status fr_rk_step(fr_solver *s, int n_steps) {
             if (st != FR_OK) return st;
             total += cnt;
         }
-        s->parity = (stages % 2) ? p0 ^ 1 : p0;
+        s->parity = (flips % 2) ? p0 ^ 1 : p0;
         ++s->steps_since_reset;
         if (s->cfg.check_every > 0 && ++s->steps_since_check >= s->cfg.check_every) {
             s->steps_since_check = 0;
@@ -1364,6 +1583,7 @@ extern "C" fr_status fr_rk_step(fr_solver *s, int n_steps) {
             }
         }
     }
+    if (s->adapt && n_steps > 0) FR_TRY(bs_settle(s, total));
     s->last_launches = total;
     return FR_OK;
 }
@@ -1386,22 +1606,38 @@ extern "C" fr_status fr_instance_status(fr_solver *s, int32_t *flags, int *first
     return FR_OK;
 }
 
+extern "C" fr_status fr_step_control(fr_solver *s, int inst, double *out8) {
+    fr_status st = check_inst(s, inst);
+    if (st != FR_OK) return st;
+    if (!s->adapt || !out8) {
+        set_error(out8 ? "fr_step_control: the solver does not use adaptive steps" : "null output");
+        return FR_ERR_INVALID_ARG;
+    }
+    FR_CK(cudaMemcpyAsync(out8, s->ADAPT + (size_t)inst * frk::kAdStride, frk::kAdStride * 8,
+                          cudaMemcpyDeviceToHost, s->stream));
+    FR_CK(cudaStreamSynchronize(s->stream));
+    return FR_OK;
+}
+
 extern "C" int64_t fr_last_launch_count(const fr_solver *s) { return s ? s->last_launches : -1; }
 
 extern "C" fr_status fr_profile_steps(fr_solver *s, int n_steps, double *ms, int64_t *count) {
     fr::Range nvtx_range("fr_profile_steps");
     if (!s || n_steps <= 0 || !ms || !count) { set_error("invalid fr_profile_steps arguments"); return FR_ERR_INVALID_ARG; }
-    const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
+    const int flips = step_flips(s);
+    FR_TRY(bs_start_if_needed(s));
     s->prof.clear();
     s->profiling = true;
     fr_status st = FR_OK;
     for (int it = 0; it < n_steps && st == FR_OK; ++it) {
         int64_t cnt = 0;
         st = enqueue_step(s, s->parity, &cnt);
-        s->parity = (stages % 2) ? s->parity ^ 1 : s->parity;
+        s->parity = (flips % 2) ? s->parity ^ 1 : s->parity;
         ++s->steps_since_reset;
     }
     s->profiling = false;
+    int64_t settle_launches = 0;
+    if (st == FR_OK && s->adapt) st = bs_settle(s, settle_launches);
     cudaError_t se = cudaStreamSynchronize(s->stream);
     for (int k = 0; k < 5; ++k) { ms[k] = 0.0; count[k] = 0; }
     for (auto &pe : s->prof) {
@@ -1524,7 +1760,7 @@ static double probe_fingerprint(const fr_solver *s) {
 extern "C" int64_t fr_accumulators_size(const fr_solver *s) {
     if (!s) return -1;
     return kAccHeader + (int64_t)s->n_inst * 3 + (int64_t)s->n_probe * (int64_t)(sizeof(frk::ProbeAcc) / 8) +
-           (int64_t)s->n_probe * frk::kHistLen;
+           (int64_t)s->n_probe * frk::kHistLen + (s->adapt ? (int64_t)s->n_inst * frk::kAdStride : 0);
 }
 
 extern "C" fr_status fr_get_accumulators(fr_solver *s, double *out) {
@@ -1542,6 +1778,9 @@ extern "C" fr_status fr_get_accumulators(fr_solver *s, double *out) {
         FR_CK(cudaMemcpyAsync(ph, s->phist, (size_t)s->n_probe * frk::kHistLen * 8, cudaMemcpyDeviceToHost,
                               s->stream));
     }
+    if (s->adapt)
+        FR_CK(cudaMemcpyAsync(ph + (size_t)s->n_probe * frk::kHistLen, s->ADAPT,
+                              (size_t)s->n_inst * frk::kAdStride * 8, cudaMemcpyDeviceToHost, s->stream));
     FR_CK(cudaStreamSynchronize(s->stream));
     return FR_OK;
 }
@@ -1572,6 +1811,9 @@ extern "C" fr_status fr_set_accumulators(fr_solver *s, const double *in, int64_t
         FR_CK(cudaMemcpyAsync(s->phist, ph, (size_t)s->n_probe * frk::kHistLen * 8, cudaMemcpyHostToDevice,
                               s->stream));
     }
+    if (s->adapt)
+        FR_CK(cudaMemcpyAsync(s->ADAPT, ph + (size_t)s->n_probe * frk::kHistLen,
+                              (size_t)s->n_inst * frk::kAdStride * 8, cudaMemcpyHostToDevice, s->stream));
     FR_CK(cudaStreamSynchronize(s->stream));
     s->steps_since_reset = (int64_t)in[0];
     return FR_OK;
@@ -1581,6 +1823,8 @@ extern "C" fr_status fr_probe_reset(fr_solver *s) {
     if (!s) { set_error("null solver"); return FR_ERR_INVALID_ARG; }
     FR_CK(cudaMemsetAsync(s->pacc, 0, sizeof(frk::ProbeAcc) * kMaxProbes, s->stream));
     FR_CK(cudaMemsetAsync(s->force_acc, 0, (size_t)s->n_inst * 3 * 8, s->stream));
+    if (s->adapt)   // the accepted-step counters of the averaging window
+        FR_CK(cudaMemset2DAsync(s->ADAPT + frk::kAdSamples, frk::kAdStride * 8, 0, 8, s->n_inst, s->stream));
     s->steps_since_reset = 0;
     return FR_OK;
 }
@@ -1609,13 +1853,16 @@ extern "C" fr_status fr_forces(fr_solver *s, int inst, double *mean_force) {
     fr_status st = check_inst(s, inst);
     if (st != FR_OK) return st;
     if (!mean_force) { set_error("null output"); return FR_ERR_INVALID_ARG; }
-    double h[3];
+    double h[3], samples = (double)s->steps_since_reset;
     FR_CK(cudaMemcpyAsync(h, s->force_acc + (size_t)inst * 3, 24, cudaMemcpyDeviceToHost, s->stream));
+    if (s->adapt)   // adaptive steps: the instance's accepted steps in the window
+        FR_CK(cudaMemcpyAsync(&samples, s->ADAPT + (size_t)inst * frk::kAdStride + frk::kAdSamples, 8,
+                              cudaMemcpyDeviceToHost, s->stream));
     FR_CK(cudaStreamSynchronize(s->stream));
-    const double n = (double)std::max<int64_t>(s->steps_since_reset, 1);
+    const double n = std::max(samples, 1.0);
     for (int d = 0; d < s->dim; ++d) {
         mean_force[d] = h[d] / n;
-        if (!s->fp64 && s->steps_since_reset > 0) mean_force[d] += s->pref64 * s->wall_nsum[(size_t)inst * 3 + d];
+        if (!s->fp64 && samples > 0) mean_force[d] += s->pref64 * s->wall_nsum[(size_t)inst * 3 + d];
     }
     return FR_OK;
 }
@@ -1868,7 +2115,8 @@ bool apply_schedule(fr_solver *s, const std::string &v, const char *source) {
     const bool fusable = s->visc && s->cfg.viscous_scheme == FR_VISC_BR2 && s->n_mortar == 0;
     if ((fused && !fusable) || regs < 0 || regs >= frk::kRegLevels || (tc && s->fp64)) return false;
     s->fused = fused;
-    s->regs_level = s->fp64 ? 0 : regs;
+    // FP64 and adaptive steps run the stage kernels at register level 0 only
+    s->regs_level = (s->fp64 || s->adapt) ? 0 : regs;
     s->tc = tc;
     const size_t m = v.find("ms=");
     s->schedule_ms = m == std::string::npos ? 0.0 : std::atof(v.c_str() + m + 3);
@@ -1917,9 +2165,9 @@ extern "C" fr_status fr_tune(fr_solver *s, const char *cache_path, int mode, cha
     const bool fusable = s->visc && s->cfg.viscous_scheme == FR_VISC_BR2 && s->n_mortar == 0;
     for (int c = 0; c < (s->fp64 ? 1 : 2); ++c)
         for (int f = 0; f < (fusable ? 2 : 1); ++f)
-            for (int r = 0; r < (s->fp64 ? 1 : frk::kRegLevels); ++r) cands.push_back({f == 1, r, c == 1, 0.0});
+            for (int r = 0; r < ((s->fp64 || s->adapt) ? 1 : frk::kRegLevels); ++r) cands.push_back({f == 1, r, c == 1, 0.0});
     const int warm = 2, timed = 3;
-    const int stages = s->cfg.rk == FR_RK4 ? 4 : 5;
+    const int flips = step_flips(s);
     // every instance starts from the free stream of the configuration
     {
         const int V = s->V;
@@ -1962,11 +2210,12 @@ extern "C" fr_status fr_tune(fr_solver *s, const char *cache_path, int mode, cha
             }
             if (st == FR_OK && mortar(s, 0, s->parity, s->moff[i], s->mcnt[i]) != cudaSuccess) st = FR_ERR_CUDA;
         }
+        if (st == FR_OK) st = bs_start_if_needed(s);
         for (int it = 0; it < warm + timed && st == FR_OK; ++it) {
             if (it == warm && cudaEventRecord(e0, s->stream) != cudaSuccess) st = FR_ERR_CUDA;
             int64_t cnt = 0;
             if (st == FR_OK) st = enqueue_step(s, s->parity, &cnt);
-            s->parity = (stages % 2) ? s->parity ^ 1 : s->parity;
+            s->parity = (flips % 2) ? s->parity ^ 1 : s->parity;
         }
         if (st == FR_OK && cudaEventRecord(e1, s->stream) != cudaSuccess) st = FR_ERR_CUDA;
         if (st == FR_OK && cudaEventSynchronize(e1) != cudaSuccess) st = FR_ERR_CUDA;
@@ -1982,6 +2231,7 @@ extern "C" fr_status fr_tune(fr_solver *s, const char *cache_path, int mode, cha
     cudaMemsetAsync(s->force_acc, 0, (size_t)s->n_inst * 3 * 8, s->stream);
     cudaMemsetAsync(s->FLAGS, 0, (size_t)s->n_inst * 4, s->stream);
     s->steps_since_reset = 0;
+    if (st == FR_OK && s->adapt) st = reset_step_control(s, -1);
     if (st != FR_OK) {
         set_error("fr_tune: a candidate schedule failed to run");
         return st;

@@ -20,11 +20,17 @@ static cudaError_t prepare_n(bool visc) {
     if (visc) e = prep_smem(k_flux<2, N, double, true>, smem_bytes<2, N, double>(K_FLUX, true));
     else e = prep_smem(k_flux<2, N, double, false>, smem_bytes<2, N, double>(K_FLUX, false));
     if (e != cudaSuccess) return e;
+    // adaptive steps (their own instantiations, register level 0)
+    if (visc) e = prep_smem(k_flux<2, N, double, true, 0, true>, smem_bytes<2, N, double>(K_FLUX, true));
+    else e = prep_smem(k_flux<2, N, double, false, 0, true>, smem_bytes<2, N, double>(K_FLUX, false));
+    if (e != cudaSuccess) return e;
     e = prep_smem(k_grad<2, N, double>, smem_bytes<2, N, double>(K_GRAD, true));
     if (e != cudaSuccess) return e;
     e = prep_smem(k_interp<2, N, double>, smem_bytes<2, N, double>(K_INTERP, false));
     if (e != cudaSuccess || !visc) return e;
     e = prep_smem(k_stage<2, N, double>, smem_bytes<2, N, double>(K_STAGE, true));
+    if (e != cudaSuccess) return e;
+    e = prep_smem(k_stage<2, N, double, 0, true>, smem_bytes<2, N, double>(K_STAGE, true));
     if (e != cudaSuccess) return e;
     return prep_smem(k_interp_visc<2, N, double>, smem_bytes<2, N, double>(K_INTERP_VISC, true));
 }

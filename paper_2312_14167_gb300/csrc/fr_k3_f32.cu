@@ -20,11 +20,17 @@ static cudaError_t prepare_n(bool visc) {
     if (visc) e = prep_smem(k_flux<3, N, float, true>, smem_bytes<3, N, float>(K_FLUX, true));
     else e = prep_smem(k_flux<3, N, float, false>, smem_bytes<3, N, float>(K_FLUX, false));
     if (e != cudaSuccess) return e;
+    // adaptive steps (their own instantiations, register level 0)
+    if (visc) e = prep_smem(k_flux<3, N, float, true, 0, true>, smem_bytes<3, N, float>(K_FLUX, true));
+    else e = prep_smem(k_flux<3, N, float, false, 0, true>, smem_bytes<3, N, float>(K_FLUX, false));
+    if (e != cudaSuccess) return e;
     e = prep_smem(k_grad<3, N, float>, smem_bytes<3, N, float>(K_GRAD, true));
     if (e != cudaSuccess) return e;
     e = prep_smem(k_interp<3, N, float>, smem_bytes<3, N, float>(K_INTERP, false));
     if (e != cudaSuccess || !visc) return e;
     e = prep_smem(k_stage<3, N, float>, smem_bytes<3, N, float>(K_STAGE, true));
+    if (e != cudaSuccess) return e;
+    e = prep_smem(k_stage<3, N, float, 0, true>, smem_bytes<3, N, float>(K_STAGE, true));
     if (e != cudaSuccess) return e;
     e = prep_smem(k_interp_visc<3, N, float>, smem_bytes<3, N, float>(K_INTERP_VISC, true));
     if (e != cudaSuccess || !has_level1<N, float>()) return e;

@@ -3,7 +3,8 @@
 // Method (arXiv:2312.14167): compressible Navier-Stokes (Sec. 2.1, Eqs. 1-7)
 // discretised with Huynh's Flux Reconstruction (Sec. 2.3), DG-recovery
 // correction on tensor Gauss-Legendre points, Rusanov inviscid interface flux,
-// BR2 viscous interface flux; explicit RK4 / LSRK45 in time.
+// BR2 viscous interface flux; explicit RK4 / LSRK45 in time, or adaptive
+// steps with an embedded 3(2) pair (Bogacki-Shampine).
 //
 // Design (one GPU, HBM-bound):
 //  * element-blocked layout: every per-element array is [elem][point][var],
@@ -45,6 +46,8 @@ enum Kind : int {
     K_FINITE = 8,    // per-instance non-finite flags of the state
     K_STAGE = 9,     // fused BR2 stage (K_GRAD + K_FLUX in one kernel)
     K_INTERP_VISC = 10,  // face states + gradient flux parts (fused stage prologue)
+    K_BS_COMMIT = 11,    // adaptive steps: accept / roll back, first stage state
+    K_BS_CONTROL = 12,   // adaptive steps: error norm and step-size control per instance
 };
 
 enum Mode : int {
@@ -56,6 +59,37 @@ enum Mode : int {
     M_RK4_4 = 5,       // u = R1 + c (R2 + R)
     M_RESIDUAL = 6,    // RES = R
     M_RESIDUAL_J = 7,  // RES = J R (= -divergence)
+    // adaptive steps, Bogacki-Shampine 3(2) pair with h the instance's step:
+    // registers R1 = k1 = R(u_n), R2 = k2, then the error combination, then
+    // k4 = R(u_{n+1}), R3 = u_n
+    M_BS_START = 8,    // fresh instances: R1 = R, R3 = u
+    M_BS_2 = 9,        // R2 = R; u = R3 + (3/4) h R
+    M_BS_3 = 10,       // u = R3 + h (2/9 R1 + 1/3 R2 + 4/9 R); R2 = -5/72 R1 + 1/12 R2 + 1/9 R
+    M_BS_4 = 11,       // error of h (R2 - R/8) per element; R2 = R (state unchanged)
+};
+
+// Step-control record of one instance (adaptive steps), FP64
+enum AdaptField : int {
+    kAdT = 0,        // time of the current solution u_n
+    kAdH = 1,        // proposed step size
+    kAdHuse = 2,     // step size of the next (or running) attempt
+    kAdErr = 3,      // error norm of the last attempt
+    kAdRej = 4,      // 1 when the step being made has had a rejected attempt
+    kAdNacc = 5,     // accepted attempts
+    kAdNrej = 6,     // rejected attempts
+    kAdSamples = 7,  // accepted steps since the observer / force accumulators were reset
+    kAdStride = 8,
+};
+// accepted flag of the last attempt: 1 accepted, 0 rejected or no step,
+// -1 fresh state (its k1 = R(u) is still to be computed)
+constexpr int kAccFresh = -1;
+constexpr int kMaxGroupsAd = 5;   // degree groups (degrees 0..4)
+
+// the elements of one instance in the per-element error array, per degree
+// group, and the number of values (points x variables) of its error norm
+struct AdaptRange {
+    int64_t start[kMaxGroupsAd], count[kMaxGroupsAd];
+    double nval, pad;
 };
 
 enum BcTag : int { BC_WALL = 2, BC_FARFIELD = 3, BC_INFLOW = 4, BC_OUTFLOW = 5 };
@@ -158,6 +192,17 @@ struct KArgs {
     int local_ref;             // FP32: evaluate fluxes about element-local references
     int regs_level;            // register level of the stage kernels (host-side launch choice)
     int tc;                    // FP32: line contractions on the tensor cores (3xTF32 mma.sync)
+    // adaptive steps (modes M_BS_*, K_BS_*): step-control records [n_inst][kAdStride],
+    // accepted flags [n_inst] (null outside adaptive runs: observers and wall
+    // forces then sample every step), third RK register, per-element error
+    // sums of the whole batch (this group's part at ERRE), instance ranges
+    double *ADAPT;
+    int32_t *ACC;
+    real *R3;
+    double *ERRE;
+    const AdaptRange *ARANGE;
+    real bs_rtol, bs_atol[5];
+    double t_end, dt_max;
 };
 
 // --------------------------------------------------------------------------
@@ -1315,7 +1360,7 @@ k_grad(const KArgs<real> a) {
         if (wall) fvn[V - 1] = 0;
         if (!a.force) {
             st_v<V>(a.FV + (e * NFP + f) * V, fvn);
-        } else if (wall) {
+        } else if (wall && (!a.ACC || a.ACC[a.EINST[e]] == 1)) {   // adaptive: accepted steps only
             // face quadrature weight: product of the free directions' weights
             const int l = f % G::NFPF;
             const double wf = (D == 2) ? a.opW[l] : a.opW[l % N] * a.opW[l / N];
@@ -1341,9 +1386,99 @@ k_grad(const KArgs<real> a) {
 }
 
 // --------------------------------------------------------------------------
+// Adaptive steps: the Bogacki-Shampine 3(2) pair (third-order solution,
+// second-order embedded one, first stage of a step = last stage of the
+// previous one).  With h the instance's step size and k_i the stage
+// derivatives,
+//   stage inputs  u_n + h/2 k1,  u_n + 3h/4 k2,  u_{n+1} = u_n + h (2/9 k1 + 1/3 k2 + 4/9 k3),
+//   k4 = R(u_{n+1}),  error e = h (-5/72 k1 + 1/12 k2 + 1/9 k3 - 1/8 k4),
+// and the error norm is the root mean square of e / (atol + rtol max(|u_n|, |u_{n+1}|))
+// over the instance's values.  The stage kernels apply the register updates
+// (bs_update) and, in the last evaluation, the per-element sums of the
+// squared scaled error (bs_error_sums); K_BS_CONTROL decides.
+// --------------------------------------------------------------------------
+template <int V, typename real>
+__device__ __forceinline__ real bs_update(const KArgs<real> &a, int mode, int64_t e, int64_t g, const real *u0,
+                                          const real *R, real *un) {
+    constexpr bool PERT = sizeof(real) == 4;
+    const int inst = a.EINST[e];
+    const double h = a.ADAPT[(int64_t)inst * kAdStride + kAdHuse];
+    real es = 0;
+    if (mode == M_BS_START) {
+        if (a.ACC[inst] == kAccFresh) {
+            st_v<V>(a.R1 + g, R);
+            st_v<V>(a.R3 + g, u0);
+        }
+#pragma unroll
+        for (int v = 0; v < V; ++v) un[v] = u0[v];
+    } else if (mode == M_BS_2) {
+        real q[V];
+        ld_v<V>(a.R3 + g, q);
+        const real c = (real)(0.75 * h);
+#pragma unroll
+        for (int v = 0; v < V; ++v) un[v] = q[v] + c * R[v];
+        st_v<V>(a.R2 + g, R);
+    } else if (mode == M_BS_3) {
+        // one register array in flight at a time; u_n is added last
+        real t[V], cm[V];
+        const real c1 = (real)(h * (2.0 / 9.0)), c2 = (real)(h * (1.0 / 3.0)), c3 = (real)(h * (4.0 / 9.0));
+        ld_v<V>(a.R1 + g, t);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            un[v] = c1 * t[v] + c3 * R[v];
+            cm[v] = real(-5.0 / 72.0) * t[v] + real(1.0 / 9.0) * R[v];
+        }
+        ld_v<V>(a.R2 + g, t);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            un[v] += c2 * t[v];
+            cm[v] += real(1.0 / 12.0) * t[v];
+        }
+        st_v<V>(a.R2 + g, cm);
+        ld_v<V>(a.R3 + g, t);
+#pragma unroll
+        for (int v = 0; v < V; ++v) un[v] += t[v];
+    } else {  // M_BS_4
+        real cm[V], q[V];
+        ld_v<V>(a.R2 + g, cm);
+        ld_v<V>(a.R3 + g, q);
+        st_v<V>(a.R2 + g, R);
+        const real hr = (real)h;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            real uq = q[v], uf = u0[v];
+            if constexpr (PERT) {   // full conserved values
+                const real rv = v == 0 ? a.ref.rho : (v == V - 1 ? a.ref.E : a.ref.m[v - 1]);
+                uq += rv;
+                uf += rv;
+            }
+            const real ev = hr * (cm[v] - real(0.125) * R[v]);
+            const real r = ev / (a.bs_atol[v] + a.bs_rtol * fmax(fabs(uq), fabs(uf)));
+            es += r * r;
+        }
+    }
+    return es;
+}
+
+// per-element sums (fixed order, FP64) of the points' squared scaled errors,
+// which the last evaluation left in the first value of each point's shared
+// state slot, into ERRE (after the barrier that ends the evaluation)
+template <int D, int N, bool PAD, typename real>
+__device__ __forceinline__ void bs_error_sums(const KArgs<real> &a, const real *sU, int64_t e0, int ne, int tid,
+                                              int threads) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, V = G::V;
+    for (int j = tid; j < ne; j += threads) {
+        double sum = 0.0;
+        for (int q = 0; q < NSP; ++q) sum += (double)sU[G::template slot<PAD>(j * NSP + q) * V];
+        a.ERRE[e0 + j] = sum;
+    }
+}
+
+// --------------------------------------------------------------------------
 // K_FLUX: fused common flux + transformed flux + divergence/correction + RK
 // --------------------------------------------------------------------------
-template <int D, int N, typename real, bool VISC, int RL = 0>
+template <int D, int N, typename real, bool VISC, int RL = 0, bool AD = false>
 __global__ void __launch_bounds__(Geo<D, N>::THREADS, (MinBlocks<D, real, false, N, RL>::value))
 k_flux(const KArgs<real> a) {
     using G = Geo<D, N>;
@@ -1674,15 +1809,28 @@ k_flux(const KArgs<real> a) {
                 un[v] = r1[it][v] + a.rk_c * R[v];
             }
             st_v<V>(a.R2 + g, acc);
+        } else if (AD && mode >= M_BS_START) {
+            // adaptive steps; the last evaluation leaves the state as it is and
+            // puts the point's squared scaled error in its own state slot
+            const real es = bs_update<V>(a, mode, e, g, u0, R, un);
+            if (mode == M_BS_4) {
+                su[0] = es;
+                continue;
+            }
         } else {  // M_RK4_4
 #pragma unroll
             for (int v = 0; v < V; ++v) un[v] = r1[it][v] + a.rk_c * (r2[it][v] + R[v]);
         }
-        st_v<V>(a.U + g, un);
+        if (!AD || mode != M_BS_START) st_v<V>(a.U + g, un);
         st_v<V>(su, un);
     }
     if (mode == M_RESIDUAL || mode == M_RESIDUAL_J) return;
     __syncthreads();
+    if (AD && (mode == M_BS_START || mode == M_BS_4)) {
+        // the next attempt derives its face data from its first stage state
+        if (mode == M_BS_4) bs_error_sums<D, N, PAD>(a, sU, e0, ne, tid, G::THREADS);
+        return;
+    }
 
     // 4) face values of the new state, stored in the partner's inbound slot
     // for the next stage (boundary points have no partner)
@@ -1808,7 +1956,7 @@ __device__ __forceinline__ void send_faces(const KArgs<real> &a, const real *sU,
     }
 }
 
-template <int D, int N, typename real, int RL = 0>
+template <int D, int N, typename real, int RL = 0, bool AD = false>
 __global__ void __launch_bounds__(Geo<D, N>::GTHREADS, (MinBlocks<D, real, false, N, RL, Geo<D, N>::WIDE>::value))
 k_stage(const KArgs<real> a) {
     using G = Geo<D, N>;
@@ -2137,15 +2285,28 @@ k_stage(const KArgs<real> a) {
                 un[v] = r1[it][v] + a.rk_c * R[v];
             }
             st_v<V>(a.R2 + g, acc);
+        } else if (AD && mode >= M_BS_START) {
+            // adaptive steps; the last evaluation leaves the state as it is and
+            // puts the point's squared scaled error in its own state slot
+            const real es = bs_update<V>(a, mode, e, g, u0, R, un);
+            if (mode == M_BS_4) {
+                su[0] = es;
+                continue;
+            }
         } else {  // M_RK4_4
 #pragma unroll
             for (int v = 0; v < V; ++v) un[v] = r1[it][v] + a.rk_c * (r2[it][v] + R[v]);
         }
-        st_v<V>(a.U + g, un);
+        if (!AD || mode != M_BS_START) st_v<V>(a.U + g, un);
         st_v<V>(su, un);
     }
     if (mode == M_RESIDUAL || mode == M_RESIDUAL_J) return;
     __syncthreads();
+    if (AD && (mode == M_BS_START || mode == M_BS_4)) {
+        // the next attempt derives its face data from its first stage state
+        if (mode == M_BS_4) bs_error_sums<D, N, PAD>(a, sU, e0, ne, tid, TH);
+        return;
+    }
 
     // 4) the new state's gradient, then face state + gradient flux part to
     // the partners' inbound slots for the next stage
@@ -2230,6 +2391,7 @@ __global__ void k_probe(const KArgs<real> a) {
     if (pr >= a.n_probe) return;
     const ProbeDesc &P = a.probes[pr];
     if (P.group != a.group) return;
+    if (a.ACC && a.ACC[P.inst] != 1) return;   // adaptive: accepted steps only
     double u[V];
 #pragma unroll
     for (int v = 0; v < V; ++v) u[v] = 0.0;
@@ -2395,7 +2557,9 @@ __global__ void k_finite(const KArgs<real> a) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
          i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = a.elem0 + i / NSP;
-        const real *u = a.U + (e * NSP + i % NSP) * V;
+        // adaptive steps: a rejected attempt's trial state is not the solution
+        const real *src = (a.ACC && a.ACC[a.EINST[e]] == 0) ? a.R3 : a.U;
+        const real *u = src + (e * NSP + i % NSP) * V;
         bool bad = false;
 #pragma unroll
         for (int v = 0; v < V; ++v) bad |= !isfinite(u[v]);
@@ -2432,6 +2596,97 @@ __global__ void k_to_f64(const KArgs<real> a) {
 }
 
 // --------------------------------------------------------------------------
+// Adaptive steps, between attempts.
+// K_BS_COMMIT (grid-stride over a group's values): an instance whose last
+// attempt was accepted takes u_{n+1} (U) as its new u_n and k4 (R2) as its
+// new k1; a rejected (or fresh) one keeps u_n (R3) and k1 (R1).  Either way U
+// becomes the first stage state u_n + h/2 k1 with the instance's next step h.
+// With a.mode = 1 (after the last attempt of fr_rk_step) it only puts u_n
+// back into U where the last attempt was rejected, so that U is every
+// instance's current solution between calls.
+// --------------------------------------------------------------------------
+template <int D, int N, typename real>
+__global__ void k_bs_commit(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int64_t PER = (int64_t)G::NSP * G::V;
+    const int64_t total = a.n_elem * PER;
+    const int64_t off = a.elem0 * PER;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t q = off + i;
+        const int inst = a.EINST[q / PER];
+        if (a.mode == 1) {
+            if (a.ACC[inst] == 0) a.U[q] = a.R3[q];
+            continue;
+        }
+        const real c = (real)(0.5 * a.ADAPT[(int64_t)inst * kAdStride + kAdHuse]);
+        real u, k;
+        if (a.ACC[inst] == 1) {
+            u = a.U[q];
+            k = a.R2[q];
+            a.R3[q] = u;
+            a.R1[q] = k;
+        } else {
+            u = a.R3[q];
+            k = a.R1[q];
+        }
+        a.U[q] = u + c * k;
+    }
+}
+
+// K_BS_CONTROL: one block per instance.  The error norm (fixed-shape tree
+// over the instance's per-element sums: deterministic), then the elementary
+// error-per-step controller (Hairer, Norsett and Wanner, Solving ODEs I,
+// Sec. II.4) in FP64: accepted when err < 1, and the next step is
+// h err^(-1/3) times a safety factor 0.9, the ratio kept within [0.2, 10]
+// (at most 1 right after a rejection within the same step); every step is
+// capped at dt_max and cut to end exactly at t_end (0 once reached).
+constexpr double kCtrlSafety = 0.9, kCtrlFmin = 0.2, kCtrlFmax = 10.0;
+
+template <int D, int N, typename real>
+__global__ void __launch_bounds__(kReduceThreads) k_bs_control(const KArgs<real> a) {
+    __shared__ double red[kReduceThreads];
+    const int inst = blockIdx.x;
+    const AdaptRange &r = a.ARANGE[inst];
+    double sum = 0.0;
+    for (int g = 0; g < kMaxGroupsAd; ++g)
+        for (int64_t i = threadIdx.x; i < r.count[g]; i += kReduceThreads) sum += a.ERRE[r.start[g] + i];
+    red[threadIdx.x] = sum;
+    __syncthreads();
+    for (int w = kReduceThreads / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x != 0) return;
+    double *rec = a.ADAPT + (int64_t)inst * kAdStride;
+    const double h = rec[kAdHuse];
+    int acc = 0;
+    if (h > 0.0) {
+        const double err = sqrt(red[0] / r.nval);
+        rec[kAdErr] = err;
+        if (err < 1.0) {
+            double f = err == 0.0 ? kCtrlFmax : fmin(kCtrlFmax, kCtrlSafety * pow(err, -1.0 / 3.0));
+            if (rec[kAdRej] != 0.0) f = fmin(1.0, f);
+            const double t = rec[kAdT];
+            rec[kAdT] = t + h < a.t_end ? t + h : a.t_end;
+            rec[kAdH] = h * f;
+            rec[kAdRej] = 0.0;
+            rec[kAdNacc] += 1.0;
+            rec[kAdSamples] += 1.0;
+            acc = 1;
+        } else {
+            rec[kAdH] = h * fmax(kCtrlFmin, kCtrlSafety * pow(err, -1.0 / 3.0));
+            rec[kAdRej] = 1.0;
+            rec[kAdNrej] += 1.0;
+        }
+    }
+    double hn = fmin(rec[kAdH], a.dt_max);
+    if (rec[kAdT] + hn > a.t_end) hn = a.t_end - rec[kAdT];
+    rec[kAdHuse] = fmax(hn, 0.0);
+    a.ACC[inst] = acc;
+}
+
+// --------------------------------------------------------------------------
 // Mortar faces: faces joining elements of different degree (mortar element
 // coupling, conservative).  The mortar is the higher-degree side's set of
 // flux points.  Each side's element stores its own face trace in its outbox
@@ -2448,6 +2703,7 @@ __global__ void k_to_f64(const KArgs<real> a) {
 //    On these faces the lower-degree side is LDG's left side.
 // --------------------------------------------------------------------------
 constexpr int kMaxGroups = 5;   // degrees 0..4
+static_assert(kMaxGroups == kMaxGroupsAd, "one degree-group bound");
 
 struct MortarFace {
     int32_t glo, ghi;          // degree groups of the lower and higher side
@@ -2622,10 +2878,16 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     const bool l1 = has_level1<N, real>() && a.regs_level == 1;
     const bool l2 = has_level1<N, real>() && a.regs_level == 2;
     constexpr int R1 = has_level1<N, real>() ? 1 : 0, R2 = has_level1<N, real>() ? 2 : 0;
+    const bool ad = a.ADAPT != nullptr;   // adaptive steps: their own instantiation, register level 0
     if (kind == K_FLUX) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_FLUX, visc, a.tc != 0);
-        if (visc) {
+        if (ad) {
+            auto k = visc ? k_flux<D, N, real, true, 0, true> : k_flux<D, N, real, false, 0, true>;
+            cudaError_t err = prep_smem(k, sm);
+            if (err != cudaSuccess) return err;
+            k<<<(unsigned)tiles, G::THREADS, sm, st>>>(a);
+        } else if (visc) {
             auto k = l2 ? k_flux<D, N, real, true, R2> : l1 ? k_flux<D, N, real, true, R1> : k_flux<D, N, real, true, 0>;
             cudaError_t err = prep_smem(k, sm);
             if (err != cudaSuccess) return err;
@@ -2653,7 +2915,8 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     } else if (kind == K_STAGE) {
         if (a.n_elem <= 0) return cudaSuccess;
         const size_t sm = smem_bytes<D, N, real>(K_STAGE, true, a.tc != 0);
-        auto k = l2 ? k_stage<D, N, real, R2> : l1 ? k_stage<D, N, real, R1> : k_stage<D, N, real, 0>;
+        auto k = ad ? k_stage<D, N, real, 0, true>
+                    : l2 ? k_stage<D, N, real, R2> : l1 ? k_stage<D, N, real, R1> : k_stage<D, N, real, 0>;
         cudaError_t err = prep_smem(k, sm);
         if (err != cudaSuccess) return err;
         k<<<(unsigned)tiles, G::GTHREADS, sm, st>>>(a);
@@ -2678,6 +2941,12 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     } else if (kind == K_FINITE) {
         if (a.n_elem <= 0) return cudaSuccess;
         k_finite<D, N, real><<<grid_hint, 256, 0, st>>>(a);
+    } else if (kind == K_BS_COMMIT) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        k_bs_commit<D, N, real><<<grid_hint, 256, 0, st>>>(a);
+    } else if (kind == K_BS_CONTROL) {
+        if (grid_hint <= 0) return cudaSuccess;
+        k_bs_control<D, N, real><<<grid_hint, kReduceThreads, 0, st>>>(a);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -17,7 +17,7 @@ _LIB_PATH = os.path.join(_PKG, "libfr.so")
 FR_OK = 0
 FR_TAG_INTERIOR, FR_TAG_PERIODIC, FR_TAG_WALL = 0, 1, 2
 FR_TAG_FARFIELD, FR_TAG_INFLOW, FR_TAG_OUTFLOW = 3, 4, 5
-FR_RK4, FR_LSRK45 = 0, 1
+FR_RK4, FR_LSRK45, FR_BS32 = 0, 1, 2
 FR_FP64, FR_FP32 = 0, 1
 FR_FLUX_RUSANOV, FR_FLUX_ROE = 0, 1
 FR_VISC_BR2, FR_VISC_LDG = 0, 1
@@ -35,7 +35,7 @@ EXPORTED = ["fr_mesh_create", "fr_mesh_create_varp", "fr_mesh_degrees", "fr_mesh
             "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
             "fr_integral", "fr_integral_static", "fr_last_launch_count", "fr_profile_steps",
             "fr_instance_status", "fr_force_coefficients", "fr_tune", "fr_schedule", "fr_tune_lookup",
-            "fr_alu_peak",
+            "fr_alu_peak", "fr_step_control",
             "fr_last_error"]
 
 
@@ -52,14 +52,19 @@ class Config(C.Structure):
                 ("br2_eta", C.c_double), ("dt", C.c_double), ("viscous", C.c_int),
                 ("rk", C.c_int), ("precision", C.c_int), ("flux", C.c_int),
                 ("viscous_scheme", C.c_int), ("check_every", C.c_int), ("ldg_beta", C.c_double),
-                ("ldg_tau", C.c_double), ("flux_reference", C.c_int), ("reserved", C.c_int)]
+                ("ldg_tau", C.c_double), ("flux_reference", C.c_int), ("reserved", C.c_int),
+                ("t_end", C.c_double), ("dt_max", C.c_double), ("rtol", C.c_double),
+                ("atol", C.c_double * 5)]
 
 
 def make_config(dim, gamma=1.4, prandtl=0.71, mu=0.0, rho_inf=1.0, v_inf=None, p_inf=1.0,
                 inflow_delta=0.0, inflow_ywall=0.0, br2_eta=0.0, dt=1e-3, viscous=False,
                 rk=FR_LSRK45, precision=FR_FP64, flux=FR_FLUX_RUSANOV,
                 viscous_scheme=FR_VISC_BR2, ldg_beta=0.5, ldg_tau=0.1, check_every=0,
-                flux_reference=0) -> Config:
+                flux_reference=0, t_end=0.0, dt_max=0.0, rtol=0.0, atol=None) -> Config:
+    """A solver configuration.  rk=FR_BS32 selects adaptive steps: dt is the
+    first proposed step, t_end / dt_max (<= 0: none) bound them, rtol and atol
+    (a scalar or one value per conserved variable) set the error norm."""
     c = Config()
     c.gamma, c.prandtl, c.mu = gamma, prandtl, mu
     c.rho_inf, c.p_inf = rho_inf, p_inf
@@ -72,6 +77,11 @@ def make_config(dim, gamma=1.4, prandtl=0.71, mu=0.0, rho_inf=1.0, v_inf=None, p
     c.viscous_scheme, c.ldg_beta, c.ldg_tau = viscous_scheme, ldg_beta, ldg_tau
     c.check_every = int(check_every)
     c.flux_reference = int(flux_reference)
+    c.t_end, c.dt_max, c.rtol = float(t_end), float(dt_max), float(rtol)
+    at = [0.0] * 5 if atol is None else (list(np.broadcast_to(np.asarray(atol, dtype=np.float64), (dim + 2,)))
+                                         + [0.0] * (3 - dim))
+    for i in range(5):
+        c.atol[i] = at[i]
     return c
 
 
@@ -123,6 +133,7 @@ def lib():
     L.fr_integral.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
     L.fr_integral_static.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
     L.fr_instance_status.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(I)]
+    L.fr_step_control.argtypes = [P, I, dp]
     L.fr_force_coefficients.argtypes = [P, I, D, dp, dp]
     L.fr_tune.argtypes = [P, C.c_char_p, I, C.c_char_p, C.c_size_t]
     L.fr_schedule.argtypes = [P, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t]
@@ -430,6 +441,14 @@ class Solver:
         if st not in (0, 5):
             _check(st, "fr_instance_status")
         return flags, first.value
+
+    def step_control(self, inst):
+        """Step-control record of one instance (adaptive steps, FR_BS32)."""
+        out = np.zeros(8)
+        _check(lib().fr_step_control(self.handle, inst, out.ctypes.data_as(C.POINTER(C.c_double))),
+               "fr_step_control")
+        keys = ("t", "h", "h_next", "err", "rejected_in_step", "accepted", "rejected", "samples")
+        return dict(zip(keys, out.tolist()))
 
     def synchronize(self):
         self.stream.synchronize()

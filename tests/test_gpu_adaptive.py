@@ -1,0 +1,218 @@
+"""Adaptive steps (FR_BS32: the Bogacki-Shampine 3(2) pair with the
+elementary error-per-step controller, in place of the paper's adaptive
+second-order scheme of Sec. 2.3) against the oracle's ``AdaptiveBS32``:
+
+* FP64, attempt by attempt: error norm, accept / reject, time, proposed and
+  next step of every attempt, and the state at the end (1e-12), for an Euler
+  vortex, periodic Navier-Stokes (split and fused BR2 stages) and a batch of
+  two airfoils whose instances take different step sequences; each case has
+  rejected attempts and ends on t_end, after which further attempts leave
+  the state bitwise as it is.  The oracle's error norms of all attempts stay
+  well away from the threshold 1, so both sides take the same decisions;
+* observers and wall forces sample accepted steps only (pressures against
+  the oracle's at its accepted steps, the mean force over them);
+* checkpoint (state + accumulators with the step-control records) and
+  restart continue bitwise like the uninterrupted run;
+* FP32 (perturbation storage): same decisions, end time exactly t_end and
+  the state within 1e-5 of the oracle's.
+"""
+import json
+
+import numpy as np
+import pytest
+
+from tests import fr_cases as FC
+from oracle import timestep as T
+from oracle.acoustics import Probe
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _cfg(case, precision, h0, t_end, dt_max, rtol, atol):
+    from paper_2312_14167_gb300 import fr
+    cfg = FC.lib_config(case, precision)
+    cfg.rk = fr.FR_BS32
+    cfg.dt, cfg.t_end, cfg.dt_max, cfg.rtol = h0, t_end, dt_max, rtol
+    for v in range(case.dim + 2):
+        cfg.atol[v] = atol[v]
+    return cfg
+
+
+def _solver(case, cfg, schedule=None, tmp_path=None):
+    from paper_2312_14167_gb300 import fr
+    sol = fr.Solver([fr.Mesh(m, case.p) for m in case.meshes], cfg)
+    if schedule is not None:
+        _, key = sol.schedule()
+        cache = tmp_path / "forced.json"
+        cache.write_text(json.dumps({key: schedule + ";ms=1.0"}))
+        assert schedule in sol.tune(str(cache), mode=2)
+    return sol
+
+
+def _oracle(case, inst, h0, t_end, dt_max, rtol, atol):
+    disc = FC.oracle_disc(case, inst)
+    u0 = FC.initial_state(case, disc.sol_coords(), inst)
+    ad = T.AdaptiveBS32(disc.residual, u0, h0, t_end, rtol, np.asarray(atol[:case.dim + 2]),
+                        dt_max=dt_max if dt_max > 0 else np.inf)
+    return disc, u0, ad
+
+
+def _check_attempt(rec, ad, tag):
+    """The GPU's record after one attempt against the oracle's state.  The
+    error estimate h (-5/72 k1 + 1/12 k2 + 1/9 k3 - 1/8 k4) cancels: its
+    relative rounding grows as the norm falls below 1 (4e-9 measured at
+    err = 5e-5), so err is compared to 1e-9 (1 + err) absolute, which is
+    1e-9 relative where it decides acceptance.  The step ratio
+    0.9 err^(-1/3) carries a third of that into h, and t sums the h: both
+    to 1e-8 relative."""
+    last = ad.records[-1]
+    assert rec["accepted"] == ad.n_accepted and rec["rejected"] == ad.n_rejected, tag
+    assert abs(rec["err"] - last["err"]) <= 1e-9 * (1.0 + last["err"]), (tag, rec["err"], last["err"])
+    assert abs(rec["t"] - ad.t) <= 1e-8 * max(ad.t, 1e-300), (tag, rec["t"], ad.t)
+    assert abs(rec["h"] - ad.h) <= 1e-8 * ad.h, (tag, rec["h"], ad.h)
+    assert abs(rec["h_next"] - ad.step_size()) <= 1e-8 * max(ad.h, 1e-300), tag
+    assert rec["rejected_in_step"] == float(ad.rejected_in_step), tag
+
+
+CASES = {
+    # name: (case, first step h0, t_end, dt_max (0: none), rtol, atol per variable)
+    "vortex": (lambda: FC.vortex_case(n=4, p=2), 0.2, 0.3, 0.05, 1e-5, [1e-6, 1e-6, 1e-6, 1e-5]),
+    "periodic_ns": (lambda: FC.periodic_ns_case(n=4, p=3), 0.04, 0.12, 0.0, 1e-6, [1e-7] * 4),
+}
+
+
+@pytest.mark.parametrize("name,schedule", [("vortex", None), ("periodic_ns", None),
+                                           ("periodic_ns", "stage=fused;regs=0;contract=simt")])
+def test_fp64_attempts_match_the_oracle(tmp_path, name, schedule):
+    make, h0, t_end, dt_max, rtol, atol = CASES[name]
+    case = make()
+    sol = _solver(case, _cfg(case, "fp64", h0, t_end, dt_max, rtol, atol), schedule, tmp_path)
+    disc, u0, ad = _oracle(case, 0, h0, t_end, dt_max, rtol, atol)
+    sol.set_state(0, u0)
+    rec0 = sol.step_control(0)
+    assert rec0["t"] == 0.0 and rec0["h"] == h0 and rec0["h_next"] == ad.step_size()
+    n = 0
+    while ad.t < t_end:
+        sol.rk_step(1)
+        ad.attempt()
+        n += 1
+        _check_attempt(sol.step_control(0), ad, f"{name} attempt {n}")
+        assert n < 200
+    errs = np.array([r["err"] for r in ad.records])
+    print(f"{name} {schedule}: {n} attempts, {ad.n_accepted} accepted, {ad.n_rejected} rejected, "
+          f"min |err - 1| {np.min(np.abs(errs - 1)):.3f}")
+    assert ad.n_rejected >= 1 and np.min(np.abs(errs - 1)) > 1e-3
+    u = sol.get_state(0)
+    err = FC.rel_l2(u, ad.u)
+    print(f"{name}: state at t_end vs oracle {err:.3e}")
+    assert err < 1e-12
+    # at t_end every further attempt is a no-op
+    sol.rk_step(3)
+    rec = sol.step_control(0)
+    assert rec["t"] == t_end and rec["h_next"] == 0.0 and rec["accepted"] == ad.n_accepted
+    assert np.array_equal(sol.get_state(0), u)
+
+
+def test_fp64_batch_instances_step_independently_and_sample_accepted_steps():
+    """Two airfoils of different sizes: each instance has its own step
+    sequence (they reach t_end after different numbers of attempts); one
+    observer per instance samples the accepted steps only, and the mean wall
+    force averages over them."""
+    case = FC.airfoil_case(n_inst=2, e_lo=300, e_hi=400)
+    h0, t_end, rtol, atol = 3 * case.dt, 40 * case.dt, 1e-7, [1e-8] * 4
+    sol = _solver(case, _cfg(case, "fp64", h0, t_end, 0.0, rtol, atol))
+    orc = [_oracle(case, i, h0, t_end, 0.0, rtol, atol) for i in range(2)]
+    pts = [np.array([0.8, 0.35]), np.array([-0.6, -0.5])]
+    ids, probes = [], []
+    for i in range(2):
+        sol.set_state(i, orc[i][1])
+        ids.append(sol.probe_add(i, pts[i]))
+        probes.append(Probe(orc[i][0], pts[i]))
+    sol.probe_reset()
+    hist = [[], []]
+    force = [np.zeros(2), np.zeros(2)]
+    n = 0
+    while any(o[2].t < t_end for o in orc):
+        sol.rk_step(1)
+        n += 1
+        for i in range(2):
+            disc, _, ad = orc[i]
+            if ad.t < t_end:
+                if ad.attempt():
+                    hist[i].append(probes[i].pressure(ad.u))
+                    force[i] += disc.wall_force(ad.u)
+            _check_attempt(sol.step_control(i), ad, f"airfoil[{i}] attempt {n}")
+        assert n < 200
+    counts = [o[2].n_accepted + o[2].n_rejected for o in orc]
+    print(f"airfoils: attempts to t_end {counts}, accepted {[o[2].n_accepted for o in orc]}")
+    assert counts[0] != counts[1] and all(o[2].n_rejected >= 1 for o in orc)
+    for i in range(2):
+        ad = orc[i][2]
+        assert FC.rel_l2(sol.get_state(i), ad.u) < 1e-12
+        h = sol.probe_history(ids[i])
+        assert h.size == ad.n_accepted
+        assert np.allclose(h, hist[i], rtol=1e-11, atol=0.0)
+        rec = sol.step_control(i)
+        assert rec["samples"] == ad.n_accepted
+        want = force[i] / ad.n_accepted
+        assert np.all(np.abs(sol.forces(i) - want) < 1e-12 * case.p_inf * 2.2)
+
+
+def test_checkpoint_restart_continues_bitwise():
+    case = FC.airfoil_case(n_inst=2, e_lo=300, e_hi=400)
+    h0, t_end = 3 * case.dt, 40 * case.dt
+    sol = _solver(case, _cfg(case, "fp64", h0, t_end, 0.0, 1e-7, [1e-8] * 4))
+    us = [FC.initial_state(case, FC.oracle_disc(case, i).sol_coords(), i) for i in range(2)]
+    ids = []
+    for i in range(2):
+        sol.set_state(i, us[i])
+        ids.append(sol.probe_add(i, np.array([0.8, 0.35])))
+    sol.probe_reset()
+    sol.rk_step(10)
+    snap = [sol.get_state(i) for i in range(2)]
+    acc = sol.get_accumulators()
+    sol.rk_step(12)
+    ref = ([sol.get_state(i) for i in range(2)], [sol.step_control(i) for i in range(2)],
+           [sol.probe_history(p) for p in ids])
+    for i in range(2):
+        sol.set_state(i, snap[i])
+    sol.set_accumulators(acc)
+    sol.rk_step(12)
+    for i in range(2):
+        assert np.array_equal(sol.get_state(i), ref[0][i])
+        assert sol.step_control(i) == ref[1][i]
+        assert np.array_equal(sol.probe_history(ids[i]), ref[2][i])
+
+
+def test_fp32_adaptive_run_matches_the_oracle():
+    make, h0, t_end, dt_max, rtol, atol = CASES["periodic_ns"]
+    case = make()
+    sol = _solver(case, _cfg(case, "fp32", h0, t_end, dt_max, rtol, atol))
+    disc, u0, ad = _oracle(case, 0, h0, t_end, dt_max, rtol, atol)
+    sol.set_state(0, u0)
+    n = 0
+    worst, worst_near = 0.0, 0.0
+    while ad.t < t_end:
+        sol.rk_step(1)
+        ad.attempt()
+        n += 1
+        rec = sol.step_control(0)
+        assert rec["accepted"] == ad.n_accepted and rec["rejected"] == ad.n_rejected
+        e_ref = ad.records[-1]["err"]
+        d = abs(rec["err"] - e_ref) / e_ref
+        worst = max(worst, d)
+        if 0.1 <= e_ref <= 10.0:   # where the norm decides acceptance
+            worst_near = max(worst_near, d)
+        assert n < 200
+    rec = sol.step_control(0)
+    err = FC.rel_l2(sol.get_state(0), ad.u)
+    print(f"fp32 adaptive: {n} attempts, same decisions; error norms within {worst_near:.2e} relative "
+          f"for err in [0.1, 10] ({worst:.2e} over all), t {rec['t']} vs {ad.t}, state vs oracle {err:.3e}")
+    assert rec["t"] == t_end and worst_near < 1e-3 and err < 1e-5

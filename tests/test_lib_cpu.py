@@ -100,6 +100,33 @@ def test_solver_needs_a_device_workspace(fr):
     assert st == 7 and b"too small" in fr.lib().fr_last_error()
 
 
+def test_adaptive_configuration_is_checked_and_sized(fr):
+    """FR_BS32 wants dt > 0 and tolerances that give every variable a positive
+    scale (atol_v + rtol > 0); its workspace adds the third RK register and
+    the per-element error sums (state size + 8 bytes per element, give or
+    take the 256-byte slots of the two buffers)."""
+    import ctypes as C
+    vm = M.vortex_mesh(4)
+    m = fr.Mesh(vm, 2)
+    arr = (C.c_void_p * 1)(m.handle)
+    base = fr.lib().fr_workspace_bytes(arr, 1, C.byref(fr.make_config(2, p_inf=1.0)))
+    good = fr.make_config(2, p_inf=1.0, rk=fr.FR_BS32, dt=0.01, rtol=1e-6, atol=1e-8)
+    need = fr.lib().fr_workspace_bytes(arr, 1, C.byref(good))
+    n_elem, nsp = vm.elem_vert.shape[0], 9
+    extra = n_elem * nsp * 4 * 8 + n_elem * 8
+    # (without adaptive steps both buffers still take one 256-byte slot)
+    assert extra - 2 * 256 <= need - base <= extra + 2 * 256
+    for bad in (dict(dt=0.0, rtol=1e-6, atol=1e-8), dict(dt=0.01, rtol=-1.0, atol=1e-8),
+                dict(dt=0.01, rtol=0.0, atol=0.0), dict(dt=0.01, rtol=0.0, atol=[1e-8, 1e-8, 0.0, 1e-8]),
+                dict(dt=0.01, rtol=1e-6, atol=-1e-8)):
+        cfg = fr.make_config(2, p_inf=1.0, rk=fr.FR_BS32, **bad)
+        assert fr.lib().fr_workspace_bytes(arr, 1, C.byref(cfg)) == 0, bad
+    # relative tolerance alone is enough; an unknown scheme is refused
+    assert fr.lib().fr_workspace_bytes(arr, 1, C.byref(fr.make_config(2, p_inf=1.0, rk=fr.FR_BS32,
+                                                                       dt=0.01, rtol=1e-6))) == need
+    assert fr.lib().fr_workspace_bytes(arr, 1, C.byref(fr.make_config(2, p_inf=1.0, rk=3))) == 0
+
+
 @pytest.mark.parametrize("dim", [2, 3])
 def test_variable_degree_mesh_host_processing_matches_oracle(fr, dim):
     from oracle.fr_var import VarFRDiscretisation
