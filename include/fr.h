@@ -243,6 +243,14 @@ fr_status fr_rk_step(fr_solver *solver, int n_steps);
  * for other schemes, a null output or an instance out of range. */
 fr_status fr_step_control(fr_solver *solver, int inst, double *out8);
 
+/* FR_BS32: move the end time of every instance to t_end (<= 0: none).
+ * Instances that had stopped at the old end time continue from there with
+ * their proposed step; none goes past the new one.  With it a run reaches a
+ * common time in every instance (the end of the transient period, where the
+ * observers are reset, Secs. 3.1.2 and 5.2), then goes on.  Synchronises.
+ * FR_ERR_INVALID_ARG for other schemes or a NaN time. */
+fr_status fr_set_end_time(fr_solver *solver, double t_end);
+
 /* Add an observer at physical point x (dim values) of instance ``inst``; the
  * containing element and reference coordinates are found by Newton's method
  * on the element maps (FP64).  Returns its id in *probe_id.  The pressure is

@@ -1619,6 +1619,33 @@ extern "C" fr_status fr_step_control(fr_solver *s, int inst, double *out8) {
     return FR_OK;
 }
 
+extern "C" fr_status fr_set_end_time(fr_solver *s, double t_end) {
+    if (!s) { set_error("null solver"); return FR_ERR_INVALID_ARG; }
+    if (!s->adapt || std::isnan(t_end)) {
+        set_error(s->adapt ? "fr_set_end_time: invalid end time" : "fr_set_end_time: the solver does not use adaptive steps");
+        return FR_ERR_INVALID_ARG;
+    }
+    s->cfg.t_end = t_end;
+    // every instance's next step under the new end time (the rule of K_BS_CONTROL)
+    const size_t n = (size_t)s->n_inst * frk::kAdStride;
+    std::vector<double> rec(n);
+    FR_CK(cudaMemcpyAsync(rec.data(), s->ADAPT, n * 8, cudaMemcpyDeviceToHost, s->stream));
+    FR_CK(cudaStreamSynchronize(s->stream));
+    const double te = eff_t_end(s->cfg), hm = eff_dt_max(s->cfg);
+    for (int i = 0; i < s->n_inst; ++i) {
+        double *r = &rec[(size_t)i * frk::kAdStride];
+        double h = std::min(r[frk::kAdH], hm);
+        if (r[frk::kAdT] + h > te) h = te - r[frk::kAdT];
+        r[frk::kAdHuse] = std::max(h, 0.0);
+    }
+    FR_CK(cudaMemcpyAsync(s->ADAPT, rec.data(), n * 8, cudaMemcpyHostToDevice, s->stream));
+    FR_CK(cudaStreamSynchronize(s->stream));
+    // the initial record of a state set later ends at the new time too
+    for (int i = 0; i < s->n_inst; ++i) s->adapt_init[(size_t)i * frk::kAdStride + frk::kAdHuse] = first_step(s->cfg);
+    drop_graphs(s);   // the captured attempts carry the end time
+    return FR_OK;
+}
+
 extern "C" int64_t fr_last_launch_count(const fr_solver *s) { return s ? s->last_launches : -1; }
 
 extern "C" fr_status fr_profile_steps(fr_solver *s, int n_steps, double *ms, int64_t *count) {

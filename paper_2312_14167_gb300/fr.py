@@ -35,7 +35,7 @@ EXPORTED = ["fr_mesh_create", "fr_mesh_create_varp", "fr_mesh_degrees", "fr_mesh
             "fr_probe_reset", "fr_oaspl", "fr_probe_stats", "fr_forces", "fr_conservation",
             "fr_integral", "fr_integral_static", "fr_last_launch_count", "fr_profile_steps",
             "fr_instance_status", "fr_force_coefficients", "fr_tune", "fr_schedule", "fr_tune_lookup",
-            "fr_alu_peak", "fr_step_control",
+            "fr_alu_peak", "fr_step_control", "fr_set_end_time",
             "fr_last_error"]
 
 
@@ -134,6 +134,7 @@ def lib():
     L.fr_integral_static.argtypes = [P, I, dp, C.POINTER(C.c_int64)]
     L.fr_instance_status.argtypes = [P, C.POINTER(C.c_int32), C.POINTER(I)]
     L.fr_step_control.argtypes = [P, I, dp]
+    L.fr_set_end_time.argtypes = [P, D]
     L.fr_force_coefficients.argtypes = [P, I, D, dp, dp]
     L.fr_tune.argtypes = [P, C.c_char_p, I, C.c_char_p, C.c_size_t]
     L.fr_schedule.argtypes = [P, C.c_char_p, C.c_size_t, C.c_char_p, C.c_size_t]
@@ -449,6 +450,28 @@ class Solver:
                "fr_step_control")
         keys = ("t", "h", "h_next", "err", "rejected_in_step", "accepted", "rejected", "samples")
         return dict(zip(keys, out.tolist()))
+
+    def set_end_time(self, t_end):
+        """Adaptive steps: move every instance's end time (fr_set_end_time)."""
+        _check(lib().fr_set_end_time(self.handle, float(t_end)), "fr_set_end_time")
+
+    def advance_to(self, t_end, chunk=50, max_attempts=100000):
+        """Adaptive steps: attempts until every instance has reached t_end
+        (checked every `chunk` attempts), at most max_attempts.  Returns one
+        flag per instance: True where t_end was reached (False means the
+        step size collapsed, e.g. on a diverging flow)."""
+        self.set_end_time(t_end)
+        n = len(self.meshes)
+        done = 0
+        reached = np.zeros(n, dtype=bool)
+        while done < max_attempts:
+            k = min(chunk, max_attempts - done)
+            self.rk_step(k)
+            done += k
+            reached = np.array([self.step_control(i)["t"] >= t_end for i in range(n)])
+            if reached.all():
+                break
+        return reached
 
     def synchronize(self):
         self.stream.synchronize()

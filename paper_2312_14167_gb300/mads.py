@@ -231,12 +231,18 @@ class BatchedPollEvaluator:
     mesh -> degree per element (the far-field sponge zones of Sec. 5.1).
     With ``config.check_every > 0`` a candidate whose flow went non-finite
     during the run is flagged by the solver and scores +inf (rejected, like
-    an infeasible design)."""
+    an infeasible design).  With adaptive steps (``config.rk == FR_BS32``)
+    the horizons are times instead: every candidate advances to
+    ``t_transient``, the observers are reset, and every candidate advances
+    by ``t_average`` more; a candidate that does not get there within
+    ``max_attempts`` attempts per phase (its step collapsed) scores +inf."""
 
     def __init__(self, make_mesh, p: int, config, n_transient: int, n_average: int, start,
                  objective, p_ref: float = 2e-5, p_scale: float = 1.0, mean_mode: int = 0,
-                 a_ref: float | None = None):
+                 a_ref: float | None = None, t_transient: float | None = None,
+                 t_average: float | None = None, max_attempts: int = 100000):
         self.make_mesh, self.p, self.cfg = make_mesh, p, config
+        self.t_transient, self.t_average, self.max_attempts = t_transient, t_average, max_attempts
         self.n_transient, self.n_average = n_transient, n_average
         self.start, self.objective = start, objective
         self.p_ref, self.p_scale, self.mean_mode = p_ref, p_scale, mean_mode
@@ -255,10 +261,19 @@ class BatchedPollEvaluator:
             sol.set_state(i, self.start(fm.sol_coords(), designs[i], m))
             pts = m.info.get("probes", [m.info["probe"]] if "probe" in m.info else [])
             ids.append([sol.probe_add(i, np.asarray(x, float)) for x in pts])
-        sol.rk_step(self.n_transient)
-        sol.probe_reset()
-        sol.rk_step(self.n_average)
+        if self.cfg.rk == fr.FR_BS32:
+            if self.t_transient is None or self.t_average is None:
+                raise ValueError("adaptive steps need t_transient and t_average")
+            ok = sol.advance_to(self.t_transient, max_attempts=self.max_attempts)
+            sol.probe_reset()
+            ok &= sol.advance_to(self.t_transient + self.t_average, max_attempts=self.max_attempts)
+        else:
+            sol.rk_step(self.n_transient)
+            sol.probe_reset()
+            sol.rk_step(self.n_average)
+            ok = np.ones(len(designs), dtype=bool)
         failed = sol.instance_status()[0] if self.cfg.check_every > 0 else np.zeros(len(designs), np.int32)
+        failed = np.where(ok, failed, 1).astype(np.int32)
         out = []
         for i, d in enumerate(designs):
             if failed[i]:

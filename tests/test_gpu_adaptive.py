@@ -216,3 +216,42 @@ def test_fp32_adaptive_run_matches_the_oracle():
     print(f"fp32 adaptive: {n} attempts, same decisions; error norms within {worst_near:.2e} relative "
           f"for err in [0.1, 10] ({worst:.2e} over all), t {rec['t']} vs {ad.t}, state vs oracle {err:.3e}")
     assert rec["t"] == t_end and worst_near < 1e-3 and err < 1e-5
+
+
+def test_advance_to_a_common_time_then_average():
+    """The transient / averaging protocol with per-instance steps: both
+    airfoils stop exactly at t1 (their last steps cut to it), the observers
+    are reset there, and both go on to t2 from their proposed steps; the
+    window's samples are the oracle's accepted steps after t1."""
+    case = FC.airfoil_case(n_inst=2, e_lo=300, e_hi=400)
+    h0, rtol, atol = 3 * case.dt, 1e-7, [1e-8] * 4
+    t1, t2 = 20 * case.dt, 45 * case.dt
+    sol = _solver(case, _cfg(case, "fp64", h0, 0.0, 0.0, rtol, atol))
+    orc = [_oracle(case, i, h0, t1, 0.0, rtol, atol) for i in range(2)]
+    pt = np.array([0.8, 0.35])
+    ids, probes = [], []
+    for i in range(2):
+        sol.set_state(i, orc[i][1])
+        ids.append(sol.probe_add(i, pt))
+        probes.append(Probe(orc[i][0], pt))
+    assert sol.advance_to(t1, chunk=7).all()
+    for i in range(2):
+        assert sol.step_control(i)["t"] == t1
+        orc[i][2].run()
+        assert FC.rel_l2(sol.get_state(i), orc[i][2].u) < 1e-12
+    sol.probe_reset()
+    hist = [[], []]
+    for i in range(2):
+        ad = orc[i][2]
+        ad.t_end = t2
+        while ad.t < t2:
+            if ad.attempt():
+                hist[i].append(probes[i].pressure(ad.u))
+    assert sol.advance_to(t2, chunk=7).all()
+    for i in range(2):
+        ad = orc[i][2]
+        rec = sol.step_control(i)
+        assert rec["t"] == t2 and rec["samples"] == len(hist[i])
+        assert rec["accepted"] == ad.n_accepted and rec["rejected"] == ad.n_rejected
+        assert FC.rel_l2(sol.get_state(i), ad.u) < 1e-12
+        assert np.allclose(sol.probe_history(ids[i]), hist[i], rtol=1e-11, atol=0.0)

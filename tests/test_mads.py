@@ -156,3 +156,49 @@ def test_batched_poll_evaluator_runs_a_poll_on_the_gpu():
     vals3 = ev3([np.array([0.02, 0.12]), np.array([0.03, 0.10])])
     assert np.isfinite(vals3[0]) and vals3[0] == pytest.approx(vals[0], rel=1e-12)
     assert vals3[1] == math.inf and ev3.last["failed"] == [0, 1]
+
+
+@pytest.mark.gpu
+def test_batched_poll_evaluator_with_adaptive_steps():
+    """Adaptive steps: every candidate advances to the end of the transient
+    period (a common time), the observers are reset, every candidate advances
+    through the averaging window; a candidate started from a NaN never gets
+    there (its step collapses) and scores +inf, and the healthy candidate's
+    objective does not depend on the other one."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_14167_gb300 import fr
+    from synth import meshes as M, states as S
+    from tests import fr_cases as FC
+
+    def make_mesh(d):
+        return M.naca_omesh(d[0], 0.4, d[1], 3.0, 300)
+
+    dt = FC.cfl_dt([make_mesh((0.02, 0.12))], 0.2, 3)
+    p_inf = 1 / (1.4 * 0.04)
+    cfg = fr.make_config(2, mu=1 / 23000, v_inf=(1.0, 0.0), p_inf=p_inf, dt=dt, viscous=True,
+                         precision=fr.FR_FP32, rk=fr.FR_BS32, rtol=1e-6,
+                         atol=[1e-6, 1e-6, 1e-6, 1e-6 * p_inf / 0.4], check_every=5)
+
+    def start(x, d, m):
+        return S.wall_damped(x, m.info["wall_points"], 0.05, S.smooth_perturbed(x, 2, 0.2, amp=0.01))
+
+    def start_bad(x, d, m):
+        u = start(x, d, m)
+        if d[0] > 0.025:
+            u[0, 0, 0] = np.nan
+        return u
+
+    def objective(level, coeffs, d):
+        return mads.penalised_objective(level, coeffs[0], coeffs[1], 0.3, 0.05)
+
+    kw = dict(p_scale=101325 * 1.4 * 0.04, a_ref=1.0, t_transient=5 * dt, t_average=20 * dt,
+              max_attempts=300)
+    ev = mads.BatchedPollEvaluator(make_mesh, 3, cfg, 0, 0, start, objective, **kw)
+    vals = ev([np.array([0.02, 0.12]), np.array([0.01, 0.14])])
+    assert all(np.isfinite(vals)) and ev.last["failed"] == [0, 0]
+    ev2 = mads.BatchedPollEvaluator(make_mesh, 3, cfg, 0, 0, start_bad, objective, **kw)
+    vals2 = ev2([np.array([0.02, 0.12]), np.array([0.03, 0.10])])
+    assert vals2[0] == vals[0]
+    assert vals2[1] == math.inf and ev2.last["failed"] == [0, 1]
