@@ -826,7 +826,15 @@ def run_adaptive(args):
         runs.append((f"bs32_rtol{rtol:g}", dict(rk=fr.FR_BS32, rtol=rtol, atol=at), rtol))
     for name, kw, rtol in runs:
         sol = fr.Solver(fms, fr.make_config(W.dim, **{**common, **kw}))
-        sched = sol.tune(None, mode=1)
+        if args.schedule:   # fixed schedule (profiling): no measurement
+            _, key = sol.schedule()
+            cache = os.path.join(tempfile.gettempdir(), f"fr_tune_adaptive_{os.getpid()}.json")
+            with open(cache, "w") as f:
+                json.dump({key: args.schedule}, f)
+            sched = sol.tune(cache, mode=2)
+            os.unlink(cache)
+        else:
+            sched = sol.tune(None, mode=1)
         for i, u in enumerate(states):
             sol.set_state(i, u)
         sol.rk_step(args.warmup)

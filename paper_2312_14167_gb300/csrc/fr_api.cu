@@ -275,7 +275,7 @@ Plan make_plan(fr_mesh *const *meshes, int n_inst) {
                 if (wall) ++P.n_wall[g];
             }
         }
-        P.stage_doubles = std::max(P.stage_doubles, nsp_inst * V);
+        P.stage_doubles += nsp_inst * V;   // FP64 staging of the whole batch
         for (const MortarLink &L : m->mortars) {
             const fr_mesh *lo = m->parts[L.part_lo].get(), *hi = m->parts[L.part_hi].get();
             P.box_lo[P.group_of_degree[lo->p]] += lo->ref.nfpf;
@@ -648,9 +648,9 @@ fr_status enqueue_faces(fr_solver *s, int par, int64_t &cnt) {
 
 // One adaptive attempt (FR_BS32) from face-buffer parity p0: accept or roll
 // back the previous attempt and form the first stage state (K_BS_COMMIT), its
-// faces, the three stage evaluations (the last one computes k4 and the
-// per-element errors and writes no faces), the controller, then the samples
-// of accepted steps (on the faces of u_n+1, which the last evaluation read).
+// faces, the three stage evaluations (the last one computes k4 and writes no
+// faces), the per-element errors, the controller, then the samples of
+// accepted steps (on the faces of u_n+1, which the last evaluation read).
 fr_status enqueue_attempt(fr_solver *s, int p0, int64_t *n_launch) {
     int par = p0;
     int64_t cnt = 0;
@@ -669,6 +669,14 @@ fr_status enqueue_attempt(fr_solver *s, int p0, int64_t *n_launch) {
     for (int st = 0; st < 3; ++st) {
         FR_TRY(enqueue_eval(s, par, modes[st], 0.0, 0.0, 0.0, cnt));
         par ^= 1;
+    }
+    for (size_t g = 0; g < s->grp.size(); ++g) {
+        Launch er;
+        er.kind = frk::K_BS_ERROR;
+        er.g = (int)g;
+        er.n_elem = s->grp[g].E;
+        FR_CK(launch(s, er));
+        ++cnt;
     }
     Launch ct;
     ct.kind = frk::K_BS_CONTROL;
@@ -1462,6 +1470,85 @@ void finish_download(const fr_solver *s, int inst, const std::vector<double> &tm
     }
 }
 
+// Whole-batch staging (every instance in one degree group, the usual case):
+// one copy of all instances' FP64 states each way through the FP64 staging
+// buffer, which holds the batch in the ABI's order; the conversions run over
+// runs of instances that are consecutive both there and in their group.
+bool batch_stageable(const fr_solver *s) {
+    for (int i = 0; i < s->n_inst; ++i)
+        if (spread(s, i)) return false;
+    return true;
+}
+
+template <typename F>
+fr_status for_instance_runs(const fr_solver *s, F &&fn) {
+    const int V = s->V;
+    int g_run = -1;
+    int64_t e0 = 0, ne = 0, so = 0, off = 0;
+    for (int i = 0; i <= s->n_inst; ++i) {
+        int g = -1;
+        if (i < s->n_inst)
+            for (size_t h = 0; h < s->grp.size(); ++h)
+                if (s->grp[h].ne[i] > 0) g = (int)h;
+        const bool extend = i < s->n_inst && g == g_run && s->grp[g].off[i] == e0 + ne &&
+                            off == so + ne * s->grp[g].nsp * V;
+        if (!extend) {
+            if (g_run >= 0 && ne > 0) FR_TRY(fn(g_run, e0, ne, so));
+            if (i < s->n_inst) {
+                g_run = g;
+                e0 = g >= 0 ? s->grp[g].off[i] : 0;
+                ne = 0;
+                so = off;
+            }
+        }
+        if (i < s->n_inst) {
+            if (g >= 0) ne += s->grp[g].ne[i];
+            off += s->inst_nsp[i] * V;
+        }
+    }
+    return FR_OK;
+}
+
+fr_status enqueue_upload_batch(fr_solver *s, const double *u) {
+    size_t total = 0;
+    for (int i = 0; i < s->n_inst; ++i) total += (size_t)s->inst_nsp[i] * s->V;
+    FR_CK(cudaMemsetAsync(s->FLAGS, 0, (size_t)s->n_inst * 4, s->stream));
+    if (s->adapt) FR_TRY(reset_step_control(s, -1));
+    FR_CK(cudaMemcpyAsync(s->stage64, u, total * 8, cudaMemcpyHostToDevice, s->stream));
+    FR_TRY(for_instance_runs(s, [&](int g, int64_t e0, int64_t ne, int64_t so) -> fr_status {
+        Launch c;
+        c.kind = frk::K_TO_REAL;
+        c.g = g;
+        c.elem0 = e0;
+        c.n_elem = ne;
+        c.stage_off = so;
+        c.grid = grid_for(ne * s->grp[g].nsp * s->V);
+        FR_CK(launch(s, c));
+        return FR_OK;
+    }));
+    int64_t cnt = 0;
+    return enqueue_faces(s, s->parity, cnt);
+}
+
+fr_status enqueue_download_batch(fr_solver *s, int src, double *u) {
+    size_t total = 0;
+    for (int i = 0; i < s->n_inst; ++i) total += (size_t)s->inst_nsp[i] * s->V;
+    FR_TRY(for_instance_runs(s, [&](int g, int64_t e0, int64_t ne, int64_t so) -> fr_status {
+        Launch c;
+        c.kind = frk::K_TO_F64;
+        c.g = g;
+        c.elem0 = e0;
+        c.n_elem = ne;
+        c.integral_src = src;
+        c.stage_off = so;
+        c.grid = grid_for(ne * s->grp[g].nsp * s->V);
+        FR_CK(launch(s, c));
+        return FR_OK;
+    }));
+    FR_CK(cudaMemcpyAsync(u, s->stage64, total * 8, cudaMemcpyDeviceToHost, s->stream));
+    return FR_OK;
+}
+
 }  // namespace
 
 extern "C" fr_status fr_set_state(fr_solver *s, int inst, const double *u) {
@@ -1488,6 +1575,13 @@ static fr_status copy_out(fr_solver *s, int inst, int src, double *u) {
 extern "C" fr_status fr_set_states(fr_solver *s, const double *u) {
     fr::Range nvtx_range("fr_set_states");
     if (!s || !u) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
+    if (batch_stageable(s)) {
+        fr_status st = enqueue_upload_batch(s, u);
+        cudaError_t e = cudaStreamSynchronize(s->stream);   // the host array must outlive the copy
+        if (st != FR_OK) return st;
+        FR_CK(e);
+        return FR_OK;
+    }
     std::vector<std::vector<double>> tmp(s->n_inst);
     size_t off = 0;
     for (int i = 0; i < s->n_inst; ++i) {
@@ -1505,6 +1599,13 @@ extern "C" fr_status fr_set_states(fr_solver *s, const double *u) {
 extern "C" fr_status fr_get_states(fr_solver *s, double *u) {
     fr::Range nvtx_range("fr_get_states");
     if (!s || !u) { set_error("null argument"); return FR_ERR_INVALID_ARG; }
+    if (batch_stageable(s)) {
+        fr_status st = enqueue_download_batch(s, 0, u);
+        cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (st != FR_OK) return st;
+        FR_CK(e);
+        return FR_OK;
+    }
     std::vector<std::vector<double>> tmp(s->n_inst);
     std::vector<size_t> off(s->n_inst + 1, 0);
     for (int i = 0; i < s->n_inst; ++i) off[i + 1] = off[i] + (size_t)s->inst_nsp[i] * s->V;

@@ -48,6 +48,7 @@ enum Kind : int {
     K_INTERP_VISC = 10,  // face states + gradient flux parts (fused stage prologue)
     K_BS_COMMIT = 11,    // adaptive steps: accept / roll back, first stage state
     K_BS_CONTROL = 12,   // adaptive steps: error norm and step-size control per instance
+    K_BS_ERROR = 13,     // adaptive steps: per-element squared scaled errors of an attempt
 };
 
 enum Mode : int {
@@ -60,12 +61,12 @@ enum Mode : int {
     M_RESIDUAL = 6,    // RES = R
     M_RESIDUAL_J = 7,  // RES = J R (= -divergence)
     // adaptive steps, Bogacki-Shampine 3(2) pair with h the instance's step:
-    // registers R1 = k1 = R(u_n), R2 = k2, then the error combination, then
-    // k4 = R(u_{n+1}), R3 = u_n
+    // registers R1 = k1 = R(u_n), R2 = k2, then k4 = R(u_{n+1}), R3 = u_n,
+    // and RES (unused while stepping) the error combination
     M_BS_START = 8,    // fresh instances: R1 = R, R3 = u
     M_BS_2 = 9,        // R2 = R; u = R3 + (3/4) h R
-    M_BS_3 = 10,       // u = R3 + h (2/9 R1 + 1/3 R2 + 4/9 R); R2 = -5/72 R1 + 1/12 R2 + 1/9 R
-    M_BS_4 = 11,       // error of h (R2 - R/8) per element; R2 = R (state unchanged)
+    M_BS_3 = 10,       // u = R3 + h (2/9 R1 + 1/3 R2 + 4/9 R); RES = -5/72 R1 + 1/12 R2 + 1/9 R
+    M_BS_4 = 11,       // R2 = R (state unchanged); K_BS_ERROR then sums the error h (RES - R2/8)
 };
 
 // Step-control record of one instance (adaptive steps), FP64
@@ -1394,16 +1395,14 @@ k_grad(const KArgs<real> a) {
 //   k4 = R(u_{n+1}),  error e = h (-5/72 k1 + 1/12 k2 + 1/9 k3 - 1/8 k4),
 // and the error norm is the root mean square of e / (atol + rtol max(|u_n|, |u_{n+1}|))
 // over the instance's values.  The stage kernels apply the register updates
-// (bs_update) and, in the last evaluation, the per-element sums of the
-// squared scaled error (bs_error_sums); K_BS_CONTROL decides.
+// (bs_update); K_BS_ERROR forms the per-element sums of the squared scaled
+// error after the last evaluation, and K_BS_CONTROL decides.
 // --------------------------------------------------------------------------
 template <int V, typename real>
-__device__ __forceinline__ real bs_update(const KArgs<real> &a, int mode, int64_t e, int64_t g, const real *u0,
+__device__ __forceinline__ void bs_update(const KArgs<real> &a, int mode, int64_t e, int64_t g, const real *u0,
                                           const real *R, real *un) {
-    constexpr bool PERT = sizeof(real) == 4;
     const int inst = a.EINST[e];
     const double h = a.ADAPT[(int64_t)inst * kAdStride + kAdHuse];
-    real es = 0;
     if (mode == M_BS_START) {
         if (a.ACC[inst] == kAccFresh) {
             st_v<V>(a.R1 + g, R);
@@ -1434,44 +1433,12 @@ __device__ __forceinline__ real bs_update(const KArgs<real> &a, int mode, int64_
             un[v] += c2 * t[v];
             cm[v] += real(1.0 / 12.0) * t[v];
         }
-        st_v<V>(a.R2 + g, cm);
+        st_v<V>(a.RES + g, cm);
         ld_v<V>(a.R3 + g, t);
 #pragma unroll
         for (int v = 0; v < V; ++v) un[v] += t[v];
-    } else {  // M_BS_4
-        real cm[V], q[V];
-        ld_v<V>(a.R2 + g, cm);
-        ld_v<V>(a.R3 + g, q);
+    } else {  // M_BS_4: k4 only (the error is K_BS_ERROR's)
         st_v<V>(a.R2 + g, R);
-        const real hr = (real)h;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            real uq = q[v], uf = u0[v];
-            if constexpr (PERT) {   // full conserved values
-                const real rv = v == 0 ? a.ref.rho : (v == V - 1 ? a.ref.E : a.ref.m[v - 1]);
-                uq += rv;
-                uf += rv;
-            }
-            const real ev = hr * (cm[v] - real(0.125) * R[v]);
-            const real r = ev / (a.bs_atol[v] + a.bs_rtol * fmax(fabs(uq), fabs(uf)));
-            es += r * r;
-        }
-    }
-    return es;
-}
-
-// per-element sums (fixed order, FP64) of the points' squared scaled errors,
-// which the last evaluation left in the first value of each point's shared
-// state slot, into ERRE (after the barrier that ends the evaluation)
-template <int D, int N, bool PAD, typename real>
-__device__ __forceinline__ void bs_error_sums(const KArgs<real> &a, const real *sU, int64_t e0, int ne, int tid,
-                                              int threads) {
-    using G = Geo<D, N>;
-    constexpr int NSP = G::NSP, V = G::V;
-    for (int j = tid; j < ne; j += threads) {
-        double sum = 0.0;
-        for (int q = 0; q < NSP; ++q) sum += (double)sU[G::template slot<PAD>(j * NSP + q) * V];
-        a.ERRE[e0 + j] = sum;
     }
 }
 
@@ -1810,13 +1777,9 @@ k_flux(const KArgs<real> a) {
             }
             st_v<V>(a.R2 + g, acc);
         } else if (AD && mode >= M_BS_START) {
-            // adaptive steps; the last evaluation leaves the state as it is and
-            // puts the point's squared scaled error in its own state slot
-            const real es = bs_update<V>(a, mode, e, g, u0, R, un);
-            if (mode == M_BS_4) {
-                su[0] = es;
-                continue;
-            }
+            // adaptive steps; the last evaluation leaves the state as it is
+            bs_update<V>(a, mode, e, g, u0, R, un);
+            if (mode == M_BS_4) continue;
         } else {  // M_RK4_4
 #pragma unroll
             for (int v = 0; v < V; ++v) un[v] = r1[it][v] + a.rk_c * (r2[it][v] + R[v]);
@@ -1826,11 +1789,8 @@ k_flux(const KArgs<real> a) {
     }
     if (mode == M_RESIDUAL || mode == M_RESIDUAL_J) return;
     __syncthreads();
-    if (AD && (mode == M_BS_START || mode == M_BS_4)) {
-        // the next attempt derives its face data from its first stage state
-        if (mode == M_BS_4) bs_error_sums<D, N, PAD>(a, sU, e0, ne, tid, G::THREADS);
-        return;
-    }
+    // the next attempt derives its face data from its first stage state
+    if (AD && (mode == M_BS_START || mode == M_BS_4)) return;
 
     // 4) face values of the new state, stored in the partner's inbound slot
     // for the next stage (boundary points have no partner)
@@ -2286,13 +2246,9 @@ k_stage(const KArgs<real> a) {
             }
             st_v<V>(a.R2 + g, acc);
         } else if (AD && mode >= M_BS_START) {
-            // adaptive steps; the last evaluation leaves the state as it is and
-            // puts the point's squared scaled error in its own state slot
-            const real es = bs_update<V>(a, mode, e, g, u0, R, un);
-            if (mode == M_BS_4) {
-                su[0] = es;
-                continue;
-            }
+            // adaptive steps; the last evaluation leaves the state as it is
+            bs_update<V>(a, mode, e, g, u0, R, un);
+            if (mode == M_BS_4) continue;
         } else {  // M_RK4_4
 #pragma unroll
             for (int v = 0; v < V; ++v) un[v] = r1[it][v] + a.rk_c * (r2[it][v] + R[v]);
@@ -2302,11 +2258,8 @@ k_stage(const KArgs<real> a) {
     }
     if (mode == M_RESIDUAL || mode == M_RESIDUAL_J) return;
     __syncthreads();
-    if (AD && (mode == M_BS_START || mode == M_BS_4)) {
-        // the next attempt derives its face data from its first stage state
-        if (mode == M_BS_4) bs_error_sums<D, N, PAD>(a, sU, e0, ne, tid, TH);
-        return;
-    }
+    // the next attempt derives its face data from its first stage state
+    if (AD && (mode == M_BS_START || mode == M_BS_4)) return;
 
     // 4) the new state's gradient, then face state + gradient flux part to
     // the partners' inbound slots for the next stage
@@ -2570,29 +2523,74 @@ __global__ void k_finite(const KArgs<real> a) {
 // --------------------------------------------------------------------------
 // K_TO_REAL / K_TO_F64: FP64 host-layout staging <-> state of one instance
 // --------------------------------------------------------------------------
+// The staging conversions are pure HBM streams: with the value count, the
+// state offset and the staging address even (16-byte pairs of doubles), every
+// thread keeps kConvPairs pairs in flight; otherwise one value at a time.
+constexpr int kConvPairs = 4;
+
 template <int D, int N, typename real>
 __global__ void k_to_real(const KArgs<real> a) {
     using G = Geo<D, N>;
-    const int64_t total = a.n_elem * G::NSP * G::V;
-    const int64_t off = a.elem0 * G::NSP * G::V;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        // FP32: store the perturbation about the reference state
-        const double r = sizeof(real) == 4 ? a.uref64[i % G::V] : 0.0;
-        a.U[off + i] = (real)(a.stage64[i] - r);
+    constexpr int V = G::V;
+    const int64_t total = a.n_elem * G::NSP * V;
+    const int64_t off = a.elem0 * G::NSP * V;
+    // FP32: store the perturbation about the reference state
+    auto ref = [&](int64_t i) { return sizeof(real) == 4 ? a.uref64[i % V] : 0.0; };
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    if (((total | off) & 1) == 0 && (reinterpret_cast<uintptr_t>(a.stage64) & 15) == 0) {
+        const double2 *src = reinterpret_cast<const double2 *>(a.stage64);
+        const int64_t np = total / 2;
+        for (int64_t k0 = t0; k0 < np; k0 += nt * kConvPairs) {
+            double2 x[kConvPairs];
+#pragma unroll
+            for (int c = 0; c < kConvPairs; ++c)
+                if (k0 + c * nt < np) x[c] = src[k0 + c * nt];
+#pragma unroll
+            for (int c = 0; c < kConvPairs; ++c) {
+                const int64_t k = k0 + c * nt;
+                if (k >= np) break;
+                a.U[off + 2 * k] = (real)(x[c].x - ref(2 * k));
+                a.U[off + 2 * k + 1] = (real)(x[c].y - ref(2 * k + 1));
+            }
+        }
+        return;
     }
+    for (int64_t i = t0; i < total; i += nt) a.U[off + i] = (real)(a.stage64[i] - ref(i));
 }
 
 template <int D, int N, typename real>
 __global__ void k_to_f64(const KArgs<real> a) {
     using G = Geo<D, N>;
-    const int64_t total = a.n_elem * G::NSP * G::V;
-    const int64_t off = a.elem0 * G::NSP * G::V;
+    constexpr int V = G::V;
+    const int64_t total = a.n_elem * G::NSP * V;
+    const int64_t off = a.elem0 * G::NSP * V;
     const real *src = a.integral_src ? a.RES : a.U;
     const bool shift = sizeof(real) == 4 && !a.integral_src;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x)
-        a.stage64_out[i] = (double)src[off + i] + (shift ? a.uref64[i % G::V] : 0.0);
+    auto ref = [&](int64_t i) { return shift ? a.uref64[i % V] : 0.0; };
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    if (((total | off) & 1) == 0 && (reinterpret_cast<uintptr_t>(a.stage64_out) & 15) == 0) {
+        double2 *dst = reinterpret_cast<double2 *>(a.stage64_out);
+        const int64_t np = total / 2;
+        for (int64_t k0 = t0; k0 < np; k0 += nt * kConvPairs) {
+            real x0[kConvPairs], x1[kConvPairs];
+#pragma unroll
+            for (int c = 0; c < kConvPairs; ++c) {
+                const int64_t k = k0 + c * nt;
+                if (k < np) {
+                    x0[c] = src[off + 2 * k];
+                    x1[c] = src[off + 2 * k + 1];
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kConvPairs; ++c) {
+                const int64_t k = k0 + c * nt;
+                if (k >= np) break;
+                dst[k] = make_double2((double)x0[c] + ref(2 * k), (double)x1[c] + ref(2 * k + 1));
+            }
+        }
+        return;
+    }
+    for (int64_t i = t0; i < total; i += nt) a.stage64_out[i] = (double)src[off + i] + ref(i);
 }
 
 // --------------------------------------------------------------------------
@@ -2605,32 +2603,114 @@ __global__ void k_to_f64(const KArgs<real> a) {
 // back into U where the last attempt was rejected, so that U is every
 // instance's current solution between calls.
 // --------------------------------------------------------------------------
+__device__ __forceinline__ void bs_commit4(float4 *U, float4 *R1, const float4 *R2, float4 *R3, int64_t q,
+                                           int acc, float c, int mode) {
+    if (mode == 1) {   // after the last attempt: u_n back where it was rejected
+        if (acc == 0) U[q] = R3[q];
+        return;
+    }
+    float4 u, k;
+    if (acc == 1) {
+        u = U[q];
+        k = R2[q];
+        R3[q] = u;
+        R1[q] = k;
+    } else {
+        u = R3[q];
+        k = R1[q];
+    }
+    U[q] = make_float4(u.x + c * k.x, u.y + c * k.y, u.z + c * k.z, u.w + c * k.w);
+}
+
 template <int D, int N, typename real>
 __global__ void k_bs_commit(const KArgs<real> a) {
     using G = Geo<D, N>;
     constexpr int64_t PER = (int64_t)G::NSP * G::V;
     const int64_t total = a.n_elem * PER;
     const int64_t off = a.elem0 * PER;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t q = off + i;
-        const int inst = a.EINST[q / PER];
-        if (a.mode == 1) {
-            if (a.ACC[inst] == 0) a.U[q] = a.R3[q];
-            continue;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, nt = (int64_t)gridDim.x * blockDim.x;
+    if constexpr (sizeof(real) == 4 && PER % 4 == 0) {
+        // FP32 elements of whole float4s: one instance look-up per four values
+        float4 *U = reinterpret_cast<float4 *>(a.U), *R1 = reinterpret_cast<float4 *>(a.R1);
+        float4 *R2 = reinterpret_cast<float4 *>(a.R2), *R3 = reinterpret_cast<float4 *>(a.R3);
+        for (int64_t k = t0; k < total / 4; k += nt) {
+            const int64_t q = off / 4 + k;
+            const int inst = a.EINST[(4 * q) / PER];
+            const float c = (float)(0.5 * a.ADAPT[(int64_t)inst * kAdStride + kAdHuse]);
+            bs_commit4(U, R1, R2, R3, q, a.ACC[inst], c, a.mode);
         }
-        const real c = (real)(0.5 * a.ADAPT[(int64_t)inst * kAdStride + kAdHuse]);
-        real u, k;
-        if (a.ACC[inst] == 1) {
-            u = a.U[q];
-            k = a.R2[q];
-            a.R3[q] = u;
-            a.R1[q] = k;
-        } else {
-            u = a.R3[q];
-            k = a.R1[q];
+    } else {
+        for (int64_t i = t0; i < total; i += nt) {
+            const int64_t q = off + i;
+            const int inst = a.EINST[q / PER];
+            const real c = (real)(0.5 * a.ADAPT[(int64_t)inst * kAdStride + kAdHuse]);
+            const int acc = a.ACC[inst];
+            if (a.mode == 1) {
+                if (acc == 0) a.U[q] = a.R3[q];
+                continue;
+            }
+            real u, k;
+            if (acc == 1) {
+                u = a.U[q];
+                k = a.R2[q];
+                a.R3[q] = u;
+                a.R1[q] = k;
+            } else {
+                u = a.R3[q];
+                k = a.R1[q];
+            }
+            a.U[q] = u + c * k;
         }
-        a.U[q] = u + c * k;
+    }
+}
+
+// K_BS_ERROR: after the last evaluation of an attempt, every element's sum
+// of the squared scaled errors (e / (atol_v + rtol max(|u_n|, |u_n+1|)))^2,
+// e = h (RES - R2/8), over its points and variables: each point's sum in the
+// state's precision, then the points' sums in FP64 in point order.  One
+// thread per point, kErrThreads / NSP elements per block.
+constexpr int kErrThreads = 256;
+
+template <int D, int N, typename real>
+__global__ void __launch_bounds__(kErrThreads) k_bs_error(const KArgs<real> a) {
+    using G = Geo<D, N>;
+    constexpr int NSP = G::NSP, V = G::V, NEB = kErrThreads / NSP;
+    constexpr bool PERT = sizeof(real) == 4;
+    __shared__ real part[NEB * NSP];
+    const int j = threadIdx.x / NSP, s = threadIdx.x % NSP;
+    const int64_t e = a.elem0 + (int64_t)blockIdx.x * NEB + j;
+    const bool live = j < NEB && e < a.elem0 + a.n_elem;
+    if (live) {
+        const int64_t g = (e * NSP + s) * V;
+        const real h = (real)a.ADAPT[(int64_t)a.EINST[e] * kAdStride + kAdHuse];
+        real cm[V], k4[V], q[V], u[V];
+        ldg_v<V>(a.RES + g, cm);
+        ldg_v<V>(a.R2 + g, k4);
+        ldg_v<V>(a.R3 + g, q);
+        ldg_v<V>(a.U + g, u);
+        real es = 0;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+            real uq = q[v], uf = u[v];
+            if constexpr (PERT) {   // full conserved values
+                const real rv = v == 0 ? a.ref.rho : (v == V - 1 ? a.ref.E : a.ref.m[v - 1]);
+                uq += rv;
+                uf += rv;
+            }
+            const real ev = h * (cm[v] - real(0.125) * k4[v]);
+            const real r = ev / (a.bs_atol[v] + a.bs_rtol * fmax(fabs(uq), fabs(uf)));
+            es += r * r;
+        }
+        part[j * NSP + s] = es;
+    }
+    __syncthreads();
+    if (threadIdx.x < NEB) {
+        const int64_t ee = a.elem0 + (int64_t)blockIdx.x * NEB + threadIdx.x;
+        if (ee < a.elem0 + a.n_elem) {
+            double sum = 0.0;
+            for (int qq = 0; qq < NSP; ++qq) sum += (double)part[threadIdx.x * NSP + qq];
+            a.ERRE[ee] = sum;
+        }
     }
 }
 
@@ -2944,6 +3024,10 @@ cudaError_t launch_n(int kind, bool visc, const KArgs<real> &a, int grid_hint, c
     } else if (kind == K_BS_COMMIT) {
         if (a.n_elem <= 0) return cudaSuccess;
         k_bs_commit<D, N, real><<<grid_hint, 256, 0, st>>>(a);
+    } else if (kind == K_BS_ERROR) {
+        if (a.n_elem <= 0) return cudaSuccess;
+        constexpr int NEB = kErrThreads / Geo<D, N>::NSP;
+        k_bs_error<D, N, real><<<(unsigned)((a.n_elem + NEB - 1) / NEB), kErrThreads, 0, st>>>(a);
     } else if (kind == K_BS_CONTROL) {
         if (grid_hint <= 0) return cudaSuccess;
         k_bs_control<D, N, real><<<grid_hint, kReduceThreads, 0, st>>>(a);

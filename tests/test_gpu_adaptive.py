@@ -255,3 +255,47 @@ def test_advance_to_a_common_time_then_average():
         assert rec["accepted"] == ad.n_accepted and rec["rejected"] == ad.n_rejected
         assert FC.rel_l2(sol.get_state(i), ad.u) < 1e-12
         assert np.allclose(sol.probe_history(ids[i]), hist[i], rtol=1e-11, atol=0.0)
+
+
+def _attempts_match(sol, ad, tag):
+    n = 0
+    while ad.t < ad.t_end:
+        sol.rk_step(1)
+        ad.attempt()
+        n += 1
+        _check_attempt(sol.step_control(0), ad, f"{tag} attempt {n}")
+        assert n < 300
+    errs = np.array([r["err"] for r in ad.records])
+    err = FC.rel_l2(sol.get_state(0), ad.u)
+    print(f"{tag}: {n} attempts, {ad.n_rejected} rejected, min |err - 1| {np.min(np.abs(errs - 1)):.3f}, "
+          f"state at t_end vs oracle {err:.3e}")
+    assert ad.n_rejected >= 1 and np.min(np.abs(errs - 1)) > 1e-3 and err < 1e-12
+
+
+def test_fp64_3d_attempts_match_the_oracle():
+    """Taylor-Green vortex on 4^3 hexes, p = 3 (viscous, five variables)."""
+    case = FC.tgv_case(n=4, p=3)
+    h0, t_end, rtol, atol = 0.02, 0.2, 1e-6, [1e-7] * 5
+    sol = _solver(case, _cfg(case, "fp64", h0, t_end, 0.0, rtol, atol))
+    disc, u0, ad = _oracle(case, 0, h0, t_end, 0.0, rtol, atol)
+    sol.set_state(0, u0)
+    _attempts_match(sol, ad, "tgv 4^3")
+
+
+def test_fp64_variable_degree_attempts_match_the_oracle():
+    """Degrees 1-4 per element with mortar faces (BR2): the attempt's face
+    data and the skipped mortar passes of the stage-1 and last evaluations."""
+    from paper_2312_14167_gb300 import fr
+    from oracle.fr_var import VarFRDiscretisation
+    from tests.test_gpu_varp import _box, _phys, _state, MU, GAMMA, PR, MACH
+    m, ep = _box(2)
+    disc = VarFRDiscretisation(m, ep, _phys(2, True, "rusanov", MU), viscous_scheme="br2")
+    h0, t_end, rtol, atol = 2e-3, 1e-2, 1e-6, [1e-7] * 4
+    cfg = fr.make_config(2, gamma=GAMMA, prandtl=PR, mu=MU, rho_inf=1.0, v_inf=(1.0, 0.0),
+                         p_inf=1.0 / (GAMMA * MACH ** 2), dt=h0, viscous=True, rk=fr.FR_BS32,
+                         precision=fr.FR_FP64, t_end=t_end, rtol=rtol, atol=atol)
+    sol = fr.Solver([fr.Mesh(m, ep)], cfg)
+    u0 = _state(sol.meshes[0].sol_coords(), 2, mesh=m)
+    sol.set_state(0, u0)
+    ad = T.AdaptiveBS32(disc.residual, u0, h0, t_end, rtol, np.asarray(atol))
+    _attempts_match(sol, ad, "box2d degrees 1-4")

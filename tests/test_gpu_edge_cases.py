@@ -222,3 +222,35 @@ def test_non_finite_instance_is_flagged_inside_the_time_loop():
     assert sol.instance_status()[1] == -1
     sol.rk_step(2)
     assert sol.instance_status()[1] == -1
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("degrees", [(3, 3, 3), (2, 3, 2)])
+def test_batch_transfers_equal_per_instance_transfers(precision, degrees):
+    """fr_set_states / fr_get_states move the whole batch through one FP64
+    staging copy each way when no instance spans several degree groups (one
+    group, or uniform instances of different degrees, whose conversions run
+    over runs of consecutive instances): bitwise the per-instance calls, and
+    the residuals and steps that follow are bitwise the same too."""
+    from paper_2312_14167_gb300 import fr
+    ms = M.airfoil_batch(3, seed=11, e_lo=200, e_hi=320, p_geo=3)
+    case = FC.airfoil_case(n_inst=1, e_lo=200, e_hi=201)
+    cfg = FC.lib_config(case, precision)
+
+    def solver():
+        return fr.Solver([fr.Mesh(m, p) for m, p in zip(ms, degrees)], cfg)
+    a, b = solver(), solver()
+    us = [S.wall_damped(a.meshes[i].sol_coords(), ms[i].info["wall_points"], 0.05,
+                        S.smooth_perturbed(a.meshes[i].sol_coords(), 2, 0.2, amp=0.05, seed=i))
+          for i in range(3)]
+    for i, u in enumerate(us):
+        a.set_state(i, u)
+    b.set_states(np.concatenate([u.reshape(-1) for u in us]))
+    flat = b.get_states()
+    assert np.array_equal(flat, np.concatenate([a.get_state(i).reshape(-1) for i in range(3)]))
+    for i in range(3):
+        assert np.array_equal(a.get_state(i), b.get_state(i))
+        assert np.array_equal(a.residual(i), b.residual(i))
+    a.rk_step(2)
+    b.rk_step(2)
+    assert np.array_equal(b.get_states(), np.concatenate([a.get_state(i).reshape(-1) for i in range(3)]))
