@@ -145,6 +145,10 @@ NCU_TRAFFIC = {
     # launches (profiles/k_flux_airfoil8_full.md), scaled to a launch by the element count
     "9ce1259f965df7a6229c93f4b0d7905bb8e40b0ec59992f643dadead8b30bb73":
         {"flux_bytes_per_elem": ((316.185344e6 + 378.621184e6) / 2 + (151.570944e6 + 153.314560e6) / 2) / 243854},
+    # one-pass dram__bytes capture of k_flux<2,4,float,1,0,0> on the same case
+    # (profiles/traffic_airfoil8_split_stage.md): 316.2 MB read + 149.0 MB written
+    "718c2aecf7009444c359541293d3c384c3fcf704339a068bec575a1ab20458a6":
+        {"flux_bytes_per_elem": (316.209920e6 + 148.992000e6) / 243854},
 }
 
 
@@ -156,6 +160,7 @@ NCU_FP64_FLOPS = {
     # k_grad<2,4,double> 1.9361e8 + k_flux<2,4,double> 3.6875e8 flops per stage over candidate 0
     # (33,800 quads x 16 points), split schedule; profiles/fp64_stage_airfoil8_flops.md
     "9ce1259f965df7a6229c93f4b0d7905bb8e40b0ec59992f643dadead8b30bb73": (1.9361e8 + 3.6875e8) / (33800 * 16),
+    "718c2aecf7009444c359541293d3c384c3fcf704339a068bec575a1ab20458a6": (1.93613e8 + 3.68746e8) / (33800 * 16),
 }
 
 
