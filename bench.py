@@ -619,6 +619,22 @@ def run_gpu(args):
     del sol
     torch.cuda.empty_cache()
 
+    # adaptive steps (FR_BS32) on the same poll against the fixed-step
+    # LSRK45 line above: simulated time per device second (one GPU)
+    adaptive = None
+    if world == 1 and not args.no_adaptive:
+        rtol = 1e-6
+        cfg_bs = fr.make_config(W.dim, precision=fr.FR_FP32,
+                                **{**common, "rk": fr.FR_BS32, "rtol": rtol,
+                                   "atol": adaptive_tolerances(rtol, ph), "check_every": 50})
+        n_att = max(20, min(args.steps, 100))
+        adaptive = adaptive_run(fr, fms, states, dt, cfg_bs, n_att, 20)
+        adaptive.pop("kernel_ms_per_step", None)
+        fixed = len(fms) * dt / (ms / args.steps / 1e3)
+        adaptive.update({"rtol": rtol, "atol": "rtol x each variable's free-stream scale",
+                         "attempts": n_att, "lsrk45_simulated_time_per_device_second": fixed,
+                         "speed_vs_fixed_lsrk45": adaptive["simulated_time_per_device_second"] / fixed})
+
     # the plain single-instance FP64 path, candidates one after another
     n64 = 10
     fp64_sched = []
@@ -673,6 +689,7 @@ def run_gpu(args):
                         "how": "per step: fr_set_states (every candidate, from one pinned FP64 "
                                "host array), fr_rk_step(1), fr_get_states into one pinned FP64 "
                                "host array"},
+                "adaptive_steps": adaptive,
                 "gpu_launches": int(launches),
                 "clocks": clocks,
                 "fp64_single_instance": {"value": fp64_val, "unit": UNIT,
@@ -793,13 +810,73 @@ def run_observe(args):
     return 0
 
 
+def adaptive_run(fr, fms, states, dt, cfg, n_timed, warmup, schedule=""):
+    """One solver over the poll: `warmup` steps (attempts, for FR_BS32), then
+    `n_timed` timed ones (CUDA events on the solver stream): device time,
+    simulated time advanced per device second (summed over the candidates)
+    and, for adaptive steps, the accepted / rejected attempts and the steps
+    taken against the fixed CFL step `dt`."""
+    import torch
+    n_inst = len(fms)
+    adaptive = cfg.rk == fr.FR_BS32
+    sol = fr.Solver(fms, cfg)
+    if schedule:   # fixed schedule (profiling): no measurement
+        _, key = sol.schedule()
+        cache = os.path.join(tempfile.gettempdir(), f"fr_tune_adaptive_{os.getpid()}.json")
+        with open(cache, "w") as f:
+            json.dump({key: schedule}, f)
+        sched = sol.tune(cache, mode=2)
+        os.unlink(cache)
+    else:
+        sched = sol.tune(None, mode=1)
+    for i, u in enumerate(states):
+        sol.set_state(i, u)
+    sol.rk_step(warmup)
+    sol.synchronize()
+    rec0 = [sol.step_control(i) for i in range(n_inst)] if adaptive else None
+    st = sol.stream
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    sol.rk_step(n_timed)
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    # first instance with a non-finite state (-1: none; scanned every check_every steps)
+    res = {"ms": ms, "ms_per_step": ms / n_timed, "schedule": sched.split(";source")[0],
+           "first_nonfinite_instance": sol.instance_status()[1]}
+    if adaptive:
+        rec = [sol.step_control(i) for i in range(n_inst)]
+        adv = [r["t"] - a["t"] for r, a in zip(rec, rec0)]
+        acc = [r["accepted"] - a["accepted"] for r, a in zip(rec, rec0)]
+        rej = [r["rejected"] - a["rejected"] for r, a in zip(rec, rec0)]
+        res.update({"accepted": int(sum(acc)), "rejected": int(sum(rej)),
+                    "mean_step_over_cfl_dt": float(np.sum(adv) / max(np.sum(acc), 1) / dt),
+                    "min_max_h_next_over_cfl_dt": [min(r["h_next"] for r in rec) / dt,
+                                                   max(r["h_next"] for r in rec) / dt]})
+    else:
+        adv = [n_timed * dt] * n_inst
+    res["simulated_time_per_device_second"] = float(np.sum(adv) / (ms / 1e3))
+    kms, kcnt = sol.profile_steps(3)
+    res["kernel_ms_per_step"] = {k: float(kms[j] * kcnt[j] / 3)
+                                 for j, k in enumerate(["flux", "grad", "probe", "force", "other"])}
+    del sol
+    torch.cuda.empty_cache()
+    return res
+
+
+def adaptive_tolerances(rtol, ph):
+    """atol at rtol times each conserved variable's free-stream scale."""
+    return [rtol * 1.0] + [rtol * 1.0] * W.dim + [rtol * ph["p_inf"] / (GAMMA - 1.0)]
+
+
 def run_adaptive(args):
     """Adaptive steps (FR_BS32) against fixed LSRK45 steps on one workload,
     FP32 batched: simulated time advanced per second of device time (summed
     over the candidates), the steps the controller takes against the fixed
     CFL step, rejections, and the cost of one attempt against one LSRK45
     step.  Each solver runs `--warmup` steps/attempts, then `--adaptive` timed
-    ones (CUDA events on the solver stream)."""
+    ones."""
     import torch
     torch.cuda.set_device(0)
     from paper_2312_14167_gb300 import fr
@@ -810,69 +887,16 @@ def run_adaptive(args):
                   inflow_delta=W.inflow_delta, inflow_ywall=0.0, dt=dt, viscous=True, precision=fr.FR_FP32,
                   check_every=50)
     fms = [fr.Mesh(m, W.p if W.degrees is None else W.elem_degrees(m)) for m in meshes]
-    n_inst = len(fms)
     states = [initial_state(m.sol_coords(), i, meshes[i]) for i, m in enumerate(fms)]
     out = {"workload": workload_text(), "cfl_dt": dt, "timed": args.adaptive, "warmup": args.warmup}
-
-    def timed(sol, n):
-        st = sol.stream
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(st)
-        sol.rk_step(n)
-        e1.record(st)
-        e1.synchronize()
-        return e0.elapsed_time(e1)
-
-    runs = [("lsrk45", dict(rk=fr.FR_LSRK45), None)]
+    runs = [("lsrk45", dict(rk=fr.FR_LSRK45))]
     for rtol in args.adaptive_rtol:
-        # absolute tolerances at rtol times each variable's free-stream scale
-        at = [rtol * 1.0] + [rtol * 1.0] * W.dim + [rtol * ph["p_inf"] / (GAMMA - 1.0)]
-        runs.append((f"bs32_rtol{rtol:g}", dict(rk=fr.FR_BS32, rtol=rtol, atol=at), rtol))
-    for name, kw, rtol in runs:
-        sol = fr.Solver(fms, fr.make_config(W.dim, **{**common, **kw}))
-        if args.schedule:   # fixed schedule (profiling): no measurement
-            _, key = sol.schedule()
-            cache = os.path.join(tempfile.gettempdir(), f"fr_tune_adaptive_{os.getpid()}.json")
-            with open(cache, "w") as f:
-                json.dump({key: args.schedule}, f)
-            sched = sol.tune(cache, mode=2)
-            os.unlink(cache)
-        else:
-            sched = sol.tune(None, mode=1)
-        for i, u in enumerate(states):
-            sol.set_state(i, u)
-        sol.rk_step(args.warmup)
-        sol.synchronize()
-        if rtol is None:
-            t0 = [args.warmup * dt] * n_inst
-        else:
-            rec0 = [sol.step_control(i) for i in range(n_inst)]
-            t0 = [r["t"] for r in rec0]
-        ms = timed(sol, args.adaptive)
-        # first instance with a non-finite state (-1: none), scanned every 50 steps/attempts
-        res = {"ms": ms, "ms_per_step": ms / args.adaptive, "schedule": sched.split(";source")[0],
-               "first_nonfinite_instance": sol.instance_status()[1]}
-        if rtol is None:
-            adv = [args.adaptive * dt] * n_inst
-        else:
-            rec = [sol.step_control(i) for i in range(n_inst)]
-            adv = [r["t"] - a for r, a in zip(rec, t0)]
-            acc = [r["accepted"] - a["accepted"] for r, a in zip(rec, rec0)]
-            rej = [r["rejected"] - a["rejected"] for r, a in zip(rec, rec0)]
-            res.update({"accepted": int(sum(acc)), "rejected": int(sum(rej)),
-                        "mean_step_over_cfl_dt": float(np.sum(adv) / max(np.sum(acc), 1) / dt),
-                        "min_max_h_next_over_cfl_dt": [min(r["h_next"] for r in rec) / dt,
-                                                       max(r["h_next"] for r in rec) / dt]})
-        res["simulated_time_per_device_second"] = float(np.sum(adv) / (ms / 1e3))
-        kms, kcnt = sol.profile_steps(3)
-        res["kernel_ms_per_step"] = {k: float(kms[j] * kcnt[j] / 3)
-                                     for j, k in enumerate(["flux", "grad", "probe", "force", "other"])}
-        out[name] = res
-        del sol
-        torch.cuda.empty_cache()
+        runs.append((f"bs32_rtol{rtol:g}", dict(rk=fr.FR_BS32, rtol=rtol, atol=adaptive_tolerances(rtol, ph))))
+    for name, kw in runs:
+        cfg = fr.make_config(W.dim, **{**common, **kw})
+        out[name] = adaptive_run(fr, fms, states, dt, cfg, args.adaptive, args.warmup, args.schedule)
     base = out["lsrk45"]["simulated_time_per_device_second"]
-    for name, _, rtol in runs[1:]:
+    for name, _ in runs[1:]:
         out[name]["speed_vs_lsrk45"] = out[name]["simulated_time_per_device_second"] / base
     print(json.dumps({"adaptive": out}), flush=True)
     return 0
@@ -899,6 +923,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adaptive", action="store_true",
+                    help="skip the adaptive-steps (FR_BS32) comparison of the default run")
     ap.add_argument("--workload", default="airfoil", choices=sorted(WORKLOADS))
     ap.add_argument("--candidates", type=int, default=0)
     ap.add_argument("--observe", type=int, default=0,
