@@ -197,3 +197,37 @@ def test_adaptive_bs32_matches_scipy_rk23_on_the_fr_semidiscretisation():
     acc_t = np.cumsum([r["h"] for r in ad.records if r["accepted"]])
     assert np.max(np.abs(acc_t - ref.t[1:])) < 1e-12
     assert np.max(np.abs(ad.u.ravel() - ref.y[:, -1])) < 1e-11
+
+
+def test_adaptive_run_at_the_stability_limit_is_sensitive_to_rounding():
+    """Why the GPU compares the Taylor-Green 4^3 adaptive run over its first
+    16 attempts only: the oracle run twice, once with its residual perturbed
+    by 1e-14 relative (rounding-sized), agrees to 1e-7 in the error norm
+    through attempt 16, but once the steps ride the stability limit the
+    difference grows by orders of magnitude (above 1e-4 by attempt 30).  The
+    periodic 2-D case, whose steps stay accuracy-limited, keeps it below
+    1e-8 to its end."""
+    from tests import fr_cases as FC
+
+    def drift(case, h0, t_end, rtol, atol, n):
+        disc = FC.oracle_disc(case)
+        u0 = FC.initial_state(case, disc.sol_coords())
+        rng = np.random.default_rng(1)
+
+        def noisy(u):
+            r = disc.residual(u)
+            return r * (1.0 + 1e-14 * rng.standard_normal(r.shape))
+        a = timestep.AdaptiveBS32(disc.residual, u0, h0, t_end, rtol, np.asarray(atol))
+        b = timestep.AdaptiveBS32(noisy, u0, h0, t_end, rtol, np.asarray(atol))
+        out = []
+        while len(out) < n and a.t < t_end and b.t < t_end:
+            a.attempt()
+            b.attempt()
+            ea, eb = a.records[-1]["err"], b.records[-1]["err"]
+            out.append(abs(ea - eb) / ea)
+        return np.array(out)
+
+    tgv = drift(FC.tgv_case(n=4, p=3), 0.05, 0.3, 1e-4, [1e-5] * 5, 30)
+    assert tgv.size == 30 and tgv[:16].max() < 1e-7 and tgv[24:].max() > 1e-4
+    pns = drift(FC.periodic_ns_case(n=4, p=3), 0.04, 0.12, 1e-6, [1e-7] * 4, 100)
+    assert pns.max() < 1e-8
