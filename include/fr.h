@@ -214,11 +214,15 @@ fr_status fr_set_state(fr_solver *solver, int inst, const double *u);
 fr_status fr_get_state(fr_solver *solver, int inst, double *u);
 /* The states of all instances at once: u holds instance 0's state, then
  * instance 1's, ... (each in the layout of fr_set_state), sum over instances
- * of n_sol_points * V doubles.  The copies and conversions of all instances
- * are queued back to back and the stream is synchronised once, which is what
- * a poll evaluator that moves every candidate each step wants; with pinned
- * host memory the copies run at the host link's speed.  Same results as one
- * fr_set_state / fr_get_state per instance.  Errors: FR_ERR_INVALID_ARG
+ * of n_sol_points * V doubles.  When every instance lies in one degree group
+ * (the usual case) the whole batch moves in one copy each way through the
+ * workspace's FP64 staging area, converted by one launch per run of
+ * consecutive instances; an instance with elements of several degrees goes
+ * through a host reorder, one instance after another.  The stream is
+ * synchronised once, which is what a poll evaluator that moves every
+ * candidate each step wants; with pinned host memory the copies run at the
+ * host link's speed.  Same results as one fr_set_state / fr_get_state per
+ * instance.  Errors: FR_ERR_INVALID_ARG
  * (null pointer), FR_ERR_CUDA. */
 fr_status fr_set_states(fr_solver *solver, const double *u);
 fr_status fr_get_states(fr_solver *solver, double *u);
@@ -231,7 +235,9 @@ fr_status fr_residual(fr_solver *solver, int inst, double *r);
 /* Advance every instance by n_steps fixed steps of cfg->dt with cfg->rk,
  * sampling every probe (and the wall force) after each completed step.  Work
  * is replayed from a CUDA graph captured on first use.  Asynchronous.
- * FR_BS32: n_steps attempts of every instance (see FR_BS32). */
+ * FR_BS32: n_steps attempts of every instance (see FR_BS32); when the call's
+ * work is done, every instance's device state is its current (accepted)
+ * solution, so fr_get_state, fr_residual and fr_integral see that. */
 fr_status fr_rk_step(fr_solver *solver, int n_steps);
 
 /* FR_BS32: the step-control record of instance ``inst`` into out (8 doubles):
