@@ -178,6 +178,10 @@ struct fr_solver {
     int32_t *ACC = nullptr;
     frk::AdaptRange *ARANGE = nullptr;
     std::vector<double> adapt_init;   // host: the initial record of every instance
+    // batch transfers: an auxiliary stream for the host-link copies (so that
+    // one chunk's copy overlaps the previous chunk's conversion) and events
+    cudaStream_t xfer = nullptr;
+    cudaEvent_t xev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
     std::string schedule_source = "default";
     double schedule_ms = 0.0;
     std::vector<std::unique_ptr<fr_mesh>> host_meshes;   // for probe location
@@ -1363,6 +1367,12 @@ extern "C" void fr_solver_destroy(fr_solver *s) {
     if (s->stream) cudaStreamSynchronize(s->stream);
     else cudaDeviceSynchronize();
     drop_graphs(s);
+    if (s->xfer) {
+        cudaStreamSynchronize(s->xfer);
+        cudaStreamDestroy(s->xfer);
+    }
+    for (cudaEvent_t e : s->xev)
+        if (e) cudaEventDestroy(e);
     delete s;
 }
 
@@ -1480,28 +1490,32 @@ bool batch_stageable(const fr_solver *s) {
     return true;
 }
 
+// Runs of consecutive instances in [i0, i1) that are consecutive both in the
+// staging buffer and in their degree group: fn(group, first element, elements,
+// staging offset in doubles).
 template <typename F>
-fr_status for_instance_runs(const fr_solver *s, F &&fn) {
+fr_status for_instance_runs(const fr_solver *s, int i0, int i1, F &&fn) {
     const int V = s->V;
     int g_run = -1;
     int64_t e0 = 0, ne = 0, so = 0, off = 0;
-    for (int i = 0; i <= s->n_inst; ++i) {
+    for (int i = 0; i < i0; ++i) off += s->inst_nsp[i] * V;
+    for (int i = i0; i <= i1; ++i) {
         int g = -1;
-        if (i < s->n_inst)
+        if (i < i1)
             for (size_t h = 0; h < s->grp.size(); ++h)
                 if (s->grp[h].ne[i] > 0) g = (int)h;
-        const bool extend = i < s->n_inst && g == g_run && s->grp[g].off[i] == e0 + ne &&
+        const bool extend = i < i1 && g == g_run && s->grp[g].off[i] == e0 + ne &&
                             off == so + ne * s->grp[g].nsp * V;
         if (!extend) {
             if (g_run >= 0 && ne > 0) FR_TRY(fn(g_run, e0, ne, so));
-            if (i < s->n_inst) {
+            if (i < i1) {
                 g_run = g;
                 e0 = g >= 0 ? s->grp[g].off[i] : 0;
                 ne = 0;
                 so = off;
             }
         }
-        if (i < s->n_inst) {
+        if (i < i1) {
             if (g >= 0) ne += s->grp[g].ne[i];
             off += s->inst_nsp[i] * V;
         }
@@ -1509,43 +1523,127 @@ fr_status for_instance_runs(const fr_solver *s, F &&fn) {
     return FR_OK;
 }
 
-fr_status enqueue_upload_batch(fr_solver *s, const double *u) {
-    size_t total = 0;
-    for (int i = 0; i < s->n_inst; ++i) total += (size_t)s->inst_nsp[i] * s->V;
-    FR_CK(cudaMemsetAsync(s->FLAGS, 0, (size_t)s->n_inst * 4, s->stream));
-    if (s->adapt) FR_TRY(reset_step_control(s, -1));
-    FR_CK(cudaMemcpyAsync(s->stage64, u, total * 8, cudaMemcpyHostToDevice, s->stream));
-    FR_TRY(for_instance_runs(s, [&](int g, int64_t e0, int64_t ne, int64_t so) -> fr_status {
-        Launch c;
-        c.kind = frk::K_TO_REAL;
-        c.g = g;
-        c.elem0 = e0;
-        c.n_elem = ne;
-        c.stage_off = so;
-        c.grid = grid_for(ne * s->grp[g].nsp * s->V);
-        FR_CK(launch(s, c));
-        return FR_OK;
-    }));
-    int64_t cnt = 0;
-    return enqueue_faces(s, s->parity, cnt);
+// Instance chunks of a batch transfer (up to kXferChunks, balanced by size):
+// instance range [i0, i1), staging offset and length in doubles.
+constexpr int kXferChunks = 4;
+struct XferChunk { int i0, i1; int64_t off, n; };
+
+std::vector<XferChunk> xfer_chunks(const fr_solver *s) {
+    int64_t total = 0;
+    for (int i = 0; i < s->n_inst; ++i) total += s->inst_nsp[i] * s->V;
+    const int k = std::min(kXferChunks, s->n_inst);
+    std::vector<XferChunk> out;
+    int64_t off = 0;
+    int i = 0;
+    for (int c = 0; c < k && i < s->n_inst; ++c) {
+        const int64_t goal = total * (c + 1) / k;
+        XferChunk x{i, i, off, 0};
+        while (i < s->n_inst && (off < goal || x.i1 == x.i0)) {
+            const int64_t n = s->inst_nsp[i] * s->V;
+            off += n;
+            x.n += n;
+            x.i1 = ++i;
+        }
+        out.push_back(x);
+    }
+    if (i < s->n_inst) {   // (rounding) the rest joins the last chunk
+        for (; i < s->n_inst; ++i) out.back().n += s->inst_nsp[i] * s->V;
+        out.back().i1 = s->n_inst;
+    }
+    return out;
 }
 
+cudaError_t ensure_xfer(fr_solver *s) {
+    if (s->xfer) return cudaSuccess;
+    cudaError_t e = cudaStreamCreateWithFlags(&s->xfer, cudaStreamNonBlocking);
+    for (int c = 0; c <= kXferChunks && e == cudaSuccess; ++c)
+        e = cudaEventCreateWithFlags(&s->xev[c], cudaEventDisableTiming);
+    return e;
+}
+
+// face data of the instances [i0, i1) (each in one degree group)
+fr_status enqueue_faces_of(fr_solver *s, int i0, int i1) {
+    for (size_t g = 0; g < s->grp.size(); ++g) {
+        const Group &G = s->grp[g];
+        int first = -1, last = -1;
+        for (int i = i0; i < i1; ++i)
+            if (G.ne[i] > 0) {
+                if (first < 0) first = i;
+                last = i;
+            }
+        if (first < 0) continue;
+        Launch in;
+        in.kind = s->fused ? frk::K_INTERP_VISC : frk::K_INTERP;
+        in.g = (int)g;
+        in.elem0 = G.off[first];
+        in.n_elem = G.off[last] + G.ne[last] - G.off[first];
+        in.UFout = G.UF[s->parity];
+        in.FVout = fvbuf(G, s->parity);
+        FR_CK(launch(s, in));
+    }
+    return FR_OK;
+}
+
+// Upload of the whole batch: chunk c's host-link copy runs on the auxiliary
+// stream while the solver's stream converts chunk c - 1 and derives its face
+// data.  The copies start after the solver stream's earlier work (which may
+// still read the staging buffer).
+fr_status enqueue_upload_batch(fr_solver *s, const double *u) {
+    FR_CK(cudaMemsetAsync(s->FLAGS, 0, (size_t)s->n_inst * 4, s->stream));
+    if (s->adapt) FR_TRY(reset_step_control(s, -1));
+    FR_CK(ensure_xfer(s));
+    const std::vector<XferChunk> ch = xfer_chunks(s);
+    FR_CK(cudaEventRecord(s->xev[kXferChunks], s->stream));
+    FR_CK(cudaStreamWaitEvent(s->xfer, s->xev[kXferChunks], 0));
+    for (size_t c = 0; c < ch.size(); ++c) {
+        FR_CK(cudaMemcpyAsync(s->stage64 + ch[c].off, u + ch[c].off, (size_t)ch[c].n * 8,
+                              cudaMemcpyHostToDevice, s->xfer));
+        FR_CK(cudaEventRecord(s->xev[c], s->xfer));
+    }
+    for (size_t c = 0; c < ch.size(); ++c) {
+        FR_CK(cudaStreamWaitEvent(s->stream, s->xev[c], 0));
+        FR_TRY(for_instance_runs(s, ch[c].i0, ch[c].i1, [&](int g, int64_t e0, int64_t ne, int64_t so) -> fr_status {
+            Launch cv;
+            cv.kind = frk::K_TO_REAL;
+            cv.g = g;
+            cv.elem0 = e0;
+            cv.n_elem = ne;
+            cv.stage_off = so;
+            cv.grid = grid_for(ne * s->grp[g].nsp * s->V);
+            FR_CK(launch(s, cv));
+            return FR_OK;
+        }));
+        FR_TRY(enqueue_faces_of(s, ch[c].i0, ch[c].i1));
+    }
+    return FR_OK;
+}
+
+// Download of the whole batch: chunk c's conversion on the solver stream,
+// its host-link copy on the auxiliary stream (overlapping the conversion of
+// chunk c + 1); the solver stream then waits for the last copy.
 fr_status enqueue_download_batch(fr_solver *s, int src, double *u) {
-    size_t total = 0;
-    for (int i = 0; i < s->n_inst; ++i) total += (size_t)s->inst_nsp[i] * s->V;
-    FR_TRY(for_instance_runs(s, [&](int g, int64_t e0, int64_t ne, int64_t so) -> fr_status {
-        Launch c;
-        c.kind = frk::K_TO_F64;
-        c.g = g;
-        c.elem0 = e0;
-        c.n_elem = ne;
-        c.integral_src = src;
-        c.stage_off = so;
-        c.grid = grid_for(ne * s->grp[g].nsp * s->V);
-        FR_CK(launch(s, c));
-        return FR_OK;
-    }));
-    FR_CK(cudaMemcpyAsync(u, s->stage64, total * 8, cudaMemcpyDeviceToHost, s->stream));
+    FR_CK(ensure_xfer(s));
+    const std::vector<XferChunk> ch = xfer_chunks(s);
+    for (size_t c = 0; c < ch.size(); ++c) {
+        FR_TRY(for_instance_runs(s, ch[c].i0, ch[c].i1, [&](int g, int64_t e0, int64_t ne, int64_t so) -> fr_status {
+            Launch cv;
+            cv.kind = frk::K_TO_F64;
+            cv.g = g;
+            cv.elem0 = e0;
+            cv.n_elem = ne;
+            cv.integral_src = src;
+            cv.stage_off = so;
+            cv.grid = grid_for(ne * s->grp[g].nsp * s->V);
+            FR_CK(launch(s, cv));
+            return FR_OK;
+        }));
+        FR_CK(cudaEventRecord(s->xev[c], s->stream));
+        FR_CK(cudaStreamWaitEvent(s->xfer, s->xev[c], 0));
+        FR_CK(cudaMemcpyAsync(u + ch[c].off, s->stage64 + ch[c].off, (size_t)ch[c].n * 8,
+                              cudaMemcpyDeviceToHost, s->xfer));
+    }
+    FR_CK(cudaEventRecord(s->xev[kXferChunks], s->xfer));
+    FR_CK(cudaStreamWaitEvent(s->stream, s->xev[kXferChunks], 0));
     return FR_OK;
 }
 
