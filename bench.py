@@ -138,18 +138,36 @@ W = WORKLOADS["airfoil"]
 CANDIDATES = W.candidates     # --candidates: a smaller poll (profiling captures)
 
 
-# DRAM traffic of one launch of the dominant kernel from an ncu capture,
-# per element, valid only for the kernel source it was taken on.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the flux and gradient kernels from an ncu capture, per element, valid only
+# for the kernel source it was taken on.
 NCU_TRAFFIC = {
     # ncu --set full of k_flux<2,4,float,1,0> on the 8-airfoil case (243,854 quads), mean of two
     # launches (profiles/k_flux_airfoil8_full.md), scaled to a launch by the element count
     "9ce1259f965df7a6229c93f4b0d7905bb8e40b0ec59992f643dadead8b30bb73":
         {"flux_bytes_per_elem": ((316.185344e6 + 378.621184e6) / 2 + (151.570944e6 + 153.314560e6) / 2) / 243854},
-    # one-pass dram__bytes capture of k_flux<2,4,float,1,0,0> on the same case
-    # (profiles/traffic_airfoil8_split_stage.md): 316.2 MB read + 149.0 MB written
+    # one-pass dram__bytes capture of one split stage on the same case
+    # (profiles/traffic_airfoil8_split_stage.md): k_flux<2,4,float,1,0,0> 316.2 MB read
+    # + 149.0 MB written, k_grad<2,4,float,0> 249.94 MB + 43.18 MB
     "718c2aecf7009444c359541293d3c384c3fcf704339a068bec575a1ab20458a6":
-        {"flux_bytes_per_elem": (316.209920e6 + 148.992000e6) / 243854},
+        {"flux_bytes_per_elem": (316.209920e6 + 148.992000e6) / 243854,
+         "grad_bytes_per_elem": (249.94e6 + 43.18e6) / 243854},
 }
+
+
+def stage_traffic(schedule, n_elem):
+    """Measured DRAM bytes of one whole RK stage (gradient + flux kernel of
+    the split schedule) scaled to ``n_elem`` elements by the element count,
+    or None where no capture applies: another kernel source, workload,
+    stage schedule or contraction than the one captured."""
+    rec = NCU_TRAFFIC.get(kernel_source_hash())
+    if not rec or W.name != rec.get("workload", "airfoil"):
+        return None
+    opts = dict(kv.split("=", 1) for kv in schedule.split(";") if "=" in kv)
+    if opts.get("stage") != "split" or opts.get("contract") != "simt":
+        return None
+    fl, gr = rec.get("flux_bytes_per_elem"), rec.get("grad_bytes_per_elem")
+    return (fl + gr) * n_elem if fl and gr else None
 
 
 # FP64 floating-point operations per solution-point stage update of the plain
@@ -577,9 +595,17 @@ def run_gpu(args):
                     algorithmic_bytes(int(by_p[q]), 4, "flux", q) + algorithmic_bytes(int(by_p[q]), 4, "grad", q))
                    for q in range(0, 5) if by_p[q]) / max(sum(pts.values()), 1)
     achieved_stage = value / world * b_upd / 1e9
+    # measured bytes of one stage over the poll (uniform degree only: the
+    # capture is of one degree's kernels)
+    traffic_stage = stage_traffic(schedule, E) if len([q for q in range(0, 5) if by_p[q]]) == 1 else None
     roof = {"bound": "hbm", "kernel": "the whole RK stage (every kernel of the step)",
             "achieved": achieved_stage, "peak": peak, "unit": "GB/s", "frac": achieved_stage / peak,
-            "traffic": None,
+            "traffic": traffic_stage,
+            "traffic_bytes_per_update": traffic_stage / NSPT if traffic_stage else None,
+            "traffic_how": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one split stage "
+                            "(gradient + flux kernel) on 8 of the candidates, scaled to one stage of "
+                            "the poll by the element count; null when the kernel source, workload or "
+                            "schedule differs from the capture's"),
             "bytes_per_update": b_upd, "design_bytes_per_update": design_b,
             "how": "achieved = (sol-pt stage updates/s per GPU) x the method's minimum bytes per update "
                    "(4 V s + (1 + d^2) s_g + (2d/n)((2V + 2dV) s + d s_g), FP32); peak = measured copy "

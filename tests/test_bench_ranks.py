@@ -106,3 +106,26 @@ def test_bench_taylor_green_diagnostics_match_the_closed_forms():
             assert abs(bench.method_bytes_per_update(p) - want) < 1e-9
     finally:
         bench.W = saved
+
+
+def test_stage_traffic_applies_only_to_the_captured_schedule():
+    """The bench line's measured stage traffic: the split stage's DRAM bytes
+    per update sit a few per cent above the method's minimum of 188 B, and
+    no figure is given for a schedule, contraction or workload the capture
+    did not cover."""
+    import bench
+    saved = bench.W
+    try:
+        bench.W = bench.WORKLOADS["airfoil"]
+        rec = bench.NCU_TRAFFIC.get(bench.kernel_source_hash())
+        t = bench.stage_traffic("stage=split;regs=0;contract=simt;ms=4.5;source=measured", 1000)
+        if rec is None or "grad_bytes_per_elem" not in rec:
+            assert t is None
+        else:
+            assert 188.0 <= t / (1000 * 16) < 200.0
+        assert bench.stage_traffic("stage=fused;regs=0;contract=simt;ms=4.7", 1000) is None
+        assert bench.stage_traffic("stage=split;regs=0;contract=tc;ms=6.0", 1000) is None
+        bench.W = bench.WORKLOADS["tgv"]
+        assert bench.stage_traffic("stage=split;regs=2;contract=simt;ms=12.6", 1000) is None
+    finally:
+        bench.W = saved
