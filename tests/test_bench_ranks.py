@@ -72,6 +72,9 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    # the oracle ran on every host core (one process each), not the one-core fallback
+    import bench
+    assert d["cpu_baseline"]["cores"] == bench.host_cores(), d["cpu_baseline"]["sample"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
     assert "workload" in d["config"]
 
@@ -129,3 +132,24 @@ def test_stage_traffic_applies_only_to_the_captured_schedule():
         assert bench.stage_traffic("stage=split;regs=2;contract=simt;ms=12.6", 1000) is None
     finally:
         bench.W = saved
+
+
+def test_oracle_baseline_runs_on_every_core_or_falls_back_to_one(monkeypatch):
+    """The oracle's host baseline: one spawned process per host core, each on
+    its own element sample (the aggregate counts every process's updates over
+    the slowest one's time); if that run fails, one core, with the reason in
+    the sample text."""
+    import bench
+    from synth import meshes as M
+    mesh = M.periodic_box(2, (6, 6), (0, 0), (1, 1))
+    rec = bench.oracle_baseline(mesh, 8, 1, 2, 1e-4)
+    assert rec["cores"] == bench.host_cores() and rec["kind"] == "oracle"
+    assert rec["value"] > 0 and rec["per_core_value"] > 0 and rec["seconds"] > 0
+
+    def fail(*a, **k):
+        raise RuntimeError("no processes here")
+
+    monkeypatch.setattr(bench, "oracle_all_cores", fail)
+    rec = bench.oracle_baseline(mesh, 8, 1, 2, 1e-4)
+    assert rec["cores"] == 1 and rec["value"] > 0
+    assert "all-core run failed (no processes here)" in rec["sample"]
