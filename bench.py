@@ -28,6 +28,7 @@ import argparse
 import hashlib
 import json
 import os
+import queue
 import statistics
 import subprocess
 import sys
@@ -321,7 +322,7 @@ def _oracle_worker(name, mesh, n_sample, n_warm, n_steps, dt, seed, barrier, res
         results.put((seed, 0.0, 0.0, repr(ex)))
 
 
-def oracle_all_cores(mesh, n_sample, n_warm, n_steps, dt, limit_s=900.0):
+def oracle_all_cores(mesh, n_sample, n_warm, n_steps, dt, limit_s=300.0):
     """The oracle on every host core at once: one spawned process per core,
     each timing ``n_steps`` LSRK45 steps of its own sample of ``n_sample``
     elements, all starting together (a barrier).  Returns (updates/s over all
@@ -341,8 +342,17 @@ def oracle_all_cores(mesh, n_sample, n_warm, n_steps, dt, limit_s=900.0):
     out = []
     try:
         deadline = time.monotonic() + limit_s
-        for _ in range(n):
-            out.append(results.get(timeout=max(1.0, deadline - time.monotonic())))
+        while len(out) < n:
+            try:
+                out.append(results.get(timeout=1.0))
+            except queue.Empty:
+                # a process that died without reporting (or the time limit)
+                # ends the run at once instead of at the limit
+                dead = [p.exitcode for p in procs if p.exitcode not in (None, 0)]
+                if dead or time.monotonic() > deadline:
+                    barrier.abort()
+                    raise RuntimeError(f"oracle processes: exit codes {dead}" if dead else
+                                       f"oracle processes exceeded {limit_s:.0f} s")
     finally:
         for p in procs:
             p.join(timeout=10)

@@ -153,3 +153,21 @@ def test_oracle_baseline_runs_on_every_core_or_falls_back_to_one(monkeypatch):
     rec = bench.oracle_baseline(mesh, 8, 1, 2, 1e-4)
     assert rec["cores"] == 1 and rec["value"] > 0
     assert "all-core run failed (no processes here)" in rec["sample"]
+
+
+def test_oracle_all_cores_ends_at_once_when_a_process_dies(monkeypatch):
+    """A process that dies without reporting (here: a workload name it does
+    not know) ends the all-core run at once with an error, long before its
+    time limit."""
+    import copy
+    import time
+    import pytest
+    import bench
+    from synth import meshes as M
+    w = copy.copy(bench.W)
+    w.name = "no such workload"
+    monkeypatch.setattr(bench, "W", w)
+    t0 = time.monotonic()
+    with pytest.raises(RuntimeError, match="exit codes"):
+        bench.oracle_all_cores(M.periodic_box(2, (4, 4), (0, 0), (1, 1)), 4, 0, 1, 1e-4, limit_s=120.0)
+    assert time.monotonic() - t0 < 60.0
