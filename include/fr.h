@@ -46,7 +46,9 @@ typedef int fr_status;
 #define FR_ERR_UNSUPPORTED 3   /* p outside 0..4, mixed dimensions in a batch */
 #define FR_ERR_CUDA 4          /* a CUDA runtime call failed */
 #define FR_ERR_NONFINITE 5     /* NaN/Inf found in the state */
-#define FR_ERR_TIMEOUT 6       /* a bounded device wait gave up */
+#define FR_ERR_TIMEOUT 6       /* reserved for a bounded device wait that gave up;
+                                  no call returns it today (no kernel of this
+                                  library waits on another) */
 #define FR_ERR_WORKSPACE 7     /* workspace too small or misaligned */
 
 /* face tags (fr_mesh_create) */
