@@ -787,8 +787,15 @@ def run_gpu(args):
         del s64
     fp64_val = NSPT * STAGES * n64 / (t64 / 1e3)
     fp64_alu = None
+    alu_peaks = None
+    try:
+        # FMA-pipe peaks of this GPU (own microbenchmark, CUDA events)
+        alu_peaks = {"fp32_gflops": fr.alu_peak(fr.FR_FP32) / 1e9, "source": "fr_alu_peak"}
+    except Exception as ex:  # noqa: BLE001 (report, do not fail the bench)
+        alu_peaks = {"error": str(ex)}
     try:
         peak64 = fr.alu_peak(fr.FR_FP64)
+        alu_peaks["fp64_gflops"] = peak64 / 1e9
         fpu = NCU_FP64_FLOPS.get(kernel_source_hash())
         fp64_alu = {"bound": "alu", "peak_gflops": peak64 / 1e9, "peak_source": "fr_alu_peak (measured FMA chains)",
                     "flops_per_update": fpu,
@@ -822,6 +829,7 @@ def run_gpu(args):
                                "host array), fr_rk_step(1), fr_get_states into one pinned FP64 "
                                "host array"},
                 "adaptive_steps": adaptive,
+                "alu_peaks": alu_peaks,
                 "gpu_launches": int(launches),
                 "clocks": clocks,
                 "fp64_single_instance": {"value": fp64_val, "unit": UNIT,
