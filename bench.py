@@ -556,6 +556,24 @@ def sampled_parity(fr, meshes, fms, sol, n_sample=48):
     return out
 
 
+def summarise_parity(parity, target=1e-5):
+    """One verdict over the sampled parity cases: the worst error against the
+    oracle on the exact input beside the mixed-precision target, and whether
+    every case met it and every sampled point stayed within the FP32 forward
+    bound.  A miss is also written to stderr, so that it is not only a field
+    of the line."""
+    if not parity:
+        return None
+    out = {"max_rel_l2_vs_oracle_exact_input": max(c["rel_l2_vs_oracle_exact_input"] for c in parity),
+           "target_rel_l2": target,
+           "all_within_target": all(c["rel_l2_vs_oracle_exact_input"] <= target for c in parity),
+           "max_pointwise_ratio_to_bound": max(c["max_pointwise_ratio_to_bound"] for c in parity),
+           "all_pointwise_within_bound": all(c["pointwise_within_bound"] for c in parity)}
+    if not (out["all_within_target"] and out["all_pointwise_within_bound"]):
+        print("bench: sampled FP32 parity misses a bound: " + json.dumps(out), file=sys.stderr, flush=True)
+    return out
+
+
 def sampled_parity_varp(meshes, fms, sol):
     """Variable degree: the whole residual of the smallest candidate and of
     the last one (FP32 library vs the variable-degree oracle)."""
@@ -839,6 +857,7 @@ def run_gpu(args):
                                          "roofline": fp64_alu,
                                          "schedules": sorted(set(fp64_sched))},
                 "parity": parity,
+                "parity_summary": summarise_parity(parity),
                 "observers": {"oaspl_db_first4": oaspl,
                               "oaspl_window_samples": args.steps,
                               "mean_force_first2": forces,

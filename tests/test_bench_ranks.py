@@ -171,3 +171,23 @@ def test_oracle_all_cores_ends_at_once_when_a_process_dies(monkeypatch):
     with pytest.raises(RuntimeError, match="exit codes"):
         bench.oracle_all_cores(M.periodic_box(2, (4, 4), (0, 0), (1, 1)), 4, 0, 1, 1e-4, limit_s=120.0)
     assert time.monotonic() - t0 < 60.0
+
+
+def test_parity_summary_flags_a_missed_bound(capsys):
+    """The bench's sampled-parity verdict: met when every case is within the
+    target and the pointwise forward bound, flagged (and written to stderr)
+    when one case misses either."""
+    import bench
+    ok = {"rel_l2_vs_oracle_exact_input": 8e-6, "max_pointwise_ratio_to_bound": 0.4,
+          "pointwise_within_bound": True}
+    s = bench.summarise_parity([ok, dict(ok, rel_l2_vs_oracle_exact_input=9e-6)])
+    assert s["all_within_target"] and s["all_pointwise_within_bound"]
+    assert s["max_rel_l2_vs_oracle_exact_input"] == 9e-6
+    assert "misses" not in capsys.readouterr().err
+    bad = dict(ok, rel_l2_vs_oracle_exact_input=1.4e-5, max_pointwise_ratio_to_bound=2.8,
+               pointwise_within_bound=False)
+    s = bench.summarise_parity([ok, bad])
+    assert not s["all_within_target"] and not s["all_pointwise_within_bound"]
+    assert s["max_pointwise_ratio_to_bound"] == 2.8
+    assert "misses a bound" in capsys.readouterr().err
+    assert bench.summarise_parity(None) is None
