@@ -1676,6 +1676,9 @@ extern "C" fr_status fr_set_states(fr_solver *s, const double *u) {
     if (batch_stageable(s)) {
         fr_status st = enqueue_upload_batch(s, u);
         cudaError_t e = cudaStreamSynchronize(s->stream);   // the host array must outlive the copy
+        // (on an error return the solver stream may not have waited for every
+        // copy already issued on the transfer stream)
+        if (s->xfer) cudaStreamSynchronize(s->xfer);
         if (st != FR_OK) return st;
         FR_CK(e);
         return FR_OK;
@@ -1700,6 +1703,7 @@ extern "C" fr_status fr_get_states(fr_solver *s, double *u) {
     if (batch_stageable(s)) {
         fr_status st = enqueue_download_batch(s, 0, u);
         cudaError_t e = cudaStreamSynchronize(s->stream);
+        if (s->xfer) cudaStreamSynchronize(s->xfer);   // as in fr_set_states
         if (st != FR_OK) return st;
         FR_CK(e);
         return FR_OK;
