@@ -301,12 +301,22 @@ def oracle_sample_rate(mesh, n_sample, n_steps, dt, seed=0, n_warm=0, barrier=No
                             f"(their 2-ring neighbourhood evaluated), {n_steps} LSRK45 steps")
 
 
-def host_cores():
-    """Host cores this process may run on."""
+def host_cores(cpu_max="/sys/fs/cgroup/cpu.max"):
+    """Host cores this process may run on: its CPU affinity, capped by a
+    cgroup CPU quota where one is set (a container may see every core of
+    the machine but be given a share of them)."""
     try:
-        return len(os.sched_getaffinity(0))
+        n = len(os.sched_getaffinity(0))
     except AttributeError:
-        return os.cpu_count() or 1
+        n = os.cpu_count() or 1
+    try:
+        with open(cpu_max) as f:
+            quota, period = f.read().split()[:2]
+        if quota != "max" and float(period) > 0:
+            n = min(n, max(1, int(-(-float(quota) // float(period)))))
+    except (OSError, ValueError):
+        pass
+    return n
 
 
 def _oracle_worker(name, mesh, n_sample, n_warm, n_steps, dt, seed, barrier, results):

@@ -191,3 +191,19 @@ def test_parity_summary_flags_a_missed_bound(capsys):
     assert s["max_pointwise_ratio_to_bound"] == 2.8
     assert "misses a bound" in capsys.readouterr().err
     assert bench.summarise_parity(None) is None
+
+
+def test_host_cores_respects_a_cgroup_quota(tmp_path):
+    """The all-core oracle timing starts one process per core the bench may
+    use: the affinity mask, capped by a cgroup CPU quota (rounded up)."""
+    import os
+    import bench
+    aff = len(os.sched_getaffinity(0))
+    f = tmp_path / "cpu.max"
+    f.write_text("max 100000\n")
+    assert bench.host_cores(str(f)) == aff
+    f.write_text("150000 100000\n")
+    assert bench.host_cores(str(f)) == min(aff, 2)
+    f.write_text("50000 100000\n")
+    assert bench.host_cores(str(f)) == 1
+    assert bench.host_cores(str(tmp_path / "absent")) == aff
