@@ -341,7 +341,9 @@ class Solver:
         return int(lib().fr_last_launch_count(self.handle))
 
     def probe_add(self, inst, x):
-        x = np.ascontiguousarray(x, dtype=np.float64)
+        x = np.ascontiguousarray(x, dtype=np.float64).reshape(-1)
+        if x.size != self.dim:
+            raise ValueError(f"probe point needs {self.dim} coordinates")
         pid = C.c_int()
         _check(lib().fr_probe_add(self.handle, inst, _dptr(x), C.byref(pid)), "fr_probe_add")
         return pid.value
