@@ -191,8 +191,20 @@ class Mesh:
         tags = np.ascontiguousarray(mesh.face_tag, dtype=np.int32)
         sh = np.ascontiguousarray(mesh.periodic_shift, dtype=np.float64).reshape(-1, self.dim)
         gn = None if getattr(mesh, "geo_nodes", None) is None else np.ascontiguousarray(mesh.geo_nodes, dtype=np.float64)
+        q = int(getattr(mesh, "geo_order", 1))
+        # the C call reads these arrays by the sizes it is given: check their shapes here
+        if self.dim not in (2, 3):
+            raise ValueError("dim must be 2 or 3")
+        if xyz.ndim != 2 or xyz.shape[1] != self.dim:
+            raise ValueError(f"xyz must have shape (n_vert, {self.dim})")
+        if ev.ndim != 2 or ev.shape[1] != 2 ** self.dim:
+            raise ValueError(f"elem_vert must have shape (n_elem, {2 ** self.dim})")
+        if tags.shape != (ev.shape[0], 2 * self.dim):
+            raise ValueError(f"face_tag must have shape (n_elem, {2 * self.dim})")
+        if gn is not None and (q < 1 or gn.size != ev.shape[0] * (q + 1) ** self.dim * self.dim):
+            raise ValueError(f"geo_nodes must hold n_elem x (geo_order + 1)^{self.dim} x {self.dim} values")
         h = C.c_void_p()
-        geo = (int(getattr(mesh, "geo_order", 1)), None if gn is None else _dptr(gn),
+        geo = (q, None if gn is None else _dptr(gn),
                tags.ctypes.data_as(C.POINTER(C.c_int32)), sh.shape[0], _dptr(sh) if sh.size else None)
         if varp:
             ep = np.ascontiguousarray(p, dtype=np.int32)

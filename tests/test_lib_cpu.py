@@ -84,6 +84,22 @@ def test_mesh_errors_are_reported(fr):
     assert e.value.status == 1                       # FR_ERR_INVALID_ARG
 
 
+def test_binding_refuses_arrays_of_the_wrong_shape(fr):
+    """The binding checks the mesh arrays' shapes before the C call, which
+    reads them by the sizes it is given."""
+    import copy
+    base = M.naca_omesh(0.04, 0.3, 0.1, 2.0, 500)
+    for field, bad in (("xyz", lambda m: m.xyz[:, :1]),
+                       ("elem_vert", lambda m: m.elem_vert[:, :3]),
+                       ("face_tag", lambda m: m.face_tag[:-1]),
+                       ("geo_nodes", lambda m: m.geo_nodes.reshape(-1)[:-2])):
+        m = copy.copy(base)
+        setattr(m, field, bad(base))
+        with pytest.raises(ValueError, match=field):
+            fr.Mesh(m, 3)
+    assert fr.Mesh(base, 3).n_elem == base.n_elem
+
+
 def test_solver_needs_a_device_workspace(fr):
     """fr_solver_create refuses a null workspace before touching the GPU."""
     import ctypes as C
